@@ -1,0 +1,267 @@
+"""Pins of the oracle's leapfrog loop (Eq. 7) against mathematics it must obey.
+
+- exact discrete eigenmodes of the Laplacian with Dirichlet / Neumann ghosts
+  (closed-form symbol of Eq. 9), one step and many steps (closed-form
+  solution of the two-level recurrence);
+- the damping term of Eq. 4 (amplitude decay e^{-eta t});
+- source-receiver reciprocity (symmetric discrete operator);
+- mirror symmetry of a symmetric set-up;
+- the homogeneous Green's functions in 2D and 3D (Sec. 2.5, V1) with
+  convergence under refinement;
+- second-order convergence in time (Sec. 2.5, V2) and order-p convergence in
+  space (V3) with manufactured solutions;
+- the variable-density operator by manufactured solutions (Sec. 2.5, V4);
+- constant density through the variable-density path equals constant density.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import analytic
+
+
+def _symbol(order, k, h):
+    """Fourier symbol of Eq. 9 along one axis: (v_0 + 2 sum_j v_j cos(j k h)) / h^2."""
+    v = [float(x) for x in oracle.second_derivative_weights(order)]
+    return (v[0] + 2.0 * sum(v[j] * math.cos(j * k * h) for j in range(1, len(v)))) / (h * h)
+
+
+def _mode(shape, spacing, kinds, m, order):
+    """Separable sine (Dirichlet) or cosine (Neumann) mode fitting the grid exactly."""
+    f = np.ones(shape)
+    lam = 0.0
+    for a, (n, h, kind, mm) in enumerate(zip(shape, spacing, kinds, m)):
+        L = (n - 1) * h
+        k = mm * math.pi / L
+        x = np.arange(n) * h
+        g = np.sin(k * x) if kind == "d" else np.cos(k * x)
+        sh = [1] * len(shape)
+        sh[a] = n
+        f = f * g.reshape(sh)
+        lam += _symbol(order, k, h)
+    return f, lam
+
+
+@pytest.mark.parametrize("ndim,order", [(2, 4), (2, 8), (3, 8), (3, 16)])
+@pytest.mark.parametrize("kind", ["d", "n"])
+def test_one_step_is_the_exact_symbol(ndim, order, kind):
+    """p1 - p0 = kappa * symbol * mode for p0 = p_{-1} = mode (all rows incl. boundary)."""
+    r = order // 2
+    shape = (r + 9, r + 7, r + 11)[:ndim] if ndim == 3 else (r + 9, r + 13)
+    spacing = (3.0, 4.0, 5.0)[:ndim] if ndim == 3 else (3.0, 5.0)
+    m = (2, 1, 3)[:ndim] if ndim == 3 else (2, 3)
+    mode, lam = _mode(shape, spacing, [kind] * ndim, m, order)
+    c, dt = 700.0, 1e-3
+    bc = {"d": oracle.BC_DIRICHLET, "n": oracle.BC_NEUMANN}[kind]
+    bc6 = [bc] * 6 if ndim == 3 else [bc, bc, 0, 0, bc, bc]
+    vel = np.full(shape, c)
+    _, p1 = oracle.run_raw(ndim, shape, spacing, order, bc6, np.zeros(shape), dt, vel,
+                           n_steps=1, p0=mode, pm1=mode)
+    kappa = (c * dt) ** 2
+    assert np.allclose(p1 - mode, kappa * lam * mode, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("eta", [0.0, 40.0])
+def test_many_steps_follow_the_mode_recurrence(eta):
+    """A Dirichlet mode obeys (1+e) a_{n+1} = (2 - kappa lam) a_n - (1-e) a_{n-1} exactly."""
+    order = 8
+    shape, spacing = (21, 17), (5.0, 7.0)
+    mode, lam = _mode(shape, spacing, ["d", "d"], (1, 2), order)
+    c, dt = 1500.0, 1e-3
+    kappa = (c * dt) ** 2
+    e = eta * dt
+    n_steps = 300
+    _, p = oracle.run_raw(2, shape, spacing, order, [1, 1, 0, 0, 1, 1], np.full(shape, eta), dt,
+                          np.full(shape, c), n_steps=n_steps, p0=mode, pm1=mode)
+    # closed form through the roots of (1+e) mu^2 - (2 - kappa lam) mu + (1-e) = 0
+    a, b, cc = 1.0 + e, -(2.0 + kappa * lam), 1.0 - e
+    disc = complex(b * b - 4 * a * cc)
+    mu1 = (-b + disc ** 0.5) / (2 * a)
+    mu2 = (-b - disc ** 0.5) / (2 * a)
+    # a_0 = 1, a_{-1} = 1  ->  A + B = 1, A/mu1 + B/mu2 = 1
+    B = (1 - 1 / mu1) / (1 / mu2 - 1 / mu1)
+    A = 1 - B
+    amp = (A * mu1 ** n_steps + B * mu2 ** n_steps).real
+    assert np.allclose(p, amp * mode, rtol=0, atol=1e-11)
+    if eta > 0:
+        # Eq. 4: the damped oscillation decays like exp(-eta t), up to O((eta dt)^2)
+        assert math.log(abs(mu1)) == pytest.approx(-eta * dt, rel=e * e)
+        assert np.abs(p).max() < 1.5 * math.exp(-eta * n_steps * dt)
+
+
+def test_reciprocity_heterogeneous_damped():
+    """Dirichlet / 'none' faces make the operator symmetric: G(s->r) == G(r->s)."""
+    rng = np.random.default_rng(5)
+    shape, spacing, order = (40, 46), (10.0, 10.0), 8
+    vel = 1500.0 + 1500.0 * rng.random(shape)
+    dt = 0.4 * 10.0 / vel.max()
+    nbl = [6, 6, 6, 6]
+    bc = ["null_dirichlet", "none", "none", "null_dirichlet"]
+    w = oracle.ricker_samples(20.0, dt, 160)
+    a, b = (77.0, 123.4), (251.3, 180.0)
+    s1, _ = oracle.forward(2, shape, spacing, order, vel, dt, 160, src_pos=[a], wavelet=w,
+                           rec_pos=[b], nbl=nbl, bc=bc, damp_alpha=2.0, damp_degree=2)
+    s2, _ = oracle.forward(2, shape, spacing, order, vel, dt, 160, src_pos=[b], wavelet=w,
+                           rec_pos=[a], nbl=nbl, bc=bc, damp_alpha=2.0, damp_degree=2)
+    assert np.abs(s1).max() > 1e-4
+    assert np.allclose(s1, s2, rtol=0, atol=1e-12 * np.abs(s1).max())
+
+
+def test_mirror_symmetry_3d():
+    shape, spacing, order = (24, 21, 21), (10.0, 10.0, 10.0), 4
+    dt = 0.4 * 10.0 / 2000.0
+    vel = np.full(shape, 2000.0)
+    vel[12:] = 2500.0
+    w = oracle.ricker_samples(25.0, dt, 60)
+    nbl = [0, 4, 4, 4, 4, 4]
+    bc = ["null_neumann"] + ["null_dirichlet"] * 5
+    rec = [(50.0, 30.0, 60.0), (50.0, 90.0, 60.0), (50.0, 60.0, 30.0), (50.0, 60.0, 90.0)]
+    s, p = oracle.forward(3, shape, spacing, order, vel, dt, 60, src_pos=[(35.0, 60.0, 60.0)],
+                          wavelet=w, rec_pos=rec, nbl=nbl, bc=bc, damp_alpha=1.0)
+    assert np.abs(s).max() > 0
+    assert np.allclose(s[:, 0], s[:, 1], rtol=0, atol=1e-14)
+    assert np.allclose(s[:, 0], s[:, 2], rtol=0, atol=1e-14)
+    assert np.allclose(p, p[:, ::-1, :], rtol=0, atol=1e-14)
+    assert np.allclose(p, p.transpose(0, 2, 1), rtol=0, atol=1e-14)
+
+
+def test_dirichlet_boundary_nodes_stay_zero():
+    shape = (30, 30)
+    vel = np.full(shape, 1500.0)
+    dt = 0.4 * 10.0 / 1500.0
+    w = oracle.ricker_samples(20.0, dt, 120)
+    # a radius-2 source window at z = 1.25 cells covers the boundary row 0
+    _, p = oracle.forward(2, shape, (10.0, 10.0), 8, vel, dt, 120, src_pos=[(12.5, 145.0)],
+                          wavelet=w, nbl=[0, 0, 0, 0], bc=["null_dirichlet"] * 4,
+                          window_radius=2)
+    assert np.abs(p).max() > 0
+    assert np.all(p[0] == 0) and np.all(p[-1] == 0) and np.all(p[:, 0] == 0) and np.all(p[:, -1] == 0)
+
+
+def test_window_outside_grid_is_rejected():
+    shape = (30, 30)
+    with pytest.raises(ValueError):
+        oracle.forward(2, shape, (10.0, 10.0), 8, np.full(shape, 1500.0), 1e-3, 5,
+                       src_pos=[(12.5, 145.0)], wavelet=[0.0] * 5, window_radius=4)
+
+
+def test_constant_density_through_variable_density_path_is_identical():
+    rng = np.random.default_rng(1)
+    shape = (33, 29)
+    vel = 1500.0 + 500.0 * rng.random(shape)
+    dt = 0.4 * 10.0 / vel.max()
+    w = oracle.ricker_samples(15.0, dt, 80)
+    kw = dict(src_pos=[(101.0, 133.0)], wavelet=w, rec_pos=[(40.0, 70.0)], nbl=[5, 5, 5, 5],
+              bc=["null_neumann", "null_dirichlet", "null_dirichlet", "null_dirichlet"],
+              damp_alpha=3.0)
+    s1, p1 = oracle.forward(2, shape, (10.0, 10.0), 8, vel, dt, 80, **kw)
+    s2, p2 = oracle.forward(2, shape, (10.0, 10.0), 8, vel, dt, 80, rho=np.full(shape, 2.3e3), **kw)
+    assert np.array_equal(s1, s2) and np.array_equal(p1, p2)
+
+
+def test_sponge_absorbs():
+    """With the absorbing layer the late-time field is far smaller than with a bare Dirichlet box."""
+    shape = (81, 81)
+    vel = np.full(shape, 1500.0)
+    dt = 0.4 * 10.0 / 1500.0
+    n = 500
+    w = oracle.ricker_samples(15.0, dt, n)
+    e = {}
+    for nbl, alpha in ((0, 0.0), (20, 1e-3 * 8.0)):
+        shape_i = shape
+        pos = [(400.0 - 10.0 * nbl, 400.0 - 10.0 * nbl)]
+        _, p = oracle.forward(2, shape_i, (10.0, 10.0), 8, vel, dt, n, src_pos=pos, wavelet=w,
+                              nbl=[nbl] * 4, bc=["null_dirichlet"] * 4, damp_alpha=alpha)
+        e[nbl] = float(np.sum(p[20:61, 20:61] ** 2))
+    assert e[20] < 1e-3 * e[0]
+
+
+# ---- Green's functions (Sec. 2.5, V1) ---------------------------------------
+
+def _green_case_2d(h, f=20.0, c=1500.0, t_end=0.25):
+    L = 500.0
+    n = int(round(L / h)) + 1
+    shape = (n, n)
+    dt = 0.4 * h / c
+    steps = int(round(t_end / dt))
+    t0 = 1.5 / f
+    w = oracle.ricker_samples(f, dt, steps, t0=t0)
+    src = (250.0, 250.0)
+    rec = (250.0 + 60.0, 250.0 + 80.0)  # 100 m away
+    s, _ = oracle.forward(2, shape, (h, h), 8, np.full(shape, c), dt, steps, src_pos=[src],
+                          wavelet=w, rec_pos=[rec], nbl=[0, 0, 0, 0], bc=["null_dirichlet"] * 4)
+    t = (np.arange(steps) + 1) * dt
+    ref = np.array([analytic.green_2d(100.0, tt, c, f, t0) for tt in t])
+    return np.linalg.norm(s[:, 0] - ref) / np.linalg.norm(ref)
+
+
+def test_green_2d_and_refinement():
+    e1 = _green_case_2d(5.0)
+    e2 = _green_case_2d(2.5)
+    assert e1 < 3e-2
+    assert e2 < 0.5 * e1
+
+
+def test_green_3d():
+    h, c, f = 10.0, 1500.0, 10.0
+    n = 81
+    shape = (n, n, n)
+    dt = 0.4 * h / c
+    t_end = 0.42
+    steps = int(round(t_end / dt))
+    t0 = 1.5 / f
+    w = oracle.ricker_samples(f, dt, steps, t0=t0)
+    src = (400.0, 400.0, 400.0)
+    rec = (400.0 + 60.0, 400.0 - 48.0, 400.0 + 64.0)  # 100 m away
+    s, _ = oracle.forward(3, shape, (h, h, h), 8, np.full(shape, c), dt, steps, src_pos=[src],
+                          wavelet=w, rec_pos=[rec], nbl=[0] * 6, bc=["null_dirichlet"] * 6)
+    t = (np.arange(steps) + 1) * dt
+    ref = np.array([analytic.green_3d(100.0, tt, c, f, t0) for tt in t])
+    assert np.linalg.norm(s[:, 0] - ref) / np.linalg.norm(ref) < 3e-2
+
+
+# ---- convergence (Sec. 2.5, V2-V4) -------------------------------------------
+
+def _mms_error(order, h, dt, t_end, density, c=2000.0, L=440.0):
+    n = int(round(L / h)) + 1
+    steps = int(round(t_end / dt))
+    rho, F, T, uN = analytic.mms_2d(L, c, n, n, h, dt, steps, density)
+    _, p = oracle.forward(2, (n, n), (h, h), order, np.full((n, n), c), dt, steps, nbl=[0] * 4,
+                          bc=["null_dirichlet"] * 4, rho=rho, force_fields=F, force_sigs=T)
+    # normalise by the spatial shape (|T(t)| <= 1), not by u*(t_N), which can vanish
+    shape_norm = np.linalg.norm(analytic.mms_2d(L, c, n, n, h, dt, 0, None)[1][0]) * c * c
+    return np.linalg.norm(p - uN) / shape_norm
+
+
+def test_time_convergence_second_order():
+    """V2: space error negligible (order 16, fine grid); halving dt quarters the error."""
+    errs = [_mms_error(16, 11.0, dt, 0.1, None) for dt in (8e-4, 4e-4, 2e-4)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.9 < r < 2.1 for r in rates), (errs, rates)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_space_convergence_order(order):
+    """V3: time error negligible (dt = 5 us); halving h divides the error by about 2^order."""
+    errs = [_mms_error(order, h, 5e-6, 0.02, None) for h in (44.0, 22.0)]
+    rate = math.log2(errs[0] / errs[1])
+    assert order - 0.4 < rate < order + 0.4, (errs, rate)
+
+
+def test_variable_density_mms_interior_order():
+    """Strong density contrast whose ln is even at the walls: about 4th-order convergence."""
+    errs = [_mms_error(4, h, 5e-6, 0.02, "cos") for h in (44.0, 22.0, 11.0)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(3.5 < r < 4.4 for r in rates), (errs, rates)
+    # the advective term matters: solving without it misses by far more
+    errs_wrong = _mms_error(4, 11.0, 5e-6, 0.02, "cos_ignored")
+    assert errs_wrong > 1000 * errs[2]
+
+
+def test_variable_density_mms_paper_setup():
+    """V4 as in the paper (Eq. 14-15, c = 2 km/s, 440 m box): error falls under refinement."""
+    errs = [_mms_error(8, h, 5e-5, 0.05, "paper") for h in (40.0, 20.0, 10.0)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 2e-6
