@@ -1,0 +1,303 @@
+"""Throughput benchmark of the forward solver (grid-point updates per second).
+
+One bench step = one complete forward simulation of the workload (every
+time step of the leapfrog loop with source injection and receiver sampling),
+inputs resident in HBM.  Default workload: 3d_layered_256 (256^3 nodes,
+order 8, 2000 time steps, 4096 receivers); Gpts/s counts every computed node
+including the absorbing layer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Under torchrun each rank runs its own independent simulation (replicas of
+the same workload, weak scaling); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpts/s (grid-point updates per second)"
+UNIT = "Gpts/s"
+BYTES_PER_UPDATE = {False: 16, True: 20}  # algorithmic bytes per node update (constant / variable density)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("stencil_plain.cuh",):
+        with open(os.path.join(ROOT, "paper_2201_05278_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(workload):
+    """DRAM bytes per stencil launch from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
+    try:
+        rec = {}
+        with open(path) as f:
+            for ln in f:
+                if ":" in ln and not ln.startswith("#"):
+                    k, v = ln.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        if rec.get("workload") != workload or rec.get("source_sha") != _kernel_source_hash():
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload_name, budget_s=12.0):
+    """Times the FP64 oracle on the host cores on a bounded sample of the workload."""
+    from paper_2201_05278_b300 import workloads
+    import oracle
+    threads = os.cpu_count() or 1
+    w = workloads.make(workload_name)
+    wav = oracle.ricker_samples(w.f_peak, w.dt, 400, t0=w.t0)
+
+    def run(steps):
+        t = time.perf_counter()
+        oracle.forward(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, steps,
+                       src_pos=[tuple(p) for p in w.src_pos], wavelet=np.asarray(wav),
+                       rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc, damp_alpha=w.damp_alpha,
+                       damp_degree=w.damp_degree,
+                       rho=None if w.density is None else w.density.astype(np.float64),
+                       window_radius=w.window_radius, threads=threads)
+        return time.perf_counter() - t
+
+    # calibrate: a call costs set-up (windows, padded copies) plus a per-step loop
+    t1 = run(1)
+    t3 = run(3)
+    per_step = max((t3 - t1) / 2.0, 1e-4)
+    setup = max(t1 - per_step, 0.0)
+    steps = int(max(2, min(400, (budget_s - setup) / per_step)))
+    t = run(steps)
+    value = w.nodes * steps / t / 1e9  # whole call, set-up included
+    return {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%s full grid %s, %d of %d time steps, FP64, %d threads" % (
+                workload_name, "x".join(map(str, w.shape)), steps, w.n_steps, threads)}, t
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="3d_layered_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per, secs = [], 0.0
+        for _ in range(args.warmup):
+            cpu_baseline(args.workload, budget_s=2.0)
+        for _ in range(args.steps):
+            cb, t = cpu_baseline(args.workload, budget_s=6.0)
+            per.append(cb["value"])
+            secs += t
+        v = statistics.median(per)
+        cb["value"] = v
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": args.workload},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2201_05278_b300 import api, workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workloads.make(args.workload)
+    vd = w.density is not None
+    stream = torch.cuda.current_stream(dev)
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
+                           stream=stream)
+    vel_d = torch.from_numpy(w.velocity).to(dev)
+    rho_d = None if w.density is None else torch.from_numpy(w.density).to(dev)
+    api.sw_set_model(g, vel_d, rho_d)
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
+    api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+    n_rec = len(w.rec_pos)
+    seis = torch.empty((w.n_steps, n_rec), dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        api.sw_forward(g, w.n_steps, seis, None)
+    api.sw_set_profiling(g, True)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stencil_ms, stencil_launches, kernels = 0.0, 0, 0
+    start.record(stream)
+    for _ in range(args.steps):
+        api.sw_forward(g, w.n_steps, seis, None)
+        ms, nl, nk = api.sw_get_profile(g)
+        stencil_ms += ms
+        stencil_launches += nl
+        kernels += nk
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    api.sw_set_profiling(g, False)
+
+    updates = w.updates * args.steps * world
+    value = updates / (elapsed_ms * 1e-3) / 1e9
+
+    # e2e through the C ABI with host buffers: H2D of the velocity model every step
+    # (sw_set_model from pinned host memory) and D2H of the seismogram.
+    vel_h = torch.from_numpy(w.velocity).pin_memory()
+    rho_h = None if w.density is None else torch.from_numpy(w.density).pin_memory()
+    seis_h = torch.empty((w.n_steps, n_rec), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        api.sw_set_model(g, vel_h, rho_h)
+        api.sw_forward(g, w.n_steps, seis_h, None)
+        _ = float(seis_h[-1, 0])
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = w.updates * e2e_steps * world / e2e_s / 1e9
+    h2d = w.velocity.nbytes + (0 if w.density is None else w.density.nbytes)
+    d2h = seis_h.numel() * 4
+
+    peak, peak_kind = _peaks()
+    avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
+    alg_bytes = BYTES_PER_UPDATE[vd] * w.nodes
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = _traffic_record(args.workload)
+    api.sw_destroy_grid(g)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(w.shape), "space_order": w.order,
+                       "time_steps_per_forward": w.n_steps, "receivers": n_rec, "sources": len(w.src_pos),
+                       "variable_density": vd, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "stencil (per-launch CUDA events, %d launches)" % stencil_launches,
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(kernels),
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cb, _ = cpu_baseline(args.workload)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

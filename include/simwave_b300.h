@@ -1,0 +1,161 @@
+/*
+ * simwave_b300.h -- C ABI of the B300 (sm_103a) finite-difference acoustic
+ * wave solver.  It implements the method of "simwave - A Finite Difference
+ * Simulator for Acoustic Waves Propagation" (arXiv 2201.05278): explicit
+ * second-order leapfrog in time (Sec. 2.2, Eq. 6-7), central differences of
+ * order 2..20 in space (Sec. 2.3, Eq. 9-10), constant density (Eq. 3) or
+ * variable density (Eq. 2 in the expanded form of Eq. 5), an absorbing
+ * layer (Sec. 2.1, Eq. 4), null Dirichlet / null Neumann faces, and
+ * Kaiser-windowed sinc sources and receivers (Sec. 2.4, Eq. 11-12).
+ *
+ * Conventions shared by every call
+ *   - Axes are (z, y, x) in 3D and (z, x) in 2D; x is contiguous.  Arrays
+ *     that describe axes have ndim entries, arrays that describe faces have
+ *     2*ndim entries in the order (z-, z+, [y-, y+,] x-, x+).
+ *   - Grid-shaped arrays are dense row-major FP32 [nz][ny][nx] (3D) or
+ *     [nz][nx] (2D) and include the absorbing layer.
+ *   - Array arguments marked "host or device" may point to host memory
+ *     (pageable or pinned) or to device memory of the grid's device; the
+ *     library detects which and copies as needed.  The caller keeps
+ *     ownership of every buffer it passes; input buffers are only read
+ *     during the call.
+ *   - All device work runs on the stream given to sw_create_grid.
+ *   - No call throws; each returns a status.  sw_last_error() returns a
+ *     thread-local message for the last failing call of the calling thread.
+ *   - A grid handle must not be used from two threads at once.
+ */
+#ifndef SIMWAVE_B300_H
+#define SIMWAVE_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sw_grid sw_grid;
+
+typedef enum {
+  SW_OK = 0,
+  SW_EINVAL = 1,   /* invalid argument (sizes, order, positions, NULL pointers) */
+  SW_ECFL = 2,     /* user time step above the stability bound of Eq. 8 */
+  SW_ENOMEM = 3,   /* device or host allocation failed */
+  SW_ECUDA = 4,    /* a CUDA runtime call failed */
+  SW_ETIMEOUT = 5, /* a kernel's bounded wait gave up (device error flag set) */
+  SW_ESTATE = 6    /* call out of order (e.g. sw_forward before sw_set_model) */
+} sw_status;
+
+enum { SW_BC_NONE = 0, SW_BC_DIRICHLET = 1, SW_BC_NEUMANN = 2 };
+
+/*
+ * sw_create_grid -- grid, discretisation, boundary treatment, time step.
+ * (Sec. 2.1-2.3, Sec. 4 "SpaceModel"/"TimeModel"; Eq. 4, 8, 9-10.)
+ *
+ *   out          receives the handle (library-owned; free with sw_destroy_grid)
+ *   ndim         2 or 3
+ *   shape        [ndim] node counts including the absorbing layer, each >= r+1
+ *                where r = space_order/2
+ *   spacing      [ndim] grid spacing in metres (> 0)
+ *   space_order  even, 2..20 (stencil radius r = space_order/2)
+ *   nbl          [2*ndim] absorbing-layer width in cells per face (>= 0); the
+ *                physical domain is nodes nbl_lo .. n-1-nbl_hi on each axis
+ *   bc           [2*ndim] SW_BC_* per face: Dirichlet holds the face node at
+ *                0 with odd ghost mirroring, Neumann mirrors even, NONE uses
+ *                zero ghosts
+ *   damp_alpha   alpha of eta = alpha d^p (1/s); d is the Euclidean distance
+ *                in cells from a node to the physical domain
+ *   damp_degree  p >= 0
+ *   dt           time step in seconds; <= 0 selects the bound of Eq. 8 once
+ *                the velocity is known (sw_set_model).  A positive dt above
+ *                that bound makes sw_set_model fail with SW_ECFL.
+ *   cuda_stream  cudaStream_t the library enqueues all work on (NULL = the
+ *                legacy default stream); the current device at this call is
+ *                the grid's device
+ * Allocates the two wavefield levels and the model fields on the device.
+ */
+sw_status sw_create_grid(sw_grid** out, int ndim, const int64_t* shape, const double* spacing,
+                         int space_order, const int* nbl, const int* bc, double damp_alpha,
+                         int damp_degree, double dt, void* cuda_stream);
+
+/*
+ * sw_set_model -- velocity and optional density (Sec. 2, Eq. 2-3, 5).
+ *
+ *   velocity  grid-shaped FP32, m/s, host or device; every value finite, > 0
+ *   density   grid-shaped FP32, any unit, > 0, host or device; NULL selects
+ *             the constant-density operator.  With a density the update uses
+ *             Lap p - grad(ln rho) . grad p (Eq. 5-7), ln(rho) mirrored even
+ *             into the ghost layers.
+ * Resolves dt (Eq. 8), builds kappa = (c dt)^2 and the damping coefficients.
+ * Returns SW_ECFL if a user dt exceeds the bound.  Synchronises the stream.
+ */
+sw_status sw_set_model(sw_grid* g, const float* velocity, const float* density);
+
+/*
+ * sw_set_acquisition -- sources, receivers, wavelet (Sec. 2.4, Eq. 11-12).
+ *
+ *   n_src, src_pos      number of sources and their [n_src][ndim] positions
+ *                       in metres from the corner of the physical domain
+ *                       (host, FP64)
+ *   n_rec, rec_pos      same for receivers (host, FP64)
+ *   nt, wavelet         [nt] samples S(t_n) shared by every source, or
+ *                       [n_src][nt] when wavelet_per_source != 0; FP32, host
+ *                       or device
+ *   window_radius       Kaiser window half-width r_w, 1..10; every window
+ *                       (2 r_w nodes per axis) must lie inside the grid, else
+ *                       SW_EINVAL
+ * Each point spreads over the nodes with |i - s| < r_w with weights
+ * W(i - s) sinc(i - s) per axis (product over axes).
+ */
+sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n_rec,
+                             const double* rec_pos, int nt, const float* wavelet,
+                             int wavelet_per_source, int window_radius);
+
+/*
+ * sw_forward -- run n_steps leapfrog steps from rest (p[0] = p[-1] = 0).
+ * (Sec. 2.2 Eq. 7, Sec. 3.2 back-end, Sec. 4 "Solver.forward".)
+ *
+ * Step n (0-based) computes p[n+1] from p[n], p[n-1], adds the sources
+ * S(t_n) (t_n = n dt), then records the receivers on p[n+1].
+ *   n_steps      >= 0 and <= nt of the acquisition when there are sources
+ *   seismogram   [n_steps][n_rec] FP32 output, host or device, may be NULL
+ *                when n_rec == 0; row n holds the receivers at t_{n+1}
+ *   final_field  grid-shaped FP32 output p[n_steps], host or device, or NULL
+ * Synchronises the stream and checks the device error flag before
+ * returning (SW_ETIMEOUT if a kernel's bounded wait gave up).
+ */
+sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_field);
+
+/* Time step in use (after sw_set_model when dt was automatic). */
+sw_status sw_get_dt(const sw_grid* g, double* dt);
+
+/*
+ * Ricker wavelet samples, host-side helper (Sec. 2.4, default wavelet):
+ * out[n] = (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), tau = n dt - t0,
+ * computed in FP64 and rounded to FP32.  out is host memory [nt].
+ */
+sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
+
+/*
+ * Kernel timing.  With profiling on, sw_forward records CUDA events around
+ * every stencil launch on the grid's stream; sw_get_profile returns the
+ * summed stencil time and launch count of the last sw_forward and the
+ * number of kernels it launched in total.
+ */
+sw_status sw_set_profiling(sw_grid* g, int enable);
+sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_launches,
+                         int64_t* kernel_launches);
+
+/* Bytes of device memory the grid holds (wavefields, model, acquisition). */
+sw_status sw_get_device_bytes(const sw_grid* g, int64_t* bytes);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* sw_last_error(void);
+
+/* Frees the handle and its device memory (NULL is accepted). */
+void sw_destroy_grid(sw_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMWAVE_B300_H */

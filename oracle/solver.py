@@ -159,8 +159,8 @@ def forward(ndim: int, shape: Sequence[int], spacing: Sequence[float], order: in
     lnrho = None if rho is None else np.log(np.asarray(rho, dtype=np.float64))
     nbl_lo = [nbl[2 * a] for a in range(ndim)]
     b = kaiser_b if kaiser_b is not None else KAISER_B[window_radius]
-    sw = point_windows(src_pos, ndim, spacing, nbl_lo, window_radius, b)
-    rw = point_windows(rec_pos, ndim, spacing, nbl_lo, window_radius, b)
+    sw = point_windows(src_pos, ndim, spacing, nbl_lo, window_radius, b, shape)
+    rw = point_windows(rec_pos, ndim, spacing, nbl_lo, window_radius, b, shape)
     return run_raw(ndim, shape, spacing, order, bc6, eta, dt, vel, lnrho,
                    sw, wavelet, rw, n_steps, force_fields, force_sigs, p0, pm1,
                    threads, want_prev)

@@ -16,6 +16,9 @@ sinc(x) = sin(pi x)/(pi x).  Readings used where the paper is silent:
     parameter table (values attributed to Hicks 2002 Table 2, unverified here).
   - coordinates are metres from the corner of the physical domain, whose first
     node is node nbl_lo along each axis: s = nbl_lo + x / h.
+  - a window that sticks out of the grid only with exactly-zero weights (an
+    on-grid coordinate near a face) is moved inside the grid, each nonzero
+    weight staying on its node; a nonzero weight outside the grid is an error.
 """
 from __future__ import annotations
 
@@ -67,11 +70,31 @@ def grid_coordinate(pos_m: float, spacing: float, nbl_lo: int) -> float:
     return nbl_lo + pos_m / spacing
 
 
+def fit_window(first: int, w: List[float], n: int) -> Tuple[int, List[float]]:
+    """Move a window inside nodes 0..n-1 if only zero weights stick out (else ValueError)."""
+    L = len(w)
+    if first >= 0 and first + L <= n:
+        return first, w
+    if L > n:
+        raise ValueError("window longer than the axis")
+    new_first = min(max(first, 0), n - L)
+    out = [0.0] * L
+    for j, x in enumerate(w):
+        node = first + j
+        if new_first <= node < new_first + L:
+            out[node - new_first] = x
+        elif x != 0.0:
+            raise ValueError("window leaves the grid with a nonzero weight")
+    return new_first, out
+
+
 def point_windows(positions: Sequence[Sequence[float]], ndim: int, spacing: Sequence[float],
-                  nbl_lo: Sequence[int], r: int, b: float | None = None):
+                  nbl_lo: Sequence[int], r: int, b: float | None = None,
+                  shape: Sequence[int] | None = None):
     """Per-point, per-axis (first node, weights) in (z, y, x) order.
 
     In 2D the y axis is a dummy of length 1: first node 0, weight [1.0].
+    With `shape`, windows are fitted into the grid (see fit_window).
     Returns a list over points of [(first_z, wz), (first_y, wy), (first_x, wx)].
     """
     out = []
@@ -80,7 +103,10 @@ def point_windows(positions: Sequence[Sequence[float]], ndim: int, spacing: Sequ
             raise ValueError("position has wrong dimension")
         axes = []
         for a in range(ndim):
-            axes.append(weights_1d(grid_coordinate(p[a], spacing[a], nbl_lo[a]), r, b))
+            fw = weights_1d(grid_coordinate(p[a], spacing[a], nbl_lo[a]), r, b)
+            if shape is not None:
+                fw = fit_window(fw[0], fw[1], int(shape[a]))
+            axes.append(fw)
         if ndim == 2:
             axes = [axes[0], (0, [1.0]), axes[1]]
         out.append(axes)

@@ -1,0 +1,166 @@
+"""Python binding of the C ABI (include/simwave_b300.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays may be
+torch tensors (CPU or CUDA) or numpy arrays; they must be contiguous FP32 for
+grid-shaped data.  Each failing call raises SimwaveError with the library's
+status and message.  All computation happens in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+
+SW_OK, SW_EINVAL, SW_ECFL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_ESTATE = range(7)
+SW_BC_NONE, SW_BC_DIRICHLET, SW_BC_NEUMANN = 0, 1, 2
+STATUS_NAMES = {0: "SW_OK", 1: "SW_EINVAL", 2: "SW_ECFL", 3: "SW_ENOMEM", 4: "SW_ECUDA",
+                5: "SW_ETIMEOUT", 6: "SW_ESTATE"}
+BC_NAMES = {"none": SW_BC_NONE, "null_dirichlet": SW_BC_DIRICHLET, "dirichlet": SW_BC_DIRICHLET,
+            "null_neumann": SW_BC_NEUMANN, "neumann": SW_BC_NEUMANN}
+
+
+class SimwaveError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+def _check(status: int):
+    if status != SW_OK:
+        msg = _lib.load().sw_last_error()
+        raise SimwaveError(status, msg.decode() if msg else "")
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw address of a contiguous FP32 tensor / array (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("expected a contiguous float32 tensor")
+        return a.data_ptr()
+    arr = np.asarray(a)
+    if arr.dtype != np.float32 or not arr.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous float32 array")
+    return arr.ctypes.data
+
+
+class Grid:
+    """Owner of an sw_grid handle; destroyed with sw_destroy_grid."""
+
+    def __init__(self, handle: int, ndim: int, shape, stream):
+        self.handle = handle
+        self.ndim = ndim
+        self.shape = tuple(int(s) for s in shape)
+        self.stream = stream
+        self.n_rec = 0
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            _lib.load().sw_destroy_grid(self.handle)
+            self.handle = None
+
+
+def _faces(vals, ndim, names=None):
+    vals = list(vals)
+    if len(vals) != 2 * ndim:
+        raise ValueError("expected %d face values" % (2 * ndim))
+    if names:
+        vals = [names[v] if isinstance(v, str) else int(v) for v in vals]
+    return (ctypes.c_int * len(vals))(*vals)
+
+
+def sw_create_grid(ndim: int, shape: Sequence[int], spacing: Sequence[float], space_order: int,
+                   nbl: Sequence[int], bc: Sequence, damp_alpha: float = 0.0, damp_degree: int = 3,
+                   dt: float = 0.0, stream=None) -> Grid:
+    lib = _lib.load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * ndim)(*[int(s) for s in shape])
+    spc = (ctypes.c_double * ndim)(*[float(s) for s in spacing])
+    _check(lib.sw_create_grid(ctypes.byref(h), int(ndim), shp, spc, int(space_order),
+                              _faces(nbl, ndim), _faces(bc, ndim, BC_NAMES), float(damp_alpha),
+                              int(damp_degree), float(dt), ctypes.c_void_p(stream)))
+    return Grid(h.value, ndim, shape, stream)
+
+
+def sw_set_model(g: Grid, velocity, density=None) -> None:
+    _check(_lib.load().sw_set_model(g.handle, _ptr(velocity), _ptr(density)))
+
+
+def sw_set_acquisition(g: Grid, src_pos, rec_pos, wavelet, window_radius: int = 4,
+                       wavelet_per_source: bool = False) -> None:
+    src = np.ascontiguousarray(np.asarray(src_pos, dtype=np.float64).reshape(-1, g.ndim))
+    rec = np.ascontiguousarray(np.asarray(rec_pos, dtype=np.float64).reshape(-1, g.ndim))
+    if hasattr(wavelet, "data_ptr"):
+        wav = wavelet
+        nt = int(wavelet.shape[-1])
+    else:
+        wav = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float32))
+        nt = int(wav.shape[-1])
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.load().sw_set_acquisition(
+        g.handle, int(src.shape[0]), src.ctypes.data_as(dp), int(rec.shape[0]), rec.ctypes.data_as(dp),
+        nt, _ptr(wav), int(bool(wavelet_per_source)), int(window_radius)))
+    g.n_rec = int(rec.shape[0])
+    g._keep = [wav]
+
+
+def sw_forward(g: Grid, n_steps: int, seismogram=None, final_field=None) -> None:
+    """Runs n_steps steps; writes into the given output tensors/arrays (either may be None)."""
+    _check(_lib.load().sw_forward(g.handle, int(n_steps), _ptr(seismogram), _ptr(final_field)))
+
+
+def sw_get_dt(g: Grid) -> float:
+    v = ctypes.c_double()
+    _check(_lib.load().sw_get_dt(g.handle, ctypes.byref(v)))
+    return v.value
+
+
+def sw_ricker(f_peak: float, t0: float, dt: float, nt: int) -> np.ndarray:
+    out = np.zeros(int(nt), dtype=np.float32)
+    _check(_lib.load().sw_ricker(float(f_peak), float(t0), float(dt), int(nt), out.ctypes.data))
+    return out
+
+
+def sw_set_profiling(g: Grid, enable: bool = True) -> None:
+    _check(_lib.load().sw_set_profiling(g.handle, int(bool(enable))))
+
+
+def sw_get_profile(g: Grid):
+    """(summed stencil ms, stencil launches, kernel launches) of the last sw_forward."""
+    ms = ctypes.c_double()
+    n1 = ctypes.c_int64()
+    n2 = ctypes.c_int64()
+    _check(_lib.load().sw_get_profile(g.handle, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
+    return ms.value, n1.value, n2.value
+
+
+def sw_get_device_bytes(g: Grid) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.load().sw_get_device_bytes(g.handle, ctypes.byref(v)))
+    return v.value
+
+
+def sw_last_error() -> str:
+    msg = _lib.load().sw_last_error()
+    return msg.decode() if msg else ""
+
+
+def sw_destroy_grid(g: Grid) -> None:
+    g.close()

@@ -1,0 +1,712 @@
+// C ABI of the solver (declared in include/simwave_b300.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/simwave_b300.h"
+#include "aux_kernels.cuh"
+#include "host_setup.h"
+#include "layout.h"
+#include "stencil_plain.cuh"
+
+using namespace sw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sw_status fail(sw_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define SW_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? SW_ENOMEM : SW_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+#define SW_TRY(expr)              \
+  do {                            \
+    sw_status s_ = (expr);        \
+    if (s_ != SW_OK) return s_;   \
+  } while (0)
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int grid_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 148 * 32) b = 148 * 32;
+  return int(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+struct sw_grid {
+  int ndim = 0;
+  int64_t n[3] = {1, 1, 1};  // nz, ny, nx
+  double h[3] = {1, 1, 1};
+  int order = 0, R = 0;
+  int nbl[6] = {0, 0, 0, 0, 0, 0};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double alpha = 0.0;
+  int degree = 0;
+  double dt_user = 0.0, dt = 0.0;
+  bool dt_ready = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Layout lay;
+
+  float* u[2] = {nullptr, nullptr};
+  float* kappa = nullptr;
+  float* lnrho = nullptr;
+  float2* damp = nullptr;
+  int64_t damp_len = 0;
+  int* dflag = nullptr;        // device error flag
+  unsigned* dscratch = nullptr;  // reduction results
+  bool has_model = false, has_density = false;
+  double c_max = 0.0;
+
+  float* staging = nullptr;  // dense grid-sized buffer for host inputs/outputs
+  float* staging2 = nullptr;
+  float* seis_staging = nullptr;
+  int64_t seis_staging_elems = 0;
+
+  // acquisition
+  bool has_acq = false;
+  int n_src = 0, n_rec = 0, nt = 0, rw = 0, L = 0, lz = 1, ly = 1, lx = 1;
+  int sig_stride = 0;
+  int* src_first = nullptr;
+  float* src_w = nullptr;
+  float* wavelet = nullptr;
+  int* rec_first = nullptr;
+  float* rec_w = nullptr;
+
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  double stencil_ms = 0.0;
+  int64_t stencil_launches = 0, kernel_launches = 0;
+  int64_t device_bytes = 0;
+
+  FaceInfo faces() const {
+    FaceInfo f;
+    f.sz = lay.sz;
+    f.sy = lay.sy;
+    f.nz = int(n[0]);
+    f.ny = int(n[1]);
+    f.nx = int(n[2]);
+    for (int i = 0; i < 6; ++i) {
+      f.nbl[i] = nbl[i];
+      f.bc[i] = bc[i];
+    }
+    return f;
+  }
+  int64_t nodes() const { return n[0] * n[1] * n[2]; }
+  float* at0(float* base) const { return base + lay.origin; }
+};
+
+namespace {
+
+sw_status dev_alloc(sw_grid* g, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(SW_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  g->device_bytes += int64_t(bytes);
+  return SW_OK;
+}
+
+void dev_free(sw_grid* g, void* p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    g->device_bytes -= int64_t(bytes);
+  }
+}
+
+// Copies a grid-shaped input to the device if it lives on the host; returns the
+// device pointer to read from.
+sw_status device_input(sw_grid* g, const float* src, float** staging, const float** out) {
+  if (is_device_pointer(src)) {
+    *out = src;
+    return SW_OK;
+  }
+  const size_t bytes = size_t(g->nodes()) * sizeof(float);
+  if (!*staging) SW_TRY(dev_alloc(g, (void**)staging, bytes));
+  SW_CUDA(cudaMemcpyAsync(*staging, src, bytes, cudaMemcpyHostToDevice, g->stream));
+  *out = *staging;
+  return SW_OK;
+}
+
+// ---- stencil dispatch --------------------------------------------------------
+
+StencilArgs stencil_args(const sw_grid* g) {
+  StencilArgs a;
+  memset(&a, 0, sizeof(a));
+  a.sz = g->lay.sz;
+  a.sy = g->lay.sy;
+  a.nz = int(g->n[0]);
+  a.ny = int(g->n[1]);
+  a.nx = int(g->n[2]);
+  for (int i = 0; i < 6; ++i) {
+    a.nbl[i] = g->nbl[i];
+    a.bc[i] = g->bc[i];
+  }
+  double v[kMaxR + 1], w[kMaxR + 1];
+  fd_second_weights(g->order, v);
+  fd_first_weights(g->order, w);
+  const double hz = g->h[0], hy = g->h[1], hx = g->h[2];
+  double c0 = v[0] / (hz * hz) + v[0] / (hx * hx);
+  if (g->ndim == 3) c0 += v[0] / (hy * hy);
+  a.c0 = float(c0);
+  for (int j = 1; j <= g->R; ++j) {
+    a.cz[j] = float(v[j] / (hz * hz));
+    a.cy[j] = float(v[j] / (hy * hy));
+    a.cx[j] = float(v[j] / (hx * hx));
+    a.gz[j] = float(w[j] / (2.0 * hz));
+    a.gy[j] = float(w[j] / (2.0 * hy));
+    a.gx[j] = float(w[j] / (2.0 * hx));
+  }
+  a.damp = g->damp;
+  a.kappa = g->at0(g->kappa);
+  a.lnrho = g->has_density ? g->at0(g->lnrho) : nullptr;
+  return a;
+}
+
+template <int R, int NDIM, bool VD>
+void launch_stencil_t(StencilArgs a, cudaStream_t st) {
+  if constexpr (NDIM == 3) {
+    constexpr int TX = 32, TY = 16;
+    constexpr int PPT = (VD || R > 5) ? 2 : 4;
+    const int tiles_x = (a.nx + TX - 1) / TX, tiles_y = (a.ny + TY - 1) / TY;
+    const int target = 148 * 4;
+    int chunks = (target + tiles_x * tiles_y - 1) / (tiles_x * tiles_y);
+    int zc = (a.nz + chunks - 1) / chunks;
+    if (zc < 4 * R) zc = 4 * R;
+    a.zchunk = zc;
+    dim3 grid(tiles_x, tiles_y, (a.nz + zc - 1) / zc);
+    stencil_plain_kernel<R, 3, VD, TX, TY, PPT><<<grid, TX * (TY / PPT), 0, st>>>(a);
+  } else {
+    constexpr int TX = 128;
+    const int tiles_x = (a.nx + TX - 1) / TX;
+    const int target = 148 * 4;
+    int chunks = (target + tiles_x - 1) / tiles_x;
+    int zc = (a.nz + chunks - 1) / chunks;
+    if (zc < 4 * R) zc = 4 * R;
+    a.zchunk = zc;
+    dim3 grid(tiles_x, 1, (a.nz + zc - 1) / zc);
+    stencil_plain_kernel<R, 2, VD, TX, 1, 1><<<grid, TX, 0, st>>>(a);
+  }
+}
+
+template <int R>
+void launch_stencil_r(int ndim, bool vd, const StencilArgs& a, cudaStream_t st) {
+  if (ndim == 3) {
+    if (vd)
+      launch_stencil_t<R, 3, true>(a, st);
+    else
+      launch_stencil_t<R, 3, false>(a, st);
+  } else {
+    if (vd)
+      launch_stencil_t<R, 2, true>(a, st);
+    else
+      launch_stencil_t<R, 2, false>(a, st);
+  }
+}
+
+void launch_stencil(int R, int ndim, bool vd, const StencilArgs& a, cudaStream_t st) {
+  switch (R) {
+    case 1: launch_stencil_r<1>(ndim, vd, a, st); break;
+    case 2: launch_stencil_r<2>(ndim, vd, a, st); break;
+    case 3: launch_stencil_r<3>(ndim, vd, a, st); break;
+    case 4: launch_stencil_r<4>(ndim, vd, a, st); break;
+    case 5: launch_stencil_r<5>(ndim, vd, a, st); break;
+    case 6: launch_stencil_r<6>(ndim, vd, a, st); break;
+    case 7: launch_stencil_r<7>(ndim, vd, a, st); break;
+    case 8: launch_stencil_r<8>(ndim, vd, a, st); break;
+    case 9: launch_stencil_r<9>(ndim, vd, a, st); break;
+    case 10: launch_stencil_r<10>(ndim, vd, a, st); break;
+    default: break;
+  }
+}
+
+PointSet point_set(const sw_grid* g, bool src) {
+  PointSet p;
+  p.first = src ? g->src_first : g->rec_first;
+  p.w = src ? g->src_w : g->rec_w;
+  p.count = src ? g->n_src : g->n_rec;
+  p.L = g->L;
+  p.lz = g->lz;
+  p.ly = g->ly;
+  p.lx = g->lx;
+  return p;
+}
+
+void free_acquisition(sw_grid* g) {
+  dev_free(g, g->src_first, size_t(g->n_src) * 3 * sizeof(int));
+  dev_free(g, g->src_w, size_t(g->n_src) * 3 * g->L * sizeof(float));
+  dev_free(g, g->rec_first, size_t(g->n_rec) * 3 * sizeof(int));
+  dev_free(g, g->rec_w, size_t(g->n_rec) * 3 * g->L * sizeof(float));
+  dev_free(g, g->wavelet, size_t(g->n_src > 0 ? g->n_src : 1) * g->nt * sizeof(float));
+  g->src_first = g->rec_first = nullptr;
+  g->src_w = g->rec_w = g->wavelet = nullptr;
+  g->has_acq = false;
+}
+
+// Window weights of a set of points: per point and axis the first node and the
+// 2 r_w Kaiser-sinc weights (a single unit weight along the absent 2D y axis).
+sw_status build_windows(const sw_grid* g, int count, const double* pos, bool fold_cell,
+                        std::vector<int>& first, std::vector<float>& w) {
+  const int rw = g->rw, L = g->L;
+  first.assign(size_t(count) * 3, 0);
+  w.assign(size_t(count) * 3 * L, 0.f);
+  double cell = 1.0;
+  for (int a = 0; a < g->ndim; ++a) cell *= (g->ndim == 3 ? g->h[a] : (a == 0 ? g->h[0] : g->h[2]));
+  for (int i = 0; i < count; ++i) {
+    for (int a = 0; a < g->ndim; ++a) {
+      const int axis = (g->ndim == 3) ? a : (a == 0 ? 0 : 2);
+      const double coord = pos[size_t(i) * g->ndim + a];
+      if (!std::isfinite(coord)) return fail(SW_EINVAL, "position %d is not finite", i);
+      const double s = double(g->nbl[2 * axis]) + coord / g->h[axis];
+      int64_t f0;
+      double ww[2 * kMaxR], wf[2 * kMaxR];
+      kaiser_sinc_weights(s, rw, &f0, ww);
+      // A window that sticks out of the grid only with exactly-zero weights (an
+      // on-grid coordinate near a face) is moved inside; nonzero weights keep
+      // their nodes.
+      const int64_t nax = g->n[axis];
+      if (2 * rw > nax) return fail(SW_EINVAL, "window longer than axis %d", axis);
+      const int64_t nf = std::min(std::max<int64_t>(f0, 0), nax - 2 * rw);
+      for (int j = 0; j < 2 * rw; ++j) wf[j] = 0.0;
+      for (int j = 0; j < 2 * rw; ++j) {
+        const int64_t node = f0 + j;
+        if (node >= nf && node < nf + 2 * rw)
+          wf[node - nf] = ww[j];
+        else if (ww[j] != 0.0)
+          return fail(SW_EINVAL, "window of point %d leaves the grid along axis %d", i, axis);
+      }
+      first[size_t(i) * 3 + axis] = int(nf);
+      for (int j = 0; j < 2 * rw; ++j) {
+        double v = wf[j];
+        if (fold_cell && axis == 2) v /= cell;
+        w[(size_t(i) * 3 + axis) * L + j] = float(v);
+      }
+    }
+    if (g->ndim == 2) {
+      first[size_t(i) * 3 + 1] = 0;
+      w[(size_t(i) * 3 + 1) * L] = 1.f;
+    }
+  }
+  return SW_OK;
+}
+
+sw_status check_device_flag(sw_grid* g) {
+  int flag = 0;
+  SW_CUDA(cudaMemcpyAsync(&flag, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  if (flag != 0) {
+    SW_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+    return fail(SW_ETIMEOUT, "a kernel's bounded wait gave up (device flag 0x%x)", flag);
+  }
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sw_last_error(void) { return g_last_error.c_str(); }
+
+sw_status sw_create_grid(sw_grid** out, int ndim, const int64_t* shape, const double* spacing,
+                         int space_order, const int* nbl, const int* bc, double damp_alpha,
+                         int damp_degree, double dt, void* cuda_stream) {
+  g_last_error.clear();
+  if (!out || !shape || !spacing || !nbl || !bc) return fail(SW_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return fail(SW_EINVAL, "ndim must be 2 or 3 (got %d)", ndim);
+  if (space_order < 2 || space_order > 2 * kMaxR || space_order % 2)
+    return fail(SW_EINVAL, "space_order must be even in [2, 20] (got %d)", space_order);
+  if (!(damp_alpha >= 0.0) || !std::isfinite(damp_alpha) || damp_degree < 0 || damp_degree > 16)
+    return fail(SW_EINVAL, "damping parameters out of range");
+  if (!std::isfinite(dt)) return fail(SW_EINVAL, "dt is not finite");
+  const int R = space_order / 2;
+  sw_grid* g = new sw_grid();
+  g->ndim = ndim;
+  g->order = space_order;
+  g->R = R;
+  for (int a = 0; a < ndim; ++a) {
+    const int axis = (ndim == 3) ? a : (a == 0 ? 0 : 2);
+    if (shape[a] < R + 1 || shape[a] > (int64_t(1) << 24)) {
+      delete g;
+      return fail(SW_EINVAL, "shape[%d] = %lld out of range (needs r+1 .. 2^24)", a, (long long)shape[a]);
+    }
+    if (!(spacing[a] > 0.0) || !std::isfinite(spacing[a])) {
+      delete g;
+      return fail(SW_EINVAL, "spacing[%d] must be positive", a);
+    }
+    g->n[axis] = shape[a];
+    g->h[axis] = spacing[a];
+    for (int s = 0; s < 2; ++s) {
+      const int nb = nbl[2 * a + s], b = bc[2 * a + s];
+      if (nb < 0 || nb >= shape[a]) {
+        delete g;
+        return fail(SW_EINVAL, "nbl[%d] out of range", 2 * a + s);
+      }
+      if (b != SW_BC_NONE && b != SW_BC_DIRICHLET && b != SW_BC_NEUMANN) {
+        delete g;
+        return fail(SW_EINVAL, "bc[%d] invalid", 2 * a + s);
+      }
+      g->nbl[2 * axis + s] = nb;
+      g->bc[2 * axis + s] = b;
+    }
+    if (nbl[2 * a] + nbl[2 * a + 1] >= shape[a]) {
+      delete g;
+      return fail(SW_EINVAL, "absorbing layers cover the whole axis %d", a);
+    }
+  }
+  const int64_t total_nodes = g->n[0] * g->n[1] * g->n[2];
+  if (total_nodes > (int64_t(1) << 34)) {
+    delete g;
+    return fail(SW_EINVAL, "grid too large");
+  }
+  g->alpha = damp_alpha;
+  g->degree = damp_degree;
+  g->dt_user = dt;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&g->device);
+  g->lay.init(ndim, R, g->n);
+
+  sw_status st = SW_OK;
+  const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+  for (int i = 0; i < 2 && st == SW_OK; ++i) st = dev_alloc(g, (void**)&g->u[i], fbytes);
+  if (st == SW_OK) st = dev_alloc(g, (void**)&g->kappa, fbytes);
+  if (st == SW_OK) st = dev_alloc(g, (void**)&g->dflag, 64);
+  if (st == SW_OK) st = dev_alloc(g, (void**)&g->dscratch, 64);
+  if (st == SW_OK) {
+    int64_t maxd2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int64_t m = std::max(g->nbl[2 * a], g->nbl[2 * a + 1]);
+      maxd2 += m * m;
+    }
+    g->damp_len = maxd2 + 1;
+    st = dev_alloc(g, (void**)&g->damp, size_t(g->damp_len) * sizeof(float2));
+  }
+  if (st == SW_OK) {
+    cudaError_t e = cudaMemsetAsync(g->kappa, 0, fbytes, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->dflag, 0, 64, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) st = fail(SW_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+  }
+  if (st != SW_OK) {
+    std::string msg = g_last_error;
+    sw_destroy_grid(g);
+    g_last_error = msg;
+    return st;
+  }
+  *out = g;
+  return SW_OK;
+}
+
+sw_status sw_set_model(sw_grid* g, const float* velocity, const float* density) {
+  g_last_error.clear();
+  if (!g || !velocity) return fail(SW_EINVAL, "NULL argument");
+  const FaceInfo f = g->faces();
+  const int64_t nn = g->nodes();
+  const float* vdev = nullptr;
+  SW_TRY(device_input(g, velocity, &g->staging, &vdev));
+  // velocity range
+  unsigned init[2] = {0u, 0x7f800000u};
+  SW_CUDA(cudaMemcpyAsync(g->dscratch, init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
+  SW_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+  field_range_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(vdev, nn, g->dscratch, g->dscratch + 1,
+                                                                  g->dflag);
+  SW_CUDA(cudaGetLastError());
+  unsigned res[2];
+  int bad = 0;
+  SW_CUDA(cudaMemcpyAsync(res, g->dscratch, sizeof(res), cudaMemcpyDeviceToHost, g->stream));
+  SW_CUDA(cudaMemcpyAsync(&bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  if (bad) {
+    SW_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+    return fail(SW_EINVAL, "velocity must be finite and positive everywhere");
+  }
+  float vmax;
+  memcpy(&vmax, &res[0], sizeof(float));
+  const double hh[3] = {g->h[0], g->ndim == 3 ? g->h[1] : g->h[2], g->h[2]};
+  const double dtc = critical_dt(g->ndim, g->order, hh, double(vmax));
+  double dt = g->dt_user;
+  if (dt <= 0.0) {
+    dt = dtc;
+  } else if (dt > dtc) {
+    return fail(SW_ECFL, "dt = %.6g s exceeds the stability bound %.6g s (c_max = %.6g m/s)", dt, dtc,
+                double(vmax));
+  }
+  g->dt = dt;
+  g->dt_ready = true;
+  g->c_max = vmax;
+
+  kappa_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(vdev, g->at0(g->kappa), f, dt);
+  SW_CUDA(cudaGetLastError());
+
+  // damping coefficients by squared distance
+  std::vector<float2> table(size_t(g->damp_len));
+  for (int64_t d2 = 0; d2 < g->damp_len; ++d2) {
+    double a, b;
+    damping_coefficients(g->alpha, g->degree, dt, d2, &a, &b);
+    table[size_t(d2)] = make_float2(float(a), float(b));
+  }
+  SW_CUDA(cudaMemcpyAsync(g->damp, table.data(), table.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                          g->stream));
+
+  if (density) {
+    const float* rdev = nullptr;
+    SW_TRY(device_input(g, density, &g->staging2, &rdev));
+    SW_CUDA(cudaMemcpyAsync(g->dscratch, init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
+    field_range_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(rdev, nn, g->dscratch, g->dscratch + 1,
+                                                                    g->dflag);
+    SW_CUDA(cudaGetLastError());
+    SW_CUDA(cudaMemcpyAsync(&bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    SW_CUDA(cudaStreamSynchronize(g->stream));
+    if (bad) {
+      SW_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+      return fail(SW_EINVAL, "density must be finite and positive everywhere");
+    }
+    const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+    if (!g->lnrho) {
+      SW_TRY(dev_alloc(g, (void**)&g->lnrho, fbytes));
+      SW_CUDA(cudaMemsetAsync(g->lnrho, 0, fbytes, g->stream));
+    }
+    lnrho_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(rdev, g->at0(g->lnrho), f);
+    SW_CUDA(cudaGetLastError());
+    for (int axis = 0; axis < 3; ++axis) {
+      if (g->ndim == 2 && axis == 1) continue;
+      mirror_even_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(g->at0(g->lnrho), f, axis, g->R);
+      SW_CUDA(cudaGetLastError());
+    }
+    g->has_density = true;
+  } else {
+    g->has_density = false;
+  }
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  g->has_model = true;
+  return SW_OK;
+}
+
+sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n_rec, const double* rec_pos,
+                             int nt, const float* wavelet, int wavelet_per_source, int window_radius) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (n_src < 0 || n_rec < 0 || nt < 0) return fail(SW_EINVAL, "negative count");
+  if ((n_src > 0 && (!src_pos || !wavelet || nt == 0)) || (n_rec > 0 && !rec_pos))
+    return fail(SW_EINVAL, "NULL positions or wavelet");
+  if (window_radius < 1 || window_radius > kMaxR) return fail(SW_EINVAL, "window_radius must be in [1, 10]");
+  free_acquisition(g);
+  g->rw = window_radius;
+  g->L = 2 * window_radius;
+  g->lz = g->L;
+  g->ly = (g->ndim == 3) ? g->L : 1;
+  g->lx = g->L;
+  std::vector<int> sf, rf;
+  std::vector<float> swt, rwt;
+  SW_TRY(build_windows(g, n_src, src_pos, true, sf, swt));
+  SW_TRY(build_windows(g, n_rec, rec_pos, false, rf, rwt));
+  g->n_src = n_src;
+  g->n_rec = n_rec;
+  g->nt = nt;
+  g->sig_stride = wavelet_per_source ? nt : 0;
+  if (n_src > 0) {
+    SW_TRY(dev_alloc(g, (void**)&g->src_first, sf.size() * sizeof(int)));
+    SW_TRY(dev_alloc(g, (void**)&g->src_w, swt.size() * sizeof(float)));
+    SW_CUDA(cudaMemcpyAsync(g->src_first, sf.data(), sf.size() * sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    SW_CUDA(cudaMemcpyAsync(g->src_w, swt.data(), swt.size() * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    const size_t wl = size_t(wavelet_per_source ? n_src : 1) * nt;
+    SW_TRY(dev_alloc(g, (void**)&g->wavelet, size_t(n_src) * nt * sizeof(float)));
+    SW_CUDA(cudaMemcpyAsync(g->wavelet, wavelet, wl * sizeof(float), cudaMemcpyDefault, g->stream));
+  }
+  if (n_rec > 0) {
+    SW_TRY(dev_alloc(g, (void**)&g->rec_first, rf.size() * sizeof(int)));
+    SW_TRY(dev_alloc(g, (void**)&g->rec_w, rwt.size() * sizeof(float)));
+    SW_CUDA(cudaMemcpyAsync(g->rec_first, rf.data(), rf.size() * sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    SW_CUDA(cudaMemcpyAsync(g->rec_w, rwt.data(), rwt.size() * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+  }
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  g->has_acq = true;
+  return SW_OK;
+}
+
+sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_field) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (!g->has_model) return fail(SW_ESTATE, "sw_forward before sw_set_model");
+  if (!g->has_acq) return fail(SW_ESTATE, "sw_forward before sw_set_acquisition");
+  if (n_steps < 0) return fail(SW_EINVAL, "n_steps < 0");
+  if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
+  if (g->n_rec > 0 && n_steps > 0 && !seismogram) return fail(SW_EINVAL, "seismogram is NULL");
+
+  const FaceInfo f = g->faces();
+  const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+  SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, g->stream));
+  SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, g->stream));
+
+  float* seis_dev = nullptr;
+  const bool seis_host = seismogram && !is_device_pointer(seismogram);
+  const int64_t seis_elems = int64_t(n_steps) * g->n_rec;
+  if (g->n_rec > 0 && n_steps > 0) {
+    if (seis_host) {
+      if (g->seis_staging_elems < seis_elems) {
+        dev_free(g, g->seis_staging, size_t(g->seis_staging_elems) * sizeof(float));
+        g->seis_staging = nullptr;
+        g->seis_staging_elems = 0;
+        SW_TRY(dev_alloc(g, (void**)&g->seis_staging, size_t(seis_elems) * sizeof(float)));
+        g->seis_staging_elems = seis_elems;
+      }
+      seis_dev = g->seis_staging;
+    } else {
+      seis_dev = seismogram;
+    }
+  }
+
+  StencilArgs a = stencil_args(g);
+  const PointSet src = point_set(g, true), rec = point_set(g, false);
+  if (g->profiling && g->events.size() < size_t(2 * n_steps)) {
+    size_t old = g->events.size();
+    g->events.resize(size_t(2 * n_steps));
+    for (size_t i = old; i < g->events.size(); ++i) SW_CUDA(cudaEventCreate(&g->events[i]));
+  }
+  int64_t launches = 0;
+  const int src_threads = g->n_src * g->lz * g->ly * g->lx;
+  for (int step = 0; step < n_steps; ++step) {
+    float* pn = g->u[step & 1];
+    float* pnm1 = g->u[(step + 1) & 1];
+    a.pn = g->at0(pn);
+    a.pnm1 = g->at0(pnm1);
+    if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step], g->stream));
+    launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
+    if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step + 1], g->stream));
+    ++launches;
+    if (src_threads > 0) {
+      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(
+          a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
+      ++launches;
+    }
+    if (g->n_rec > 0) {
+      sample_receivers_kernel<<<(g->n_rec * 32 + 255) / 256, 256, 0, g->stream>>>(a.pnm1, rec, f, seis_dev,
+                                                                                  step);
+      ++launches;
+    }
+  }
+  SW_CUDA(cudaGetLastError());
+  if (final_field) {
+    float* last = g->at0(g->u[n_steps & 1]);
+    const bool fh = !is_device_pointer(final_field);
+    float* dst = final_field;
+    if (fh) {
+      if (!g->staging) SW_TRY(dev_alloc(g, (void**)&g->staging, size_t(g->nodes()) * sizeof(float)));
+      dst = g->staging;
+    }
+    extract_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, g->stream>>>(last, dst, f);
+    SW_CUDA(cudaGetLastError());
+    ++launches;
+    if (fh)
+      SW_CUDA(cudaMemcpyAsync(final_field, dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost,
+                              g->stream));
+  }
+  if (seis_host && seis_elems > 0)
+    SW_CUDA(cudaMemcpyAsync(seismogram, seis_dev, size_t(seis_elems) * sizeof(float), cudaMemcpyDeviceToHost,
+                            g->stream));
+  SW_TRY(check_device_flag(g));
+  g->kernel_launches = launches;
+  g->stencil_launches = n_steps;
+  g->stencil_ms = 0.0;
+  if (g->profiling) {
+    for (int step = 0; step < n_steps; ++step) {
+      float ms = 0.f;
+      SW_CUDA(cudaEventElapsedTime(&ms, g->events[2 * step], g->events[2 * step + 1]));
+      g->stencil_ms += ms;
+    }
+  }
+  return SW_OK;
+}
+
+sw_status sw_get_dt(const sw_grid* g, double* dt) {
+  if (!g || !dt) return fail(SW_EINVAL, "NULL argument");
+  if (!g->dt_ready) {
+    if (g->dt_user > 0.0) {
+      *dt = g->dt_user;
+      return SW_OK;
+    }
+    return fail(SW_ESTATE, "automatic dt is resolved by sw_set_model");
+  }
+  *dt = g->dt;
+  return SW_OK;
+}
+
+sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out) {
+  if (!out || nt < 0 || !(f_peak > 0.0) || !(dt > 0.0)) return fail(SW_EINVAL, "bad Ricker arguments");
+  ricker(f_peak, t0, dt, nt, out);
+  return SW_OK;
+}
+
+sw_status sw_set_profiling(sw_grid* g, int enable) {
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  g->profiling = enable != 0;
+  return SW_OK;
+}
+
+sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_launches,
+                         int64_t* kernel_launches) {
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (stencil_ms) *stencil_ms = g->stencil_ms;
+  if (stencil_launches) *stencil_launches = g->stencil_launches;
+  if (kernel_launches) *kernel_launches = g->kernel_launches;
+  return SW_OK;
+}
+
+sw_status sw_get_device_bytes(const sw_grid* g, int64_t* bytes) {
+  if (!g || !bytes) return fail(SW_EINVAL, "NULL argument");
+  *bytes = g->device_bytes;
+  return SW_OK;
+}
+
+void sw_destroy_grid(sw_grid* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  free_acquisition(g);
+  const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+  dev_free(g, g->u[0], fbytes);
+  dev_free(g, g->u[1], fbytes);
+  dev_free(g, g->kappa, fbytes);
+  dev_free(g, g->lnrho, fbytes);
+  dev_free(g, g->damp, size_t(g->damp_len) * sizeof(float2));
+  dev_free(g, g->dflag, 64);
+  dev_free(g, g->dscratch, 64);
+  dev_free(g, g->staging, size_t(g->nodes()) * sizeof(float));
+  dev_free(g, g->staging2, size_t(g->nodes()) * sizeof(float));
+  dev_free(g, g->seis_staging, size_t(g->seis_staging_elems) * sizeof(float));
+  for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Leapfrog stencil step, shared-memory plane + register z-queue version.
+//
+// One CTA owns a TX x TY column of the grid (TX x 1 in 2D) and marches along z
+// over a chunk of planes.  Each thread keeps the 2R+1 values of p[n] it needs
+// along z in registers (a queue shifted once per plane) and takes the in-plane
+// neighbours from a shared-memory copy of the current plane with an R-wide
+// halo.  p[n-1] and kappa are read once per node; p[n+1] overwrites p[n-1].
+//
+// Per node (Sec. 2.2, Eq. 7 with every term divided by 1 + eta dt):
+//   p[n+1] = a (kappa L p[n] + 2 p[n]) - b p[n-1],  a = 1/(1+e), b = (1-e)/(1+e)
+//   L = sum_axes h^-2 (v0 p + sum_j v_j (p+j + p-j))               (Eq. 9)
+//       - sum_axes D(ln rho) D(p),  D = (2h)^-1 sum_j w_j (.+j - .-j) (Eq. 10)
+// e = alpha d^p dt from a table indexed by the squared cell distance to the
+// physical domain (Eq. 4).  Face conditions are kept in ghost nodes: the
+// thread that writes a node within R of a mirrored face also writes its
+// mirror image into the ghost layer of p[n+1]; Dirichlet face nodes are 0.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "layout.h"
+
+namespace sw {
+
+struct StencilArgs {
+  const float* pn;      // p[n] at node (0,0,0) of the padded layout
+  float* pnm1;          // p[n-1] in, p[n+1] out
+  const float* kappa;   // (c dt)^2
+  const float* lnrho;   // ln(rho) with mirrored ghosts, or nullptr
+  const float2* damp;   // (a, b) indexed by squared distance (cells^2)
+  int64_t sz, sy;
+  int nz, ny, nx;
+  int nbl[6];
+  int bc[6];
+  int zchunk;
+  float c0;                                          // sum_axes v0 / h^2
+  float cz[kMaxR + 1], cy[kMaxR + 1], cx[kMaxR + 1];  // v_j / h^2
+  float gz[kMaxR + 1], gy[kMaxR + 1], gx[kMaxR + 1];  // w_j / (2h)
+};
+
+__device__ __forceinline__ int layer_distance(int i, int n, int lo, int hi) {
+  return max(max(lo - i, i - (n - 1 - hi)), 0);
+}
+
+// Writes the face-mirror images of a freshly computed node value into the
+// ghost layers of p[n+1] along one axis.  `i` is the node index along the
+// axis, `n` its length, `stride` the axis stride.
+template <int R>
+__device__ __forceinline__ void mirror_ghosts(float* p, int64_t idx, int i, int n, int64_t stride,
+                                              int bc_lo, int bc_hi, float v) {
+  if (bc_lo != kBcNone && i >= 1 && i <= R)
+    p[idx - int64_t(2 * i) * stride] = (bc_lo == kBcDirichlet) ? -v : v;
+  const int m = n - 1 - i;  // distance to the high face node
+  if (bc_hi != kBcNone && m >= 1 && m <= R)
+    p[idx + int64_t(2 * m) * stride] = (bc_hi == kBcDirichlet) ? -v : v;
+}
+
+template <int R, int NDIM, bool VD, int TX, int TY, int PPT>
+__global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const StencilArgs a) {
+  constexpr int NT = TX * (TY / PPT);
+  constexpr int SW = TX + 2 * R;
+  constexpr int SH = (NDIM == 3) ? TY + 2 * R : 1;
+  __shared__ float sp[SH][SW];
+  __shared__ float sl[VD ? SH : 1][VD ? SW : 1];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX;
+  const int ty = tid / TX;
+  const int x0 = blockIdx.x * TX;
+  const int y0 = (NDIM == 3) ? blockIdx.y * TY : 0;
+  const int zb = blockIdx.z * a.zchunk;
+  const int ze = min(zb + a.zchunk, a.nz);
+  const int x = x0 + tx;
+  const int64_t sz = a.sz, sy = a.sy;
+
+  int yrow[PPT];
+  int64_t col[PPT];  // offset of (0, y, x) for each of the thread's rows
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    yrow[i] = (NDIM == 3) ? y0 + ty * PPT + i : 0;
+    col[i] = int64_t(yrow[i]) * sy + x;
+  }
+
+  float q[PPT][2 * R + 1];
+  float ql[VD ? PPT : 1][VD ? 2 * R + 1 : 1];
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) {
+    const int64_t zoff = int64_t(zb - R + k) * sz;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      q[i][k + 1] = a.pn[zoff + col[i]];
+      if constexpr (VD) ql[i][k + 1] = a.lnrho[zoff + col[i]];
+    }
+  }
+
+  for (int z = zb; z < ze; ++z) {
+    const int64_t zoff = int64_t(z) * sz;
+    const int64_t zf = int64_t(z + R) * sz;
+    float po[PPT], kp[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+#pragma unroll
+      for (int k = 0; k < 2 * R; ++k) q[i][k] = q[i][k + 1];
+      q[i][2 * R] = a.pn[zf + col[i]];
+      if constexpr (VD) {
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) ql[i][k] = ql[i][k + 1];
+        ql[i][2 * R] = a.lnrho[zf + col[i]];
+      }
+      po[i] = a.pnm1[zoff + col[i]];
+      kp[i] = a.kappa[zoff + col[i]];
+    }
+
+    __syncthreads();  // the previous plane's readers are done with sp / sl
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int row = (NDIM == 3) ? ty * PPT + i + R : 0;
+      sp[row][tx + R] = q[i][R];
+      if constexpr (VD) sl[row][tx + R] = ql[i][R];
+    }
+    // x halo: R columns on each side of every row of the tile
+    for (int e = tid; e < (NDIM == 3 ? TY : 1) * 2 * R; e += NT) {
+      const int r = e / (2 * R);
+      const int c = e % (2 * R);
+      const int scol = (c < R) ? c : TX + c;
+      const int gxx = x0 - R + scol;
+      const int64_t off = zoff + int64_t((NDIM == 3) ? y0 + r : 0) * sy + gxx;
+      const int srow = (NDIM == 3) ? r + R : 0;
+      sp[srow][scol] = a.pn[off];
+      if constexpr (VD) sl[srow][scol] = a.lnrho[off];
+    }
+    if constexpr (NDIM == 3) {
+      // y halo: R rows above and below, TX columns
+      for (int e = tid; e < 2 * R * TX; e += NT) {
+        const int r = e / TX;
+        const int c = e % TX;
+        const int srow = (r < R) ? r : TY + r;
+        const int gyy = y0 - R + srow;
+        const int64_t off = zoff + int64_t(gyy) * sy + x0 + c;
+        sp[srow][c + R] = a.pn[off];
+        if constexpr (VD) sl[srow][c + R] = a.lnrho[off];
+      }
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int row = (NDIM == 3) ? ty * PPT + i + R : 0;
+      const float pc = q[i][R];
+      float lap = a.c0 * pc;
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        lap = fmaf(a.cz[j], q[i][R + j] + q[i][R - j], lap);
+        lap = fmaf(a.cx[j], sp[row][tx + R + j] + sp[row][tx + R - j], lap);
+        if constexpr (NDIM == 3) lap = fmaf(a.cy[j], sp[row + j][tx + R] + sp[row - j][tx + R], lap);
+      }
+      if constexpr (VD) {
+        float dpz = 0.f, dlz = 0.f, dpx = 0.f, dlx = 0.f, dpy = 0.f, dly = 0.f;
+#pragma unroll
+        for (int j = 1; j <= R; ++j) {
+          dpz = fmaf(a.gz[j], q[i][R + j] - q[i][R - j], dpz);
+          dlz = fmaf(a.gz[j], ql[i][R + j] - ql[i][R - j], dlz);
+          dpx = fmaf(a.gx[j], sp[row][tx + R + j] - sp[row][tx + R - j], dpx);
+          dlx = fmaf(a.gx[j], sl[row][tx + R + j] - sl[row][tx + R - j], dlx);
+          if constexpr (NDIM == 3) {
+            dpy = fmaf(a.gy[j], sp[row + j][tx + R] - sp[row - j][tx + R], dpy);
+            dly = fmaf(a.gy[j], sl[row + j][tx + R] - sl[row - j][tx + R], dly);
+          }
+        }
+        float adv = dlz * dpz + dlx * dpx;
+        if constexpr (NDIM == 3) adv = fmaf(dly, dpy, adv);
+        lap -= adv;
+      }
+      const int y = yrow[i];
+      if (x < a.nx && y < a.ny) {
+        const int dz = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+        const int dy = (NDIM == 3) ? layer_distance(y, a.ny, a.nbl[2], a.nbl[3]) : 0;
+        const int dx = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
+        const int d2 = dz * dz + dy * dy + dx * dx;
+        float ca = 1.f, cb = 1.f;
+        if (d2 != 0) {
+          const float2 c = __ldg(&a.damp[d2]);
+          ca = c.x;
+          cb = c.y;
+        }
+        float pnew = ca * fmaf(kp[i], lap, 2.f * pc) - cb * po[i];
+        const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
+                         (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet) ||
+                         (NDIM == 3 && ((y == 0 && a.bc[2] == kBcDirichlet) ||
+                                        (y == a.ny - 1 && a.bc[3] == kBcDirichlet)));
+        if (dir) pnew = 0.f;
+        const int64_t idx = zoff + col[i];
+        a.pnm1[idx] = pnew;
+        mirror_ghosts<R>(a.pnm1, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
+        mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
+        if constexpr (NDIM == 3) mirror_ghosts<R>(a.pnm1, idx, y, a.ny, sy, a.bc[2], a.bc[3], pnew);
+      }
+    }
+  }
+}
+
+}  // namespace sw

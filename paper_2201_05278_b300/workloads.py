@@ -1,0 +1,176 @@
+"""Seeded synthetic workloads (inputs only).
+
+This module generates the inputs that both the CUDA library and the CPU
+oracle consume: grid shapes, spacings, boundary set-up, velocity/density
+models, time step, source/receiver positions and the wavelet's parameters.
+It holds none of the solver's arithmetic (no FD weights, stability bound,
+damping profile or window weights) and imports neither the library nor the
+oracle.
+
+The paper's benchmark models (Marmousi2, Overthrust; Sec. 4-5) are not
+available, so synthetic layered models of the same kind stand in for them:
+
+  2d_homogeneous_256   256 x 256, h = 10 m, v = 1500 m/s, order 8, 1000 steps,
+                       10 Hz Ricker at the grid centre, 20-cell layer on the
+                       bottom/left/right faces, 64 receivers at 20 m depth
+  3d_layered_256       256^3, h = 10 m, order 8, 8 flat layers 1500-4500 m/s
+                       times (1 + 0.05 G), G Gaussian-smoothed white noise
+                       (sigma 3 cells, seed 2201, unit std), 2000 steps, 15 Hz
+                       Ricker 5 cells deep, 40-cell layer on five faces,
+                       64 x 64 receivers 2 cells deep
+  3d_vd_512x512x384    (384, 512, 512), h = 12.5 m, order 16, the layered
+                       model plus two dipping interfaces (+500 m/s each),
+                       Gardner density rho = 310 v^0.25, 3000 steps, 10 Hz,
+                       50-cell layer, 128 x 128 receivers at the surface
+
+Every model has no absorbing layer on the top face, which is null Neumann
+(as in the paper's listings); the other faces are null Dirichlet behind the
+layer.  dt = 0.4 h / c_max (Courant number 0.4).  The damping alpha follows a
+standard estimate for a p = 3 profile with 1e-3 reflection:
+eta_max = (p + 1) c_max ln(1000) / (2 L), alpha = eta_max / nbl^p, L the layer
+width in metres.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    ndim: int
+    shape: Tuple[int, ...]
+    spacing: Tuple[float, ...]
+    order: int
+    nbl: List[int]
+    bc: List[str]
+    damp_alpha: float
+    damp_degree: int
+    dt: float
+    n_steps: int
+    f_peak: float
+    t0: float
+    src_pos: np.ndarray
+    rec_pos: np.ndarray
+    window_radius: int
+    velocity: np.ndarray
+    density: Optional[np.ndarray] = None
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return int(np.prod(self.shape))
+
+    @property
+    def updates(self) -> int:
+        """Grid-point updates of one forward run (all nodes, absorbing layer included)."""
+        return self.nodes * self.n_steps
+
+
+def _alpha(c_max: float, nbl: int, h: float, p: int = 3, refl: float = 1e-3) -> float:
+    if nbl == 0:
+        return 0.0
+    eta_max = (p + 1) * c_max * math.log(1.0 / refl) / (2.0 * nbl * h)
+    return eta_max / nbl ** p
+
+
+def _smooth_noise(shape, sigma, seed):
+    from scipy.ndimage import gaussian_filter
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(shape).astype(np.float32)
+    g = gaussian_filter(g, sigma=sigma, mode="reflect")
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def layered_velocity(shape, n_layers=8, vmin=1500.0, vmax=4500.0, noise=0.05, sigma=3.0, seed=2201,
+                     dips=None, spacing=None):
+    """Flat layers (depth index k * nz / n_layers) with a smooth multiplicative perturbation.
+
+    dips: optional list of (dip_degrees, depth_fraction, jump_m_s) planar interfaces
+    dipping along x; below each interface the velocity increases by `jump`.
+    """
+    nz = shape[0]
+    z = np.arange(nz)
+    layer = np.minimum((z * n_layers) // nz, n_layers - 1)
+    v1 = (vmin + layer * (vmax - vmin) / (n_layers - 1)).astype(np.float32)
+    v = np.broadcast_to(v1.reshape((nz,) + (1,) * (len(shape) - 1)), shape).astype(np.float32)
+    if dips:
+        nx = shape[-1]
+        hz, hx = spacing[0], spacing[-1]
+        zz = (np.arange(nz) * hz).reshape((nz,) + (1,) * (len(shape) - 1))
+        xx = (np.arange(nx) * hx).reshape((1,) * (len(shape) - 1) + (nx,))
+        for dip, frac, jump in dips:
+            z_if = frac * nz * hz + math.tan(math.radians(dip)) * (xx - 0.5 * nx * hx)
+            v = v + np.float32(jump) * (zz > z_if).astype(np.float32)
+    if noise:
+        v = v * (1.0 + np.float32(noise) * _smooth_noise(shape, sigma, seed))
+    return np.ascontiguousarray(v, dtype=np.float32)
+
+
+def _grid_positions(lo, hi, n):
+    return np.linspace(lo, hi, n)
+
+
+def make(name: str, n_steps: Optional[int] = None, shape: Optional[Tuple[int, ...]] = None,
+         seed: int = 2201) -> Workload:
+    """Workload by name; n_steps / shape override the defaults (shape keeps the recipe)."""
+    if name == "2d_homogeneous_256":
+        shp = tuple(shape) if shape else (256, 256)
+        h = (10.0, 10.0)
+        nb = 20
+        nbl = [0, nb, nb, nb]
+        vel = np.full(shp, 1500.0, dtype=np.float32)
+        c_max = 1500.0
+        dt = 0.4 * h[0] / c_max
+        f = 10.0
+        phys_x = (shp[1] - 2 * nb - 1) * h[1]
+        src = np.array([[(shp[0] // 2) * h[0], (shp[1] // 2 - nb) * h[1]]])
+        rec = np.stack([np.full(64, 20.0), _grid_positions(0.05 * phys_x, 0.95 * phys_x, 64)], 1)
+        return Workload(name, 2, shp, h, 8, nbl, ["null_neumann", "null_dirichlet", "null_dirichlet",
+                                                   "null_dirichlet"],
+                        _alpha(c_max, nb, h[0]), 3, dt, n_steps or 1000, f, 1.0 / f, src, rec, 4, vel)
+    if name == "3d_layered_256":
+        shp = tuple(shape) if shape else (256, 256, 256)
+        h = (10.0, 10.0, 10.0)
+        nb = min(40, max(4, shp[1] // 6))
+        nbl = [0, nb, nb, nb, nb, nb]
+        vel = layered_velocity(shp, seed=seed)
+        c_max = float(vel.max())
+        dt = 0.4 * h[0] / c_max
+        f = 15.0
+        py = (shp[1] - 2 * nb - 1) * h[1]
+        px = (shp[2] - 2 * nb - 1) * h[2]
+        src = np.array([[5 * h[0], 0.5 * py, 0.5 * px]])
+        ny_r = nx_r = 64 if shp[1] >= 128 else 8
+        yy, xx = np.meshgrid(_grid_positions(0.0, py, ny_r), _grid_positions(0.0, px, nx_r), indexing="ij")
+        rec = np.stack([np.full(yy.size, 2 * h[0]), yy.ravel(), xx.ravel()], 1)
+        return Workload(name, 3, shp, h, 8, nbl, ["null_neumann"] + ["null_dirichlet"] * 5,
+                        _alpha(c_max, nb, h[0]), 3, dt, n_steps or 2000, f, 1.0 / f, src, rec, 4, vel)
+    if name == "3d_vd_512x512x384":
+        shp = tuple(shape) if shape else (384, 512, 512)
+        h = (12.5, 12.5, 12.5)
+        nb = min(50, max(8, shp[1] // 6))
+        nbl = [0, nb, nb, nb, nb, nb]
+        vel = layered_velocity(shp, seed=seed, dips=[(10.0, 0.35, 500.0), (-15.0, 0.65, 500.0)], spacing=h)
+        rho = (310.0 * vel.astype(np.float64) ** 0.25).astype(np.float32)
+        c_max = float(vel.max())
+        dt = 0.4 * h[0] / c_max
+        f = 10.0
+        py = (shp[1] - 2 * nb - 1) * h[1]
+        px = (shp[2] - 2 * nb - 1) * h[2]
+        src = np.array([[5 * h[0], 0.5 * py, 0.5 * px]])
+        ny_r = nx_r = 128 if shp[1] >= 256 else 8
+        yy, xx = np.meshgrid(_grid_positions(0.0, py, ny_r), _grid_positions(0.0, px, nx_r), indexing="ij")
+        rec = np.stack([np.zeros(yy.size), yy.ravel(), xx.ravel()], 1)
+        return Workload(name, 3, shp, h, 16, nbl, ["null_neumann"] + ["null_dirichlet"] * 5,
+                        _alpha(c_max, nb, h[0]), 3, dt, n_steps or 3000, f, 1.0 / f, src, rec, 4, vel, rho)
+    raise KeyError(name)
+
+
+NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384"]

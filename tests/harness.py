@@ -1,0 +1,75 @@
+"""Run one workload through the CUDA library (C ABI) and through the FP64 oracle.
+
+Test-side glue only: the GPU run goes through paper_2201_05278_b300.api (the
+C ABI), the reference run through oracle.forward; both read the same
+workload description from paper_2201_05278_b300.workloads.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle
+from paper_2201_05278_b300 import api
+from paper_2201_05278_b300.workloads import Workload
+
+FP32_SEIS_TOL = 1e-5  # relative L2 on the seismogram, FP32 forward vs FP64 oracle
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+
+def wavelet_of(w: Workload, nt=None):
+    return oracle.ricker_samples(w.f_peak, w.dt, nt or w.n_steps, t0=w.t0)
+
+
+def run_gpu(w: Workload, n_steps=None, device_io=True, wavelet=None, final=True, profile=False):
+    import torch
+    n_steps = w.n_steps if n_steps is None else n_steps
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree,
+                           w.dt)
+    try:
+        vel = torch.from_numpy(np.ascontiguousarray(w.velocity, dtype=np.float32))
+        rho = None if w.density is None else torch.from_numpy(np.ascontiguousarray(w.density, np.float32))
+        if device_io:
+            vel = vel.to(dev)
+            rho = None if rho is None else rho.to(dev)
+        api.sw_set_model(g, vel, rho)
+        if wavelet is None:
+            wavelet = api.sw_ricker(w.f_peak, w.t0, w.dt, max(n_steps, 1))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wavelet, window_radius=w.window_radius)
+        if profile:
+            api.sw_set_profiling(g, True)
+        n_rec = len(w.rec_pos)
+        if device_io:
+            seis = torch.zeros((n_steps, n_rec), dtype=torch.float32, device=dev)
+            fin = torch.zeros(w.shape, dtype=torch.float32, device=dev) if final else None
+        else:
+            seis = np.zeros((n_steps, n_rec), dtype=np.float32)
+            fin = np.zeros(w.shape, dtype=np.float32) if final else None
+        api.sw_forward(g, n_steps, seis if n_rec else None, fin)
+        prof = api.sw_get_profile(g) if profile else None
+        if device_io:
+            seis = seis.cpu().numpy()
+            fin = fin.cpu().numpy() if final else None
+        return (seis, fin, prof) if profile else (seis, fin)
+    finally:
+        g.close()
+
+
+def run_oracle(w: Workload, n_steps=None, wavelet=None, threads=0):
+    n_steps = w.n_steps if n_steps is None else n_steps
+    if wavelet is None:
+        wavelet = wavelet_of(w, max(n_steps, 1))
+    return oracle.forward(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, n_steps,
+                          src_pos=[tuple(p) for p in w.src_pos], wavelet=np.asarray(wavelet, np.float64),
+                          rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc,
+                          damp_alpha=w.damp_alpha, damp_degree=w.damp_degree,
+                          rho=None if w.density is None else w.density.astype(np.float64),
+                          window_radius=w.window_radius, threads=threads or os.cpu_count())

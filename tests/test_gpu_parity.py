@@ -1,0 +1,161 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: relative L2 error of the seismogram and of the final field at most
+1e-5 (FP32 forward vs FP64 oracle).  Small odd-shaped grids cover every
+space order, both dimensions, both density paths, ragged tiles and mixed
+face conditions; the named workloads are checked at full grid size with a
+reduced step count, and full-length runs are checked by properties that
+hold at any size (causality against the oracle's prefix, exact time-shift
+and amplitude-scaling invariance).
+"""
+import numpy as np
+import pytest
+
+from paper_2201_05278_b300 import api, workloads
+from paper_2201_05278_b300.workloads import Workload
+from tests.harness import FP32_SEIS_TOL, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def small_case(ndim, order, density, seed=0, n_steps=60):
+    rng = np.random.default_rng(seed)
+    r = order // 2
+    if ndim == 2:
+        shape = (41 + r, 57 + 3 * r)
+        spacing = (7.0, 9.0)
+        nbl = [0, 6, 5, 7]
+        bc = ["null_neumann", "null_dirichlet", "none", "null_dirichlet"]
+    else:
+        shape = (23 + r, 19 + 2 * r, 37 + r)
+        spacing = (9.0, 8.0, 10.0)
+        nbl = [0, 4, 3, 5, 4, 6]
+        bc = ["null_neumann", "null_dirichlet", "null_dirichlet", "none", "null_neumann", "null_dirichlet"]
+    vel = (1800.0 + 900.0 * rng.random(shape)).astype(np.float32)
+    rho = (1500.0 + 1200.0 * rng.random(shape)).astype(np.float32) if density else None
+    dt = 0.3 * min(spacing) / float(vel.max())
+    phys = [(shape[a] - nbl[2 * a] - nbl[2 * a + 1] - 1) * spacing[a] for a in range(ndim)]
+    rw = min(4, r + 1)
+    # one off-grid source, one on-grid source; receivers on and off grid
+    src = np.array([[0.31 * p for p in phys], [round(0.6 * p / s) * s for p, s in zip(phys, spacing)]])
+    rec = np.array([[0.5 * p for p in phys], [0.2 * p + 0.37 for p in phys], [0.8 * p for p in phys],
+                    [spacing[0]] + [0.45 * p for p in phys[1:]]])
+    return Workload("small", ndim, shape, spacing, order, nbl, bc, 40.0 / (max(nbl) ** 3), 3, dt, n_steps,
+                    30.0, 1.0 / 30.0, src, rec, rw, vel, rho)
+
+
+@pytest.mark.parametrize("density", [False, True])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20])
+def test_small_grids_all_orders(cuda_device, ndim, order, density):
+    w = small_case(ndim, order, density, seed=order + 7 * ndim)
+    s_gpu, p_gpu = run_gpu(w)
+    s_ref, p_ref = run_oracle(w)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_host_and_device_buffers_agree(cuda_device):
+    w = small_case(3, 8, True, seed=3, n_steps=30)
+    s_dev, p_dev = run_gpu(w, device_io=True)
+    s_host, p_host = run_gpu(w, device_io=False)
+    assert np.array_equal(s_dev, s_host) and np.array_equal(p_dev, p_host)
+
+
+def test_2d_homogeneous_full_length(cuda_device):
+    w = workloads.make("2d_homogeneous_256")
+    s_gpu, p_gpu = run_gpu(w)
+    s_ref, p_ref = run_oracle(w)
+    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_3d_layered_full_grid_reduced_steps(cuda_device):
+    w = workloads.make("3d_layered_256", n_steps=24)
+    s_gpu, p_gpu = run_gpu(w)
+    s_ref, p_ref = run_oracle(w)
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_3d_layered_reduced_grid_long(cuda_device):
+    w = workloads.make("3d_layered_256", shape=(64, 72, 80), n_steps=400)
+    s_gpu, p_gpu = run_gpu(w)
+    s_ref, p_ref = run_oracle(w)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_3d_variable_density_reduced_grid(cuda_device):
+    w = workloads.make("3d_vd_512x512x384", shape=(72, 80, 96), n_steps=300)
+    s_gpu, p_gpu = run_gpu(w)
+    s_ref, p_ref = run_oracle(w)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_3d_variable_density_full_grid_few_steps(cuda_device):
+    w = workloads.make("3d_vd_512x512x384", n_steps=6)
+    _, p_gpu = run_gpu(w)
+    _, p_ref = run_oracle(w)
+    assert np.abs(p_ref).max() > 0
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+
+
+def test_full_length_prefix_and_invariances(cuda_device):
+    """Full 2000-step 3D run: its first rows match the oracle's short run; shifting the
+    wavelet by m samples shifts the trace by m rows exactly; doubling it doubles the trace."""
+    w = workloads.make("3d_layered_256")
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
+    s_full, _ = run_gpu(w, wavelet=wav, final=False)
+    k = 40
+    s_ref, _ = run_oracle(w, n_steps=k)
+    assert rel_l2(s_full[:k], s_ref) <= FP32_SEIS_TOL or np.abs(s_ref).max() == 0
+    m = 25
+    wav_shift = np.concatenate([np.zeros(m, np.float32), wav[:-m]])
+    s_shift, _ = run_gpu(w, wavelet=wav_shift, final=False)
+    assert np.array_equal(s_shift[m:], s_full[:-m])
+    assert not np.any(s_shift[:m])
+    s_double, _ = run_gpu(w, wavelet=2.0 * wav, final=False)
+    assert np.array_equal(s_double, 2.0 * s_full)
+    assert np.all(np.isfinite(s_full)) and np.abs(s_full).max() > 0
+
+
+def test_zero_steps_and_no_sources(cuda_device):
+    w = small_case(2, 8, False, n_steps=10)
+    s, p = run_gpu(w, n_steps=0)
+    assert s.shape == (0, len(w.rec_pos)) and not np.any(p)
+    w.src_pos = np.zeros((0, 2))
+    s, p = run_gpu(w, n_steps=10)
+    assert not np.any(s) and not np.any(p)
+
+
+def test_error_statuses(cuda_device):
+    import torch
+    w = small_case(2, 8, False, n_steps=10)
+    g = api.sw_create_grid(2, w.shape, w.spacing, 8, w.nbl, w.bc, 0.0, 3, 10.0)  # dt far too large
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_forward(g, 1)
+    assert e.value.status == api.SW_ESTATE
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_model(g, torch.from_numpy(w.velocity))
+    assert e.value.status == api.SW_ECFL
+    g.close()
+    g = api.sw_create_grid(2, w.shape, w.spacing, 8, w.nbl, w.bc, 0.0, 3, 0.0)
+    api.sw_set_model(g, torch.from_numpy(w.velocity))
+    assert 0 < api.sw_get_dt(g) < 1e-2
+    bad = np.array([[3.5 * w.spacing[0] - w.spacing[0] * 5, 100.0]])
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_acquisition(g, bad, w.rec_pos, np.zeros(10, np.float32), window_radius=4)
+    assert e.value.status == api.SW_EINVAL
+    vel_bad = w.velocity.copy()
+    vel_bad[3, 4] = -1.0
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_model(g, torch.from_numpy(vel_bad))
+    assert e.value.status == api.SW_EINVAL
+    g.close()
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_create_grid(2, w.shape, w.spacing, 7, w.nbl, w.bc, 0.0, 3, 0.0)
+    assert e.value.status == api.SW_EINVAL

@@ -212,3 +212,19 @@ def test_damping_distance_brute_force():
     eta = oracle.eta_field(shape, nbl, 0.5, 3)
     assert np.allclose(eta, 0.5 * d ** 3)
     assert eta[nbl[0]:shape[0] - nbl[1], nbl[2]:shape[1] - nbl[3], nbl[4]:shape[2] - nbl[5]].max() == 0
+
+
+def test_window_fitting_keeps_nonzero_weights_on_their_nodes():
+    # on-grid in z at node 2 with r = 4: nodes -1..6, only node 2 is nonzero
+    f, w = oracle.weights_1d(2.0, 4)
+    assert f == -1
+    f2, w2 = oracle.source.fit_window(f, w, 50)
+    assert f2 == 0 and w2[2] == 1.0 and sum(abs(x) for x in w2) == 1.0
+    # high face: node 47 of 50, nodes 44..51
+    f, w = oracle.weights_1d(47.0, 4)
+    f2, w2 = oracle.source.fit_window(f, w, 50)
+    assert f2 == 42 and w2[47 - 42] == 1.0
+    # off-grid near the face: a nonzero weight would leave the grid
+    f, w = oracle.weights_1d(2.5, 4)
+    with pytest.raises(ValueError):
+        oracle.source.fit_window(f, w, 50)
