@@ -170,6 +170,9 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="3d_layered_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="override the workload's time steps per forward (profiling runs only)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="forwards timed end to end (0 skips)")
     args = ap.parse_args()
     world, rank, local = _dist()
 
@@ -202,7 +205,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    w = workloads.make(args.workload)
+    w = workloads.make(args.workload, n_steps=args.time_steps or None)
     vd = w.density is not None
     stream = torch.cuda.current_stream(dev)
     g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
@@ -253,18 +256,23 @@ def main():
     vel_h = torch.from_numpy(w.velocity).pin_memory()
     rho_h = None if w.density is None else torch.from_numpy(w.density).pin_memory()
     seis_h = torch.empty((w.n_steps, n_rec), dtype=torch.float32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        api.sw_set_model(g, vel_h, rho_h)
-        api.sw_forward(g, w.n_steps, seis_h, None)
-        _ = float(seis_h[-1, 0])
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = w.updates * e2e_steps * world / e2e_s / 1e9
-    h2d = w.velocity.nbytes + (0 if w.density is None else w.density.nbytes)
-    d2h = seis_h.numel() * 4
+    e2e = None
+    if args.e2e_steps > 0:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            api.sw_set_model(g, vel_h, rho_h)
+            api.sw_forward(g, w.n_steps, seis_h, None)
+            _ = float(seis_h[-1, 0])
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        e2e_value = w.updates * args.e2e_steps * world / float(e2e_t.item()) / 1e9
+        h2d = w.velocity.nbytes + (0 if w.density is None else w.density.nbytes)
+        e2e = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": seis_h.numel() * 4}
 
     peak, peak_kind = _peaks()
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
@@ -286,8 +294,7 @@ def main():
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "stencil (per-launch CUDA events, %d launches)" % stencil_launches,
                          "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
-            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": int(kernels),
             "clocks": clk,
         }

@@ -178,9 +178,6 @@ StencilArgs stencil_args(const sw_grid* g) {
   fd_second_weights(g->order, v);
   fd_first_weights(g->order, w);
   const double hz = g->h[0], hy = g->h[1], hx = g->h[2];
-  double c0 = v[0] / (hz * hz) + v[0] / (hx * hx);
-  if (g->ndim == 3) c0 += v[0] / (hy * hy);
-  a.c0 = float(c0);
   for (int j = 1; j <= g->R; ++j) {
     a.cz[j] = float(v[j] / (hz * hz));
     a.cy[j] = float(v[j] / (hy * hy));
@@ -473,9 +470,9 @@ sw_status sw_set_model(sw_grid* g, const float* velocity, const float* density) 
   // damping coefficients by squared distance
   std::vector<float2> table(size_t(g->damp_len));
   for (int64_t d2 = 0; d2 < g->damp_len; ++d2) {
-    double a, b;
-    damping_coefficients(g->alpha, g->degree, dt, d2, &a, &b);
-    table[size_t(d2)] = make_float2(float(a), float(b));
+    double a, e;
+    damping_coefficients(g->alpha, g->degree, dt, d2, &a, &e);
+    table[size_t(d2)] = make_float2(float(a), float(e));
   }
   SW_CUDA(cudaMemcpyAsync(g->damp, table.data(), table.size() * sizeof(float2), cudaMemcpyHostToDevice,
                           g->stream));

@@ -53,13 +53,12 @@ double critical_dt(int ndim, int order, const double* h, double c_max) {
   return 2.0 / (c_max * std::sqrt(s));
 }
 
-void damping_coefficients(double alpha, int degree, double dt, int64_t d2, double* a, double* b) {
+void damping_coefficients(double alpha, int degree, double dt, int64_t d2, double* a, double* e) {
   double d = std::sqrt(double(d2));
   double dp = 1.0;
   for (int i = 0; i < degree; ++i) dp *= d;
-  double e = (d2 == 0) ? 0.0 : alpha * dp * dt;
-  *a = 1.0 / (1.0 + e);
-  *b = (1.0 - e) / (1.0 + e);
+  *e = (d2 == 0) ? 0.0 : alpha * dp * dt;
+  *a = 1.0 / (1.0 + *e);
 }
 
 double bessel_i0(double x) {

@@ -19,8 +19,8 @@ double stencil_abs_sum(int order);
 double critical_dt(int ndim, int order, const double* h, double c_max);
 
 // Damping coefficients for a squared distance d2 (cells^2) to the physical
-// domain: e = alpha d^p dt, a = 1/(1+e), b = (1-e)/(1+e) (Eq. 4, 7).
-void damping_coefficients(double alpha, int degree, double dt, int64_t d2, double* a, double* b);
+// domain: e = eta dt = alpha d^p dt and a = 1/(1+e) (Eq. 4, 7).
+void damping_coefficients(double alpha, int degree, double dt, int64_t d2, double* a, double* e);
 
 // Sec. 2.4: modified Bessel I0 (power series), Kaiser parameter b(r), and the
 // 2r separable weights of a point at cell coordinate s.

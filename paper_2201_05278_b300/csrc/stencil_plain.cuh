@@ -7,8 +7,8 @@
 // halo.  p[n-1] and kappa are read once per node; p[n+1] overwrites p[n-1].
 //
 // Per node (Sec. 2.2, Eq. 7 with every term divided by 1 + eta dt):
-//   p[n+1] = a (kappa L p[n] + 2 p[n]) - b p[n-1],  a = 1/(1+e), b = (1-e)/(1+e)
-//   L = sum_axes h^-2 (v0 p + sum_j v_j (p+j + p-j))               (Eq. 9)
+//   p[n+1] = a (p[n] + kappa L p[n] + (p[n] - p[n-1]) + e p[n-1]),  a = 1/(1+e)
+//   L = sum_axes h^-2 sum_j v_j ((p+j + p-j) - 2p)   (Eq. 9, v0 = -2 sum_j v_j)
 //       - sum_axes D(ln rho) D(p),  D = (2h)^-1 sum_j w_j (.+j - .-j) (Eq. 10)
 // e = alpha d^p dt from a table indexed by the squared cell distance to the
 // physical domain (Eq. 4).  Face conditions are kept in ghost nodes: the
@@ -29,13 +29,12 @@ struct StencilArgs {
   float* pnm1;          // p[n-1] in, p[n+1] out
   const float* kappa;   // (c dt)^2
   const float* lnrho;   // ln(rho) with mirrored ghosts, or nullptr
-  const float2* damp;   // (a, b) indexed by squared distance (cells^2)
+  const float2* damp;   // (a, e) = (1/(1+eta dt), eta dt) by squared distance (cells^2)
   int64_t sz, sy;
   int nz, ny, nx;
   int nbl[6];
   int bc[6];
   int zchunk;
-  float c0;                                          // sum_axes v0 / h^2
   float cz[kMaxR + 1], cy[kMaxR + 1], cx[kMaxR + 1];  // v_j / h^2
   float gz[kMaxR + 1], gy[kMaxR + 1], gx[kMaxR + 1];  // w_j / (2h)
 };
@@ -149,12 +148,16 @@ __global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const Sten
     for (int i = 0; i < PPT; ++i) {
       const int row = (NDIM == 3) ? ty * PPT + i + R : 0;
       const float pc = q[i][R];
-      float lap = a.c0 * pc;
+      const float p2 = 2.f * pc;
+      // sum_j c_j ((p+j + p-j) - 2p): the FP32 operator annihilates constants exactly
+      // (a separate v0 p term would leave the FP32 rounding of sum(v) as a spurious
+      // mass term that shifts the phase of long runs).
+      float lap = 0.f;
 #pragma unroll
       for (int j = 1; j <= R; ++j) {
-        lap = fmaf(a.cz[j], q[i][R + j] + q[i][R - j], lap);
-        lap = fmaf(a.cx[j], sp[row][tx + R + j] + sp[row][tx + R - j], lap);
-        if constexpr (NDIM == 3) lap = fmaf(a.cy[j], sp[row + j][tx + R] + sp[row - j][tx + R], lap);
+        lap = fmaf(a.cz[j], (q[i][R + j] + q[i][R - j]) - p2, lap);
+        lap = fmaf(a.cx[j], (sp[row][tx + R + j] + sp[row][tx + R - j]) - p2, lap);
+        if constexpr (NDIM == 3) lap = fmaf(a.cy[j], (sp[row + j][tx + R] + sp[row - j][tx + R]) - p2, lap);
       }
       if constexpr (VD) {
         float dpz = 0.f, dlz = 0.f, dpx = 0.f, dlx = 0.f, dpy = 0.f, dly = 0.f;
@@ -179,13 +182,17 @@ __global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const Sten
         const int dy = (NDIM == 3) ? layer_distance(y, a.ny, a.nbl[2], a.nbl[3]) : 0;
         const int dx = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
         const int d2 = dz * dz + dy * dy + dx * dx;
-        float ca = 1.f, cb = 1.f;
+        float ca = 1.f, e = 0.f;
         if (d2 != 0) {
           const float2 c = __ldg(&a.damp[d2]);
           ca = c.x;
-          cb = c.y;
+          e = c.y;
         }
-        float pnew = ca * fmaf(kp[i], lap, 2.f * pc) - cb * po[i];
+        // (1+e) p[n+1] = kappa L + 2p - (1-e) p[n-1], evaluated as
+        // p[n+1] = a (p + (kappa L + (p - p[n-1]) + e p[n-1])): p - p[n-1] is small and
+        // (for a smooth field) exact, so only the last add rounds at the scale of p.
+        const float dp = pc - po[i];
+        float pnew = ca * (pc + fmaf(kp[i], lap, fmaf(e, po[i], dp)));
         const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
                          (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet) ||
                          (NDIM == 3 && ((y == 0 && a.bc[2] == kBcDirichlet) ||

@@ -6,7 +6,7 @@ space order, both dimensions, both density paths, ragged tiles and mixed
 face conditions; the named workloads are checked at full grid size with a
 reduced step count, and full-length runs are checked by properties that
 hold at any size (causality against the oracle's prefix, exact time-shift
-and amplitude-scaling invariance).
+invariance, amplitude scaling up to FP32 rounding noise).
 """
 import numpy as np
 import pytest
@@ -106,7 +106,8 @@ def test_3d_variable_density_full_grid_few_steps(cuda_device):
 
 def test_full_length_prefix_and_invariances(cuda_device):
     """Full 2000-step 3D run: its first rows match the oracle's short run; shifting the
-    wavelet by m samples shifts the trace by m rows exactly; doubling it doubles the trace."""
+    wavelet by m samples shifts the trace by m rows exactly; doubling it doubles the trace
+    up to FP32 rounding noise."""
     w = workloads.make("3d_layered_256")
     wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
     s_full, _ = run_gpu(w, wavelet=wav, final=False)
@@ -118,8 +119,11 @@ def test_full_length_prefix_and_invariances(cuda_device):
     s_shift, _ = run_gpu(w, wavelet=wav_shift, final=False)
     assert np.array_equal(s_shift[m:], s_full[:-m])
     assert not np.any(s_shift[:m])
+    # Scaling by 2 is exact in FP32 only while no value is subnormal; the far
+    # leading edge of the wavefield is, and from there on the two runs round
+    # independently, so the difference measures the FP32 rounding noise.
     s_double, _ = run_gpu(w, wavelet=2.0 * wav, final=False)
-    assert np.array_equal(s_double, 2.0 * s_full)
+    assert rel_l2(s_double, 2.0 * s_full) <= FP32_SEIS_TOL
     assert np.all(np.isfinite(s_full)) and np.abs(s_full).max() > 0
 
 
