@@ -148,6 +148,40 @@ sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_
 /* Bytes of device memory the grid holds (wavefields, model, acquisition). */
 sw_status sw_get_device_bytes(const sw_grid* g, int64_t* bytes);
 
+/*
+ * sw_forward_noalloc -- the whole forward run of sw_create_grid +
+ * sw_set_model + sw_set_acquisition + sw_forward in one call that allocates
+ * no device memory.  The paper has no counterpart; it exists for callers that
+ * cannot call cudaMalloc: programs whose device memory belongs to a pool or
+ * framework allocator with a fixed budget, and loops that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree imply.
+ *
+ * Arguments mean what they mean in the four calls above, with these limits:
+ *   - velocity, density (NULL for constant density), seismogram and
+ *     final_field (NULL to skip) must be device memory of the current
+ *     device; positions are host memory; the wavelet may be host or device.
+ *   - Wavefields, model fields, damping table and window weights live in one
+ *     static device array of SW_NOALLOC_SCRATCH_BYTES that every GPU which
+ *     loads the library holds until the process exits.  A problem that needs
+ *     more (about three padded FP32 copies of the grid, four with density)
+ *     is rejected with SW_EINVAL before any device work; the message gives
+ *     the bytes needed.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the same array and leaves its contents behind (the
+ *     call clears what must start at zero).  Calls whose GPU work overlaps,
+ *     on one device, race on the array and give wrong results: serialise them.
+ *   - Synchronises the stream before returning, like sw_forward.
+ */
+#define SW_NOALLOC_SCRATCH_BYTES (32ull << 20)
+sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const double* spacing, int space_order,
+                             const int* nbl, const int* bc, double damp_alpha, int damp_degree,
+                             double dt, const float* velocity, const float* density, int n_src,
+                             const double* src_pos, int n_rec, const double* rec_pos, int nt,
+                             const float* wavelet, int wavelet_per_source, int window_radius,
+                             int n_steps, float* seismogram, float* final_field, void* cuda_stream);
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* sw_last_error(void);
 

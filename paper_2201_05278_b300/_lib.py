@@ -30,6 +30,11 @@ SIGNATURES = {
     "sw_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_get_profile": (ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_i64p, _c_i64p]),
     "sw_get_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _c_i64p]),
+    "sw_forward_noalloc": (ctypes.c_int, [ctypes.c_int, _c_i64p, _c_dp, ctypes.c_int, _c_ip, _c_ip,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_int, _c_dp, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_destroy_grid": (None, [ctypes.c_void_p]),
 }

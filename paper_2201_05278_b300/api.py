@@ -157,6 +157,40 @@ def sw_get_device_bytes(g: Grid) -> int:
     return v.value
 
 
+SW_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def sw_forward_noalloc(ndim: int, shape: Sequence[int], spacing: Sequence[float], space_order: int,
+                       nbl: Sequence[int], bc: Sequence, damp_alpha: float, damp_degree: int, dt: float,
+                       velocity, density, src_pos, rec_pos, wavelet, window_radius: int, n_steps: int,
+                       seismogram=None, final_field=None, wavelet_per_source: bool = False, stream=None) -> None:
+    """Forward run that allocates no device memory (see sw_forward_noalloc in the C header).
+
+    velocity / density / seismogram / final_field must be CUDA tensors; the
+    outputs must be preallocated by the caller.
+    """
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    src = np.ascontiguousarray(np.asarray(src_pos, dtype=np.float64).reshape(-1, ndim))
+    rec = np.ascontiguousarray(np.asarray(rec_pos, dtype=np.float64).reshape(-1, ndim))
+    if hasattr(wavelet, "data_ptr"):
+        wav = wavelet
+    else:
+        wav = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float32))
+    nt = int(wav.shape[-1])
+    dp = ctypes.POINTER(ctypes.c_double)
+    shp = (ctypes.c_int64 * ndim)(*[int(s) for s in shape])
+    spc = (ctypes.c_double * ndim)(*[float(s) for s in spacing])
+    _check(_lib.load().sw_forward_noalloc(
+        int(ndim), shp, spc, int(space_order), _faces(nbl, ndim), _faces(bc, ndim, BC_NAMES), float(damp_alpha),
+        int(damp_degree), float(dt), _ptr(velocity), _ptr(density), int(src.shape[0]), src.ctypes.data_as(dp),
+        int(rec.shape[0]), rec.ctypes.data_as(dp), nt, _ptr(wav), int(bool(wavelet_per_source)),
+        int(window_radius), int(n_steps), _ptr(seismogram), _ptr(final_field), ctypes.c_void_p(stream)))
+
+
 def sw_last_error() -> str:
     msg = _lib.load().sw_last_error()
     return msg.decode() if msg else ""

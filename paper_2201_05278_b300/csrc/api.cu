@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -707,3 +708,307 @@ void sw_destroy_grid(sw_grid* g) {
 }
 
 }  // extern "C"
+
+// ---- allocation-free forward ------------------------------------------------
+//
+// sw_forward_noalloc runs the same forward simulation as the handle-based calls
+// (same kernels, same launch shapes) for callers that cannot allocate device
+// memory.  Everything the simulation needs besides the caller's inputs and
+// outputs lives in one file-scope device array of SW_NOALLOC_SCRATCH_BYTES.
+
+static __device__ __align__(256) float noalloc_scratch[SW_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float* g_noalloc_address[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code only
+// sees a host-side stand-in under the array's name, so the address is looked
+// up once per device (with that device current) and cached.
+sw_status noalloc_scratch_address(float** out) {
+  int dev = 0;
+  SW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SW_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_address[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(SW_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    g_noalloc_address[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_address[dev];
+  return SW_OK;
+}
+
+// Bump carving of the scratch array in 256-byte units (host arithmetic only).
+struct ScratchCarver {
+  float* base;
+  size_t used;
+  size_t cap;
+  float* take(size_t floats) {
+    const size_t n = (floats + 63) / 64 * 64;
+    float* p = base ? base + used : nullptr;
+    used += n;
+    return p;
+  }
+};
+
+// One point's per-axis first node and weights (same windows and fitting as
+// build_windows), written into fixed-size caller arrays.
+sw_status noalloc_point_window(const sw_grid* g, const double* pos, bool fold_cell, int i, int* first3,
+                               float* w3) {
+  const int rw = g->rw, L = g->L;
+  double cell = 1.0;
+  for (int a = 0; a < g->ndim; ++a) cell *= (g->ndim == 3 ? g->h[a] : (a == 0 ? g->h[0] : g->h[2]));
+  for (int k = 0; k < 3 * L; ++k) w3[k] = 0.f;
+  first3[0] = first3[1] = first3[2] = 0;
+  for (int a = 0; a < g->ndim; ++a) {
+    const int axis = (g->ndim == 3) ? a : (a == 0 ? 0 : 2);
+    const double coord = pos[size_t(i) * g->ndim + a];
+    if (!std::isfinite(coord)) return fail(SW_EINVAL, "position %d is not finite", i);
+    const double s = double(g->nbl[2 * axis]) + coord / g->h[axis];
+    int64_t f0;
+    double ww[2 * kMaxR], wf[2 * kMaxR];
+    kaiser_sinc_weights(s, rw, &f0, ww);
+    const int64_t nax = g->n[axis];
+    if (2 * rw > nax) return fail(SW_EINVAL, "window longer than axis %d", axis);
+    const int64_t nf = std::min(std::max<int64_t>(f0, 0), nax - 2 * rw);
+    for (int j = 0; j < 2 * rw; ++j) wf[j] = 0.0;
+    for (int j = 0; j < 2 * rw; ++j) {
+      const int64_t node = f0 + j;
+      if (node >= nf && node < nf + 2 * rw)
+        wf[node - nf] = ww[j];
+      else if (ww[j] != 0.0)
+        return fail(SW_EINVAL, "window of point %d leaves the grid along axis %d", i, axis);
+    }
+    first3[axis] = int(nf);
+    for (int j = 0; j < 2 * rw; ++j) {
+      double v = wf[j];
+      if (fold_cell && axis == 2) v /= cell;
+      w3[axis * L + j] = float(v);
+    }
+  }
+  if (g->ndim == 2) w3[1 * L] = 1.f;
+  return SW_OK;
+}
+
+// Uploads the windows of `count` points in fixed-size chunks from the stack
+// (pageable-source copies return once the source may be reused).
+sw_status noalloc_upload_windows(const sw_grid* g, int count, const double* pos, bool fold_cell, int* dfirst,
+                                 float* dw) {
+  constexpr int kChunk = 32;
+  int first[kChunk * 3];
+  float w[kChunk * 3 * 2 * kMaxR];
+  const int L = g->L;
+  for (int i0 = 0; i0 < count; i0 += kChunk) {
+    const int nc = std::min(kChunk, count - i0);
+    for (int k = 0; k < nc; ++k)
+      SW_TRY(noalloc_point_window(g, pos, fold_cell, i0 + k, first + 3 * k, w + 3 * L * k));
+    SW_CUDA(cudaMemcpyAsync(dfirst + 3 * i0, first, size_t(nc) * 3 * sizeof(int), cudaMemcpyHostToDevice,
+                            g->stream));
+    SW_CUDA(cudaMemcpyAsync(dw + size_t(3) * L * i0, w, size_t(nc) * 3 * L * sizeof(float),
+                            cudaMemcpyHostToDevice, g->stream));
+  }
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const double* spacing, int space_order,
+                                        const int* nbl, const int* bc, double damp_alpha, int damp_degree,
+                                        double dt, const float* velocity, const float* density, int n_src,
+                                        const double* src_pos, int n_rec, const double* rec_pos, int nt,
+                                        const float* wavelet, int wavelet_per_source, int window_radius,
+                                        int n_steps, float* seismogram, float* final_field, void* cuda_stream) {
+  g_last_error.clear();
+  // -- arguments (same rules as sw_create_grid / sw_set_model / sw_set_acquisition / sw_forward)
+  if (!shape || !spacing || !nbl || !bc || !velocity) return fail(SW_EINVAL, "NULL argument");
+  if (ndim != 2 && ndim != 3) return fail(SW_EINVAL, "ndim must be 2 or 3 (got %d)", ndim);
+  if (space_order < 2 || space_order > 2 * kMaxR || space_order % 2)
+    return fail(SW_EINVAL, "space_order must be even in [2, 20] (got %d)", space_order);
+  if (!(damp_alpha >= 0.0) || !std::isfinite(damp_alpha) || damp_degree < 0 || damp_degree > 16)
+    return fail(SW_EINVAL, "damping parameters out of range");
+  if (!std::isfinite(dt)) return fail(SW_EINVAL, "dt is not finite");
+  if (n_src < 0 || n_rec < 0 || nt < 0 || n_steps < 0) return fail(SW_EINVAL, "negative count");
+  if ((n_src > 0 && (!src_pos || !wavelet || nt == 0)) || (n_rec > 0 && !rec_pos))
+    return fail(SW_EINVAL, "NULL positions or wavelet");
+  if (window_radius < 1 || window_radius > kMaxR) return fail(SW_EINVAL, "window_radius must be in [1, 10]");
+  if (n_src > 0 && n_steps > nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, nt);
+  if (n_rec > 0 && n_steps > 0 && !seismogram) return fail(SW_EINVAL, "seismogram is NULL");
+
+  sw_grid g;  // description only: every device pointer below points into the scratch array
+  g.ndim = ndim;
+  g.order = space_order;
+  g.R = space_order / 2;
+  for (int a = 0; a < ndim; ++a) {
+    const int axis = (ndim == 3) ? a : (a == 0 ? 0 : 2);
+    if (shape[a] < g.R + 1 || shape[a] > (int64_t(1) << 24))
+      return fail(SW_EINVAL, "shape[%d] = %lld out of range", a, (long long)shape[a]);
+    if (!(spacing[a] > 0.0) || !std::isfinite(spacing[a])) return fail(SW_EINVAL, "spacing[%d] must be positive", a);
+    g.n[axis] = shape[a];
+    g.h[axis] = spacing[a];
+    for (int s = 0; s < 2; ++s) {
+      const int nb = nbl[2 * a + s], b = bc[2 * a + s];
+      if (nb < 0 || nb >= shape[a]) return fail(SW_EINVAL, "nbl[%d] out of range", 2 * a + s);
+      if (b != SW_BC_NONE && b != SW_BC_DIRICHLET && b != SW_BC_NEUMANN)
+        return fail(SW_EINVAL, "bc[%d] invalid", 2 * a + s);
+      g.nbl[2 * axis + s] = nb;
+      g.bc[2 * axis + s] = b;
+    }
+    if (nbl[2 * a] + nbl[2 * a + 1] >= shape[a]) return fail(SW_EINVAL, "absorbing layers cover the whole axis %d", a);
+  }
+  g.alpha = damp_alpha;
+  g.degree = damp_degree;
+  g.dt_user = dt;
+  g.stream = static_cast<cudaStream_t>(cuda_stream);
+  g.lay.init(ndim, g.R, g.n);
+  g.rw = window_radius;
+  g.L = 2 * window_radius;
+  g.lz = g.L;
+  g.ly = (ndim == 3) ? g.L : 1;
+  g.lx = g.L;
+  g.n_src = n_src;
+  g.n_rec = n_rec;
+  g.nt = nt;
+  g.sig_stride = wavelet_per_source ? nt : 0;
+  g.has_density = density != nullptr;
+  int64_t maxd2 = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int64_t m = std::max(g.nbl[2 * a], g.nbl[2 * a + 1]);
+    maxd2 += m * m;
+  }
+  g.damp_len = maxd2 + 1;
+
+  // -- scratch plan; reject problems that do not fit before touching the device
+  const size_t field = size_t(g.lay.total);
+  const size_t wav_floats = size_t(n_src > 0 ? (wavelet_per_source ? n_src : 1) : 0) * size_t(nt);
+  ScratchCarver plan{nullptr, 0, 0};
+  plan.take(field);
+  plan.take(field);
+  plan.take(field);
+  if (g.has_density) plan.take(field);
+  plan.take(size_t(g.damp_len) * 2);
+  plan.take(64);
+  plan.take(size_t(n_src) * 3);
+  plan.take(size_t(n_src) * 3 * g.L);
+  plan.take(wav_floats);
+  plan.take(size_t(n_rec) * 3);
+  plan.take(size_t(n_rec) * 3 * g.L);
+  const size_t cap = SW_NOALLOC_SCRATCH_BYTES / sizeof(float);
+  if (plan.used > cap)
+    return fail(SW_EINVAL, "problem needs %zu bytes of scratch; sw_forward_noalloc is limited to %zu bytes",
+                plan.used * sizeof(float), size_t(SW_NOALLOC_SCRATCH_BYTES));
+
+  // grid-shaped inputs and outputs must already be on the device (host staging would allocate)
+  if (!is_device_pointer(velocity) || (density && !is_device_pointer(density)) ||
+      (seismogram && !is_device_pointer(seismogram)) || (final_field && !is_device_pointer(final_field)))
+    return fail(SW_EINVAL, "sw_forward_noalloc needs device pointers for velocity, density and the outputs");
+
+  float* base = nullptr;
+  SW_TRY(noalloc_scratch_address(&base));
+  ScratchCarver sc{base, 0, cap};
+  g.u[0] = sc.take(field);
+  g.u[1] = sc.take(field);
+  g.kappa = sc.take(field);
+  g.lnrho = g.has_density ? sc.take(field) : nullptr;
+  g.damp = reinterpret_cast<float2*>(sc.take(size_t(g.damp_len) * 2));
+  g.dflag = reinterpret_cast<int*>(sc.take(64));
+  g.dscratch = reinterpret_cast<unsigned*>(g.dflag + 16);
+  g.src_first = reinterpret_cast<int*>(sc.take(size_t(n_src) * 3));
+  g.src_w = sc.take(size_t(n_src) * 3 * g.L);
+  g.wavelet = sc.take(wav_floats);
+  g.rec_first = reinterpret_cast<int*>(sc.take(size_t(n_rec) * 3));
+  g.rec_w = sc.take(size_t(n_rec) * 3 * g.L);
+
+  // -- the array keeps the previous call's contents: clear what must start at zero
+  const size_t fbytes = field * sizeof(float);
+  SW_CUDA(cudaMemsetAsync(g.u[0], 0, fbytes, g.stream));
+  SW_CUDA(cudaMemsetAsync(g.u[1], 0, fbytes, g.stream));
+  SW_CUDA(cudaMemsetAsync(g.kappa, 0, fbytes, g.stream));
+  if (g.lnrho) SW_CUDA(cudaMemsetAsync(g.lnrho, 0, fbytes, g.stream));
+  SW_CUDA(cudaMemsetAsync(g.dflag, 0, 64 * sizeof(float), g.stream));
+
+  // -- model: velocity range, dt (Eq. 8), kappa, damping table, ln(rho)
+  const FaceInfo f = g.faces();
+  const int64_t nn = g.nodes();
+  const unsigned init[2] = {0u, 0x7f800000u};
+  SW_CUDA(cudaMemcpyAsync(g.dscratch, init, sizeof(init), cudaMemcpyHostToDevice, g.stream));
+  field_range_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(velocity, nn, g.dscratch, g.dscratch + 1, g.dflag);
+  if (density)
+    field_range_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(density, nn, g.dscratch + 2, g.dscratch + 3,
+                                                                   g.dflag);
+  SW_CUDA(cudaGetLastError());
+  unsigned res[2];
+  int bad = 0;
+  SW_CUDA(cudaMemcpyAsync(res, g.dscratch, sizeof(res), cudaMemcpyDeviceToHost, g.stream));
+  SW_CUDA(cudaMemcpyAsync(&bad, g.dflag, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+  SW_CUDA(cudaStreamSynchronize(g.stream));
+  if (bad) return fail(SW_EINVAL, "velocity and density must be finite and positive everywhere");
+  float vmax;
+  memcpy(&vmax, &res[0], sizeof(float));
+  const double hh[3] = {g.h[0], ndim == 3 ? g.h[1] : g.h[2], g.h[2]};
+  const double dtc = critical_dt(ndim, g.order, hh, double(vmax));
+  if (dt <= 0.0)
+    dt = dtc;
+  else if (dt > dtc)
+    return fail(SW_ECFL, "dt = %.6g s exceeds the stability bound %.6g s (c_max = %.6g m/s)", dt, dtc, double(vmax));
+  g.dt = dt;
+  kappa_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(velocity, g.at0(g.kappa), f, dt);
+  SW_CUDA(cudaGetLastError());
+  {
+    constexpr int kChunk = 512;
+    float2 table[kChunk];
+    for (int64_t d0 = 0; d0 < g.damp_len; d0 += kChunk) {
+      const int nc = int(std::min<int64_t>(kChunk, g.damp_len - d0));
+      for (int k = 0; k < nc; ++k) {
+        double da, de;
+        damping_coefficients(g.alpha, g.degree, dt, d0 + k, &da, &de);
+        table[k] = make_float2(float(da), float(de));
+      }
+      SW_CUDA(cudaMemcpyAsync(g.damp + d0, table, size_t(nc) * sizeof(float2), cudaMemcpyHostToDevice, g.stream));
+    }
+  }
+  if (density) {
+    lnrho_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(density, g.at0(g.lnrho), f);
+    SW_CUDA(cudaGetLastError());
+    for (int axis = 0; axis < 3; ++axis) {
+      if (ndim == 2 && axis == 1) continue;
+      mirror_even_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(g.at0(g.lnrho), f, axis, g.R);
+      SW_CUDA(cudaGetLastError());
+    }
+  }
+
+  // -- acquisition
+  if (n_src > 0) {
+    SW_TRY(noalloc_upload_windows(&g, n_src, src_pos, true, g.src_first, g.src_w));
+    SW_CUDA(cudaMemcpyAsync(g.wavelet, wavelet, wav_floats * sizeof(float), cudaMemcpyDefault, g.stream));
+  }
+  if (n_rec > 0) SW_TRY(noalloc_upload_windows(&g, n_rec, rec_pos, false, g.rec_first, g.rec_w));
+
+  // -- time loop (as sw_forward)
+  StencilArgs a = stencil_args(&g);
+  const PointSet src = point_set(&g, true), rec = point_set(&g, false);
+  const int src_threads = n_src * g.lz * g.ly * g.lx;
+  for (int step = 0; step < n_steps; ++step) {
+    a.pn = g.at0(g.u[step & 1]);
+    a.pnm1 = g.at0(g.u[(step + 1) & 1]);
+    launch_stencil(g.R, ndim, g.has_density, a, g.stream);
+    if (src_threads > 0)
+      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g.stream>>>(a.pnm1, a.kappa, g.damp, src, g.wavelet,
+                                                                            g.sig_stride, step, f, ndim, g.R);
+    if (n_rec > 0)
+      sample_receivers_kernel<<<(n_rec * 32 + 255) / 256, 256, 0, g.stream>>>(a.pnm1, rec, f, seismogram, step);
+  }
+  SW_CUDA(cudaGetLastError());
+  if (final_field) {
+    extract_kernel<<<grid_blocks(nn, 256), 256, 0, g.stream>>>(g.at0(g.u[n_steps & 1]), final_field, f);
+    SW_CUDA(cudaGetLastError());
+  }
+  SW_CUDA(cudaMemcpyAsync(&bad, g.dflag, sizeof(int), cudaMemcpyDeviceToHost, g.stream));
+  SW_CUDA(cudaStreamSynchronize(g.stream));
+  if (bad) return fail(SW_ETIMEOUT, "a kernel raised the device error flag (0x%x)", bad);
+  return SW_OK;
+}
