@@ -136,6 +136,19 @@ sw_status sw_get_dt(const sw_grid* g, double* dt);
 sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
 
 /*
+ * Stencil kernel variant.  Two CUDA implementations of the same update:
+ * SW_STENCIL_AUTO picks the TMA-pipelined persistent kernel for 3D
+ * constant-density grids and the shared-memory-plane kernel otherwise;
+ * SW_STENCIL_PLAIN forces the latter; SW_STENCIL_TMA asks for the former
+ * (3D only, else SW_EINVAL; cases it does not cover still use the plain
+ * kernel).  sw_get_stencil_variant reports the kernel sw_forward will launch
+ * for the current model.
+ */
+enum { SW_STENCIL_AUTO = 0, SW_STENCIL_PLAIN = 1, SW_STENCIL_TMA = 2 };
+sw_status sw_set_stencil_variant(sw_grid* g, int variant);
+sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
+
+/*
  * Kernel timing.  With profiling on, sw_forward records CUDA events around
  * every stencil launch on the grid's stream; sw_get_profile returns the
  * summed stencil time and launch count of the last sw_forward and the

@@ -16,6 +16,7 @@ from . import _lib
 
 SW_OK, SW_EINVAL, SW_ECFL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_ESTATE = range(7)
 SW_BC_NONE, SW_BC_DIRICHLET, SW_BC_NEUMANN = 0, 1, 2
+SW_STENCIL_AUTO, SW_STENCIL_PLAIN, SW_STENCIL_TMA = 0, 1, 2
 STATUS_NAMES = {0: "SW_OK", 1: "SW_EINVAL", 2: "SW_ECFL", 3: "SW_ENOMEM", 4: "SW_ECUDA",
                 5: "SW_ETIMEOUT", 6: "SW_ESTATE"}
 BC_NAMES = {"none": SW_BC_NONE, "null_dirichlet": SW_BC_DIRICHLET, "dirichlet": SW_BC_DIRICHLET,
@@ -136,6 +137,16 @@ def sw_ricker(f_peak: float, t0: float, dt: float, nt: int) -> np.ndarray:
     out = np.zeros(int(nt), dtype=np.float32)
     _check(_lib.load().sw_ricker(float(f_peak), float(t0), float(dt), int(nt), out.ctypes.data))
     return out
+
+
+def sw_set_stencil_variant(g: Grid, variant: int) -> None:
+    _check(_lib.load().sw_set_stencil_variant(g.handle, int(variant)))
+
+
+def sw_get_stencil_variant(g: Grid) -> int:
+    v = ctypes.c_int()
+    _check(_lib.load().sw_get_stencil_variant(g.handle, ctypes.byref(v)))
+    return v.value
 
 
 def sw_set_profiling(g: Grid, enable: bool = True) -> None:

@@ -1,4 +1,5 @@
 // C ABI of the solver (declared in include/simwave_b300.h).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +16,7 @@
 #include "host_setup.h"
 #include "layout.h"
 #include "stencil_plain.cuh"
+#include "stencil_tma.cuh"
 
 using namespace sw;
 
@@ -102,6 +104,13 @@ struct sw_grid {
   float* wavelet = nullptr;
   int* rec_first = nullptr;
   float* rec_w = nullptr;
+
+  // TMA tensor maps of the 3D pipelined stencil: p[n] with halo box and
+  // interior box for each of the two wavefield buffers, kappa interior box
+  int variant = SW_STENCIL_AUTO;
+  bool tma_ready = false;
+  int sm_count = 0;
+  CUtensorMap map_halo[2], map_inner[2], map_kappa;
 
   // profiling
   bool profiling = false;
@@ -250,6 +259,106 @@ void launch_stencil(int R, int ndim, bool vd, const StencilArgs& a, cudaStream_t
   }
 }
 
+// ---- TMA pipelined 3D stencil ------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tile shape of the pipelined kernel per stencil radius (must match the
+// instantiations in launch_stencil_tma).
+void tma_tile(int R, int* tx, int* ty) {
+  *tx = 32;
+  *ty = (R <= 4) ? 32 : 16;
+}
+
+sw_status make_map(const sw_grid* g, float* base, uint32_t box_x, uint32_t box_y, CUtensorMap* map) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(SW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const Layout& L = g->lay;
+  cuuint64_t dims[3] = {cuuint64_t(L.pitch), cuuint64_t(L.py), cuuint64_t(L.pz)};
+  cuuint64_t strides[2] = {cuuint64_t(L.sy) * 4, cuuint64_t(L.sz) * 4};
+  cuuint32_t box[3] = {box_x, box_y, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+  return SW_OK;
+}
+
+sw_status build_tma_maps(sw_grid* g) {
+  int tx, ty;
+  tma_tile(g->R, &tx, &ty);
+  const uint32_t xh = uint32_t((g->R + 3) / 4 * 4);
+  for (int i = 0; i < 2; ++i) {
+    SW_TRY(make_map(g, g->u[i], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &g->map_halo[i]));
+    SW_TRY(make_map(g, g->u[i], uint32_t(tx), uint32_t(ty), &g->map_inner[i]));
+  }
+  SW_TRY(make_map(g, g->kappa, uint32_t(tx), uint32_t(ty), &g->map_kappa));
+  g->tma_ready = true;
+  return SW_OK;
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
+
+template <int R, int TX, int TY, int PPT, int D, int NQ>
+void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  using C = TmaConfig<R, TX, TY, PPT, D, NQ>;
+  auto kern = stencil_tma_kernel<R, TX, TY, PPT, D, NQ>;
+  static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
+  if (!blocks_per_sm) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, C::NT, C::SMEM);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  TmaWork wk;
+  wk.tiles_x = (a.nx + TX - 1) / TX;
+  const int tiles_y = (a.ny + TY - 1) / TY;
+  wk.nz = a.nz;
+  wk.total = (long long)wk.tiles_x * tiles_y * a.nz;
+  long long grid = (long long)g->sm_count * blocks_per_sm;
+  if (grid > wk.total) grid = wk.total;
+  kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf ^ 1], g->map_kappa, a, wk,
+                                                g->dflag, kWaitLimitNs);
+}
+
+void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  switch (g->R) {
+    case 1: launch_tma_t<1, 32, 32, 4, 3, 4>(g, a, buf, st); break;
+    case 2: launch_tma_t<2, 32, 32, 4, 3, 4>(g, a, buf, st); break;
+    case 3: launch_tma_t<3, 32, 32, 4, 3, 4>(g, a, buf, st); break;
+    case 4: launch_tma_t<4, 32, 32, 4, 3, 4>(g, a, buf, st); break;
+    case 5: launch_tma_t<5, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 6: launch_tma_t<6, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 7: launch_tma_t<7, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 8: launch_tma_t<8, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 9: launch_tma_t<9, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 10: launch_tma_t<10, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    default: break;
+  }
+}
+
+bool use_tma(const sw_grid* g) {
+  if (g->variant == SW_STENCIL_PLAIN) return false;
+  return g->ndim == 3 && !g->has_density && g->tma_ready;
+}
+
 PointSet point_set(const sw_grid* g, bool src) {
   PointSet p;
   p.first = src ? g->src_first : g->rec_first;
@@ -326,7 +435,8 @@ sw_status check_device_flag(sw_grid* g) {
   SW_CUDA(cudaStreamSynchronize(g->stream));
   if (flag != 0) {
     SW_CUDA(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
-    return fail(SW_ETIMEOUT, "a kernel's bounded wait gave up (device flag 0x%x)", flag);
+    return fail(SW_ETIMEOUT, "device error flag 0x%x (bit 0: a bounded wait gave up; bit 1: a tensor-copy "
+                             "buffer failed its alignment check)", flag);
   }
   return SW_OK;
 }
@@ -410,6 +520,10 @@ sw_status sw_create_grid(sw_grid** out, int ndim, const int64_t* shape, const do
     }
     g->damp_len = maxd2 + 1;
     st = dev_alloc(g, (void**)&g->damp, size_t(g->damp_len) * sizeof(float2));
+  }
+  if (st == SW_OK) {
+    cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+    if (ndim == 3) st = build_tma_maps(g);
   }
   if (st == SW_OK) {
     cudaError_t e = cudaMemsetAsync(g->kappa, 0, fbytes, g->stream);
@@ -601,7 +715,10 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step], g->stream));
-    launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
+    if (use_tma(g))
+      launch_stencil_tma(g, a, step & 1, g->stream);
+    else
+      launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step + 1], g->stream));
     ++launches;
     if (src_threads > 0) {
@@ -664,6 +781,21 @@ sw_status sw_get_dt(const sw_grid* g, double* dt) {
 sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out) {
   if (!out || nt < 0 || !(f_peak > 0.0) || !(dt > 0.0)) return fail(SW_EINVAL, "bad Ricker arguments");
   ricker(f_peak, t0, dt, nt, out);
+  return SW_OK;
+}
+
+sw_status sw_set_stencil_variant(sw_grid* g, int variant) {
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (variant != SW_STENCIL_AUTO && variant != SW_STENCIL_PLAIN && variant != SW_STENCIL_TMA)
+    return fail(SW_EINVAL, "unknown stencil variant %d", variant);
+  if (variant == SW_STENCIL_TMA && g->ndim != 3) return fail(SW_EINVAL, "the pipelined stencil is 3D only");
+  g->variant = variant;
+  return SW_OK;
+}
+
+sw_status sw_get_stencil_variant(const sw_grid* g, int* variant) {
+  if (!g || !variant) return fail(SW_EINVAL, "NULL argument");
+  *variant = use_tma(g) ? SW_STENCIL_TMA : SW_STENCIL_PLAIN;
   return SW_OK;
 }
 

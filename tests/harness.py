@@ -28,7 +28,8 @@ def wavelet_of(w: Workload, nt=None):
     return oracle.ricker_samples(w.f_peak, w.dt, nt or w.n_steps, t0=w.t0)
 
 
-def run_gpu(w: Workload, n_steps=None, device_io=True, wavelet=None, final=True, profile=False):
+def run_gpu(w: Workload, n_steps=None, device_io=True, wavelet=None, final=True, profile=False, variant=None,
+            expect_variant=None):
     import torch
     n_steps = w.n_steps if n_steps is None else n_steps
     dev = torch.device("cuda:0")
@@ -41,6 +42,10 @@ def run_gpu(w: Workload, n_steps=None, device_io=True, wavelet=None, final=True,
             vel = vel.to(dev)
             rho = None if rho is None else rho.to(dev)
         api.sw_set_model(g, vel, rho)
+        if variant is not None:
+            api.sw_set_stencil_variant(g, variant)
+        if expect_variant is not None:
+            assert api.sw_get_stencil_variant(g) == expect_variant
         if wavelet is None:
             wavelet = api.sw_ricker(w.f_peak, w.t0, w.dt, max(n_steps, 1))
         api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wavelet, window_radius=w.window_radius)

@@ -56,6 +56,30 @@ def test_small_grids_all_orders(cuda_device, ndim, order, density):
     assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
 
 
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20])
+def test_3d_both_stencil_kernels(cuda_device, order):
+    """The TMA-pipelined kernel (chosen automatically for 3D constant density) and the
+    shared-memory-plane kernel both match the oracle."""
+    w = small_case(3, order, False, seed=100 + order)
+    s_ref, p_ref = run_oracle(w)
+    s_tma, p_tma = run_gpu(w, expect_variant=api.SW_STENCIL_TMA)
+    s_pl, p_pl = run_gpu(w, variant=api.SW_STENCIL_PLAIN, expect_variant=api.SW_STENCIL_PLAIN)
+    for s, p in ((s_tma, p_tma), (s_pl, p_pl)):
+        assert rel_l2(s, s_ref) <= FP32_SEIS_TOL
+        assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
+
+
+def test_tma_kernel_many_segments(cuda_device):
+    """A grid with more work items than CTAs of one tile: segments start and end at
+    every plane offset and cross tile boundaries (ragged in x, y and z)."""
+    w = workloads.make("3d_layered_256", shape=(29, 70, 97), n_steps=120)
+    s_ref, p_ref = run_oracle(w)
+    s, p = run_gpu(w, expect_variant=api.SW_STENCIL_TMA)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
+
+
 def test_host_and_device_buffers_agree(cuda_device):
     w = small_case(3, 8, True, seed=3, n_steps=30)
     s_dev, p_dev = run_gpu(w, device_io=True)
