@@ -283,8 +283,9 @@ EncodeTiledFn encode_tiled() {
 // Tile shape of the pipelined kernel per stencil radius (must match the
 // instantiations in launch_stencil_tma).
 void tma_tile(int R, int* tx, int* ty) {
-  *tx = 32;
-  *ty = (R <= 4) ? 32 : 16;
+  *tx = 64;
+  *ty = 16;
+  (void)R;
 }
 
 sw_status make_map(const sw_grid* g, float* base, uint32_t box_x, uint32_t box_y, CUtensorMap* map) {
@@ -296,7 +297,7 @@ sw_status make_map(const sw_grid* g, float* base, uint32_t box_x, uint32_t box_y
   cuuint32_t box[3] = {box_x, box_y, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(SW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
   return SW_OK;
@@ -317,10 +318,10 @@ sw_status build_tma_maps(sw_grid* g) {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
 
-template <int R, int TX, int TY, int PPT, int D, int NQ>
-void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
-  using C = TmaConfig<R, TX, TY, PPT, D, NQ>;
-  auto kern = stencil_tma_kernel<R, TX, TY, PPT, D, NQ>;
+template <int R, int TY, int PPT, int D, int NQ, int MINB, bool ISO>
+void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  using C = TmaConfig<R, TY, PPT, D, NQ>;
+  auto kern = stencil_tma_kernel<R, TY, PPT, D, NQ, MINB, ISO>;
   static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
   if (!blocks_per_sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
@@ -328,7 +329,7 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t 
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   TmaWork wk;
-  wk.tiles_x = (a.nx + TX - 1) / TX;
+  wk.tiles_x = (a.nx + C::TX - 1) / C::TX;
   const int tiles_y = (a.ny + TY - 1) / TY;
   wk.nz = a.nz;
   wk.total = (long long)wk.tiles_x * tiles_y * a.nz;
@@ -338,25 +339,36 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t 
                                                 g->dflag, kWaitLimitNs);
 }
 
+template <int R, int TY, int PPT, int D, int NQ, int MINB>
+void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  if (g->h[0] == g->h[1] && g->h[1] == g->h[2])
+    launch_tma_iso<R, TY, PPT, D, NQ, MINB, true>(g, a, buf, st);
+  else
+    launch_tma_iso<R, TY, PPT, D, NQ, MINB, false>(g, a, buf, st);
+}
+
+// Tile height / rows per warp / prefetch depth / q-ring depth / CTAs per SM for
+// each radius (tile width 64).  tma_tile() must give the same tile shape.
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   switch (g->R) {
-    case 1: launch_tma_t<1, 32, 32, 4, 3, 4>(g, a, buf, st); break;
-    case 2: launch_tma_t<2, 32, 32, 4, 3, 4>(g, a, buf, st); break;
-    case 3: launch_tma_t<3, 32, 32, 4, 3, 4>(g, a, buf, st); break;
-    case 4: launch_tma_t<4, 32, 32, 4, 3, 4>(g, a, buf, st); break;
-    case 5: launch_tma_t<5, 32, 16, 2, 3, 4>(g, a, buf, st); break;
-    case 6: launch_tma_t<6, 32, 16, 2, 3, 4>(g, a, buf, st); break;
-    case 7: launch_tma_t<7, 32, 16, 2, 3, 4>(g, a, buf, st); break;
-    case 8: launch_tma_t<8, 32, 16, 2, 3, 4>(g, a, buf, st); break;
-    case 9: launch_tma_t<9, 32, 16, 2, 3, 4>(g, a, buf, st); break;
-    case 10: launch_tma_t<10, 32, 16, 2, 3, 4>(g, a, buf, st); break;
+    case 1: launch_tma_t<1, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 2: launch_tma_t<2, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 3: launch_tma_t<3, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 4: launch_tma_t<4, 16, 2, 3, 4, 1>(g, a, buf, st); break;
+    case 5: launch_tma_t<5, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 6: launch_tma_t<6, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 7: launch_tma_t<7, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 8: launch_tma_t<8, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 9: launch_tma_t<9, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 10: launch_tma_t<10, 16, 4, 3, 4, 1>(g, a, buf, st); break;
     default: break;
   }
 }
 
 bool use_tma(const sw_grid* g) {
   if (g->variant == SW_STENCIL_PLAIN) return false;
-  return g->ndim == 3 && !g->has_density && g->tma_ready;
+  // the pipelined kernel keeps in-plane offsets in 32 bits
+  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31);
 }
 
 PointSet point_set(const sw_grid* g, bool src) {

@@ -10,11 +10,17 @@
 //     (cp.async.bulk.tensor.3d) into a ring of NP = R+1+D shared-memory slots,
 //     D+1 planes ahead of use; p[n-1] and kappa tiles come the same way into a
 //     second ring of NQ slots; each slot completes on its own mbarrier;
-//   - each thread keeps its column's 2R+1 planes of p[n] in a register queue,
-//     so a plane is read from shared memory once for z and once per in-plane
-//     neighbour;
-//   - one block barrier per plane releases the slots of the plane that left
-//     the window, after which one thread issues the next loads.
+//   - each thread keeps its columns' 2R+1 planes of p[n] in a register queue
+//     (shifted once per plane), so a plane is read from shared memory once for
+//     z and once per in-plane neighbour;
+//   - per-slot "empty" mbarriers, which each warp signals when it is done
+//     with a plane, gate the refills; only the issuing lane waits on them, so
+//     there is no block-wide barrier inside the loop;
+//   - each lane computes two adjacent columns with 64-bit shared loads and
+//     packed FP32x2 arithmetic (same operation order as the scalar kernel);
+//   - boundary work (Dirichlet nodes, face mirroring, ragged tails) only runs
+//     for nodes within R of a face, decided per lane, row and plane;
+//     per-segment and per-plane invariants are computed once.
 // Every mbarrier wait is bounded (wall clock); on timeout the CTA raises the
 // device error flag, drains its own outstanding copies with bounded waits and
 // exits.
@@ -68,190 +74,304 @@ struct SegCursor {
   }
 };
 
-template <int R, int TX, int TY, int PPT, int D, int NQ>
+template <int R, int TY, int PPT, int D, int NQ>
 struct TmaConfig {
+  static constexpr int TX = 64;               // 32 lanes x 2 adjacent columns
   static constexpr int XH = (R + 3) / 4 * 4;  // x halo rounded to 16 bytes (TMA x alignment)
   static constexpr int PW = TX + 2 * XH;
   static constexpr int PH = TY + 2 * R;
-  static constexpr int NP = R + 1 + D;
-  static constexpr int NT = TX * (TY / PPT);
+  static constexpr int NP = R + 1 + D;       // p[n] ring: R+1 live planes + D prefetched
+  static constexpr int NCW = TY / PPT;       // warps, PPT rows each
+  static constexpr int NT = 32 * NCW;
+  static constexpr int QL = 2 * R + 1;       // register z-queue length
+  static constexpr int H = (R + 1) / 2;      // float2 loads each side for the x neighbours
   static constexpr uint32_t P_BYTES = uint32_t(PH * PW) * 4u;  // bytes one p[n] box delivers
-  static constexpr uint32_t Q_BYTES = uint32_t(TY * TX) * 4u;   // bytes one p[n-1] / kappa box delivers
+  static constexpr uint32_t Q_BYTES = uint32_t(TY * TX) * 4u;  // bytes one p[n-1] / kappa box delivers
   // Slot strides are padded to 128 bytes: a tensor copy's shared-memory
   // destination must be 128-byte aligned.
   static constexpr int P_FLOATS = int((P_BYTES + 127u) / 128u * 128u) / 4;
   static constexpr int Q_FLOATS = int((Q_BYTES + 127u) / 128u * 128u) / 4;
-  static constexpr size_t SMEM = size_t(NP) * P_FLOATS * 4 + 2 * size_t(NQ) * Q_FLOATS * 4 + size_t(NP + NQ) * 8 + 16;
+  static constexpr size_t SMEM = size_t(NP) * P_FLOATS * 4 + 2 * size_t(NQ) * Q_FLOATS * 4 +
+                                 size_t(2 * NP + 2 * NQ) * 8 + 16 + 128;  // + abort flag, producer state
   static_assert((P_FLOATS * 4) % 128 == 0 && (Q_FLOATS * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
-  static_assert(TX % 32 == 0 && kTileXMax % TX == 0 && kTileYMax % TY == 0 && TY % PPT == 0, "tile shape");
-  static_assert(PW <= 256 && PH <= 256, "TMA box extent");
+  static_assert(kTileXMax % TX == 0 && kTileYMax % TY == 0 && TY % PPT == 0, "tile shape");
+  static_assert(PW <= 256 && PH <= 256 && XH % 2 == 0, "TMA box extent / float2 alignment");
 };
 
-template <int R, int TX, int TY, int PPT, int D, int NQ>
-__global__ void __launch_bounds__(TX*(TY / PPT)) stencil_tma_kernel(const __grid_constant__ CUtensorMap map_p,
-                                                                     const __grid_constant__ CUtensorMap map_q,
-                                                                     const __grid_constant__ CUtensorMap map_k,
-                                                                     const StencilArgs a, const TmaWork wk,
-                                                                     int* err_flag, unsigned long long limit_ns) {
-  using C = TmaConfig<R, TX, TY, PPT, D, NQ>;
+// Boundary work for one node of a tile that touches a face: Dirichlet face
+// nodes are held at zero, the node itself is stored, and its mirror images go
+// into the ghost layers of p[n+1].
+template <int R>
+__device__ __forceinline__ void store_near_face(const StencilArgs& a, int64_t idx, int x, int y, int z, float v) {
+  if (x >= a.nx || y >= a.ny) return;
+  const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
+                   (y == 0 && a.bc[2] == kBcDirichlet) || (y == a.ny - 1 && a.bc[3] == kBcDirichlet) ||
+                   (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet);
+  if (dir) v = 0.f;
+  a.pnm1[idx] = v;
+  mirror_ghosts<R>(a.pnm1, idx, z, a.nz, a.sz, a.bc[0], a.bc[1], v);
+  mirror_ghosts<R>(a.pnm1, idx, y, a.ny, a.sy, a.bc[2], a.bc[3], v);
+  mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], v);
+}
+
+// Warp w owns tile rows w*PPT..w*PPT+PPT-1; lane l owns columns 2l and 2l+1,
+// handled as a float2 with packed FP32x2 arithmetic.  Lane 0 of the last warp
+// also issues every tensor copy.
+// Ring protocol per slot: full[s] (1 arrival + transaction bytes) completes when
+// a copy lands; empty[s] (NCW arrivals) completes when every consumer warp has
+// finished with the plane in it.  p[n] plane index m is used by a consumer
+// warp as the queue front at its iteration m and as the in-plane centre at
+// iteration m+R, so the warp releases index m-R at the end of iteration m.
+// Producer bookkeeping, kept in shared memory because one lane uses it.
+struct ProducerState {
+  SegCursor cp, cq;
+  long long kp, kq;  // copies issued into each ring
+};
+
+// ISO: all three spacings are equal, so one coefficient per j serves every
+// axis (fewer registers; same arithmetic).
+template <int R, int TY, int PPT, int D, int NQ, int MINB, bool ISO>
+__global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
+    stencil_tma_kernel(const __grid_constant__ CUtensorMap map_p, const __grid_constant__ CUtensorMap map_q,
+                       const __grid_constant__ CUtensorMap map_k, const StencilArgs a, const TmaWork wk,
+                       int* err_flag, unsigned long long limit_ns) {
+  using C = TmaConfig<R, TY, PPT, D, NQ>;
+  constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW;
   extern __shared__ __align__(128) unsigned char smem[];
   float* sp = reinterpret_cast<float*>(smem);
   float* sq = sp + C::NP * C::P_FLOATS;
   float* sk = sq + NQ * C::Q_FLOATS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sk + NQ * C::Q_FLOATS);
-  int* s_abort = reinterpret_cast<int*>(bars + C::NP + NQ);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * C::NP + 2 * NQ);
+  ProducerState* st = reinterpret_cast<ProducerState*>(bars + 2 * C::NP + 2 * NQ + 2);
 
-  const int tid = threadIdx.x;
-  const int tx = tid % TX;
-  const int ty = tid / TX;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const long long u0 = wk.total * blockIdx.x / gridDim.x;
   const long long u1 = wk.total * (blockIdx.x + 1) / gridDim.x;
   if (u0 >= u1) return;
   if (smem_addr(smem) & 127u) {  // tensor copies need 128-byte aligned destinations
-    if (tid == 0) atomicOr(err_flag, 2);
+    if (threadIdx.x == 0) atomicOr(err_flag, 2);
     return;
   }
-
-  const uint32_t bar_p0 = smem_addr(bars);
-  const uint32_t bar_q0 = smem_addr(bars + C::NP);
-  SegCursor cp, cq;  // producer cursors (meaningful in thread 0 only)
-  long long p_issued = 0, q_issued = 0;
-
-  auto issue_p = [&]() {
-    const int t = cp.tile();
-    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
-    const int z = cp.zb() - R + cp.j;
-    const int slot = int(p_issued % C::NP);
-    const uint32_t bar = bar_p0 + 8u * slot;
-    mbar_arrive_expect_tx(bar, C::P_BYTES);
-    tma_load_3d(smem_addr(sp + slot * C::P_FLOATS), &map_p, x0 + kXOff - C::XH, y0, z + R, bar);
-    ++p_issued;
-    cp.advance();
-  };
-  auto issue_q = [&]() {
-    const int t = cq.tile();
-    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
-    const int z = cq.zb() + cq.j;
-    const int slot = int(q_issued % NQ);
-    const uint32_t bar = bar_q0 + 8u * slot;
-    mbar_arrive_expect_tx(bar, 2u * C::Q_BYTES);
-    tma_load_3d(smem_addr(sq + slot * C::Q_FLOATS), &map_q, x0 + kXOff, y0 + R, z + R, bar);
-    tma_load_3d(smem_addr(sk + slot * C::Q_FLOATS), &map_k, x0 + kXOff, y0 + R, z + R, bar);
-    ++q_issued;
-    cq.advance();
-  };
-
-  if (tid == 0) {
-    *s_abort = 0;
-    for (int i = 0; i < C::NP; ++i) mbar_init(bar_p0 + 8u * i, 1);
-    for (int i = 0; i < NQ; ++i) mbar_init(bar_q0 + 8u * i, 1);
+  const uint32_t full_p = smem_addr(bars);
+  const uint32_t empty_p = full_p + 8u * C::NP;
+  const uint32_t full_q = empty_p + 8u * C::NP;
+  const uint32_t empty_q = full_q + 8u * NQ;
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    for (int i = 0; i < C::NP; ++i) {
+      mbar_init(full_p + 8u * i, 1);
+      mbar_init(empty_p + 8u * i, C::NCW);
+    }
+    for (int i = 0; i < NQ; ++i) {
+      mbar_init(full_q + 8u * i, 1);
+      mbar_init(empty_q + 8u * i, C::NCW);
+    }
     fence_barrier_init();
-    prefetch_tensormap(&map_p);
-    prefetch_tensormap(&map_q);
-    prefetch_tensormap(&map_k);
-    cp.init(u0, u1, wk.nz, 2 * R);
-    cq.init(u0, u1, wk.nz, 0);
-    for (int i = 0; i <= D && cp.valid(); ++i) issue_p();
-    for (int i = 0; i < NQ && cq.valid(); ++i) issue_q();
   }
   __syncthreads();
 
-  volatile int* abort_flag = s_abort;
-  float q[PPT][2 * R + 1];
-  long long m = 0, qi = 0;  // planes consumed from each ring
+  // The last warp's lane 0 is also the producer: it issues the first copies
+  // up front and then, at the end of each of its iterations, the copy into the
+  // slot every warp has just released (waiting on that slot's "empty"
+  // barrier).  The other warps never wait for it except through data: they
+  // can run up to D planes ahead.
+  const bool producer = (warp == C::NCW - 1) && lane == 0;
+  // issue the next p[n] copy; false if a bounded wait gave up
+  auto issue_p = [&]() -> bool {
+    const long long k = st->kp;
+    const int slot = int(k % C::NP);
+    if (k >= C::NP && !mbar_wait_bounded(empty_p + 8u * slot, uint32_t(((k / C::NP) - 1) & 1), limit_ns))
+      return false;
+    const int t = st->cp.tile();
+    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
+    const uint32_t bar = full_p + 8u * slot;
+    mbar_arrive_expect_tx(bar, C::P_BYTES);
+    tma_load_3d(smem_addr(sp + slot * C::P_FLOATS), &map_p, x0 + kXOff - C::XH, y0, st->cp.zb() + st->cp.j, bar);
+    st->kp = k + 1;
+    st->cp.advance();
+    return true;
+  };
+  auto issue_q = [&]() -> bool {
+    const long long k = st->kq;
+    const int slot = int(k % NQ);
+    if (k >= NQ && !mbar_wait_bounded(empty_q + 8u * slot, uint32_t(((k / NQ) - 1) & 1), limit_ns)) return false;
+    const int t = st->cq.tile();
+    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
+    const int z = st->cq.zb() + st->cq.j;
+    const uint32_t bar = full_q + 8u * slot;
+    mbar_arrive_expect_tx(bar, 2u * C::Q_BYTES);
+    tma_load_3d(smem_addr(sq + slot * C::Q_FLOATS), &map_q, x0 + kXOff, y0 + R, z + R, bar);
+    tma_load_3d(smem_addr(sk + slot * C::Q_FLOATS), &map_k, x0 + kXOff, y0 + R, z + R, bar);
+    st->kq = k + 1;
+    st->cq.advance();
+    return true;
+  };
+  // on a failed wait: raise the flags and let this CTA's issued copies land
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(err_flag, 1);
+    if (producer) {
+      const long long kp = st->kp, kq = st->kq;
+      for (long long i = (kp > C::NP ? kp - C::NP : 0); i < kp; ++i)
+        mbar_wait_bounded(full_p + 8u * int(i % C::NP), uint32_t((i / C::NP) & 1), limit_ns);
+      for (long long i = (kq > NQ ? kq - NQ : 0); i < kq; ++i)
+        mbar_wait_bounded(full_q + 8u * int(i % NQ), uint32_t((i / NQ) & 1), limit_ns);
+    }
+  };
+  if (producer) {
+    prefetch_tensormap(&map_p);
+    prefetch_tensormap(&map_q);
+    prefetch_tensormap(&map_k);
+    st->cp.init(u0, u1, wk.nz, 2 * R);
+    st->cq.init(u0, u1, wk.nz, 0);
+    st->kp = 0;
+    st->kq = 0;
+    for (int i = 0; i <= D && st->cp.valid(); ++i) issue_p();  // slots still free: no waits
+    for (int i = 0; i < NQ && st->cq.valid(); ++i) issue_q();
+  }
+
+  // --------------------------------------------------------------- consumers
+  float2 cz2[R + 1], cy2[R + 1], cx2[R + 1];  // coefficient pairs (ISO: one set)
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    cx2[j] = make_float2(a.cx[j], a.cx[j]);
+    cy2[j] = ISO ? cx2[j] : make_float2(a.cy[j], a.cy[j]);
+    cz2[j] = ISO ? cx2[j] : make_float2(a.cz[j], a.cz[j]);
+  }
+  const int r0 = warp * PPT;  // first tile row of this warp
+  float2 qz[PPT][QL];         // z-queue, shifted once per plane
+  // ring positions (32-bit): front slot and phase, centre slot, q slot and phase
+  int ps = 0, cs = C::NP - R;
+  uint32_t pph = 0;
+  int qs = 0;
+  uint32_t qph = 0;
+  int consumed = 0;  // p[n] planes consumed, saturating at R
   long long u = u0;
-  bool aborted = false;
-  while (u < u1 && !aborted) {
+  while (u < u1) {
     const int t = int(u / wk.nz);
     const int zb = int(u % wk.nz);
     const int len = int((u1 - u) < (long long)(wk.nz - zb) ? (u1 - u) : (long long)(wk.nz - zb));
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
-    const int x = x0 + tx;
-    for (int j = 0; j < len + 2 * R; ++j) {
+    const int x = x0 + 2 * lane;
+    // per-segment invariants; "near" = within R of a face (or past the last
+    // node), where Dirichlet zeroing, ghost mirroring or a tail check applies
+    const bool near_x = x <= R || x + 1 >= a.nx - 1 - R;
+    const int dxa = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
+    const int dxb = layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]);
+    int d2xy_a[PPT], d2xy_b[PPT];
+    int rowoff[PPT];  // in-plane offsets fit 32 bits (checked on the host)
+    unsigned near_rows = 0;  // bit i: row i is near a y face (or x is near an x face)
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int y = y0 + r0 + i;
+      const int dyl = layer_distance(y, a.ny, a.nbl[2], a.nbl[3]);
+      d2xy_a[i] = dyl * dyl + dxa * dxa;
+      d2xy_b[i] = dyl * dyl + dxb * dxb;
+      rowoff[i] = y * int(a.sy) + x;
+      if (near_x || y <= R || y >= a.ny - 1 - R) near_rows |= 1u << i;
+    }
+    const int nplanes = len + 2 * R;
+    for (int j = 0; j < nplanes; ++j) {
+      if (*abort_flag) return;
       const bool compute = j >= 2 * R;
-      const int slot = int(m % C::NP);
-      bool ok = mbar_wait_bounded(bar_p0 + 8u * slot, uint32_t((m / C::NP) & 1), limit_ns);
-      if (ok && compute) ok = mbar_wait_bounded(bar_q0 + 8u * int(qi % NQ), uint32_t((qi / NQ) & 1), limit_ns);
+      bool ok = mbar_wait_bounded(full_p + 8u * ps, pph, limit_ns);
+      if (ok && compute) ok = mbar_wait_bounded(full_q + 8u * qs, qph, limit_ns);
       if (!ok) {
-        *abort_flag = 1;
-      } else {
-        const float* P = sp + slot * C::P_FLOATS;
+        give_up();
+        return;
+      }
+      {
+        const float* P = sp + ps * C::P_FLOATS + (r0 + R) * PW + C::XH + 2 * lane;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
 #pragma unroll
-          for (int k = 0; k < 2 * R; ++k) q[i][k] = q[i][k + 1];
-          q[i][2 * R] = P[(ty * PPT + i + R) * C::PW + tx + C::XH];
+          for (int kk = 0; kk < QL - 1; ++kk) qz[i][kk] = qz[i][kk + 1];
+          qz[i][QL - 1] = *reinterpret_cast<const float2*>(P + i * PW);
         }
-        if (compute) {
-          const int z = zb + j - 2 * R;
-          const float* Pc = sp + int((m - R) % C::NP) * C::P_FLOATS;
-          const float* Qs = sq + int(qi % NQ) * C::Q_FLOATS;
-          const float* Ks = sk + int(qi % NQ) * C::Q_FLOATS;
-          const int64_t zoff = int64_t(z) * a.sz;
-          const int dz = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
-          const int dx = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
+      }
+      if (compute) {
+        const int z = zb + j - 2 * R;
+        const float* c0 = sp + cs * C::P_FLOATS + (r0 + R) * PW + C::XH + 2 * lane;
+        const float2* Qs = reinterpret_cast<const float2*>(sq + qs * C::Q_FLOATS + r0 * TX + 2 * lane);
+        const float2* Ks = reinterpret_cast<const float2*>(sk + qs * C::Q_FLOATS + r0 * TX + 2 * lane);
+        float* plane = a.pnm1 + int64_t(z) * a.sz;
+        const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+        const int dz2 = dzl * dzl;
+        const unsigned near = (z <= R || z >= a.nz - 1 - R) ? ~0u : near_rows;
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) {
-            const int row = ty * PPT + i;
-            const float* c = Pc + (row + R) * C::PW + tx + C::XH;  // centre node in the slot
-            const float pc = q[i][R];
-            const float p2 = 2.f * pc;
-            float lap = 0.f;
+        for (int i = 0; i < PPT; ++i) {
+          const float* c = c0 + i * PW;
+          float2 w[2 * H + 1];  // columns x-2H .. x+1+2H of this row, as pairs
 #pragma unroll
-            for (int jj = 1; jj <= R; ++jj) {
-              lap = fmaf(a.cz[jj], (q[i][R + jj] + q[i][R - jj]) - p2, lap);
-              lap = fmaf(a.cx[jj], (c[jj] + c[-jj]) - p2, lap);
-              lap = fmaf(a.cy[jj], (c[jj * C::PW] + c[-jj * C::PW]) - p2, lap);
+          for (int mm = -H; mm <= H; ++mm) w[mm + H] = *reinterpret_cast<const float2*>(c + 2 * mm);
+          const float2 pc = qz[i][R];
+          const float2 p2 = f2_add(pc, pc);
+          float2 lap = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int jj = 1; jj <= R; ++jj) {
+            lap = f2_fma(cz2[jj], f2_sub(f2_add(qz[i][R + jj], qz[i][R - jj]), p2), lap);
+            float2 xp, xm;  // x+jj and x-jj neighbours of both columns
+            if (jj % 2 == 0) {
+              xp = w[H + jj / 2];
+              xm = w[H - jj / 2];
+            } else {
+              xp = make_float2(w[H + (jj - 1) / 2].y, w[H + (jj + 1) / 2].x);
+              xm = make_float2(w[H - (jj + 1) / 2].y, w[H - (jj - 1) / 2].x);
             }
-            const float po = Qs[row * TX + tx];
-            const float kp = Ks[row * TX + tx];
-            const int y = y0 + row;
-            if (x < a.nx && y < a.ny) {
-              const int dy = layer_distance(y, a.ny, a.nbl[2], a.nbl[3]);
-              const int d2 = dz * dz + dy * dy + dx * dx;
-              float ca = 1.f, e = 0.f;
-              if (d2 != 0) {
-                const float2 cc = __ldg(&a.damp[d2]);
-                ca = cc.x;
-                e = cc.y;
-              }
-              const float dp = pc - po;
-              float pnew = ca * (pc + fmaf(kp, lap, fmaf(e, po, dp)));
-              const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
-                               (y == 0 && a.bc[2] == kBcDirichlet) || (y == a.ny - 1 && a.bc[3] == kBcDirichlet) ||
-                               (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet);
-              if (dir) pnew = 0.f;
-              const int64_t idx = zoff + int64_t(y) * a.sy + x;
-              a.pnm1[idx] = pnew;
-              mirror_ghosts<R>(a.pnm1, idx, z, a.nz, a.sz, a.bc[0], a.bc[1], pnew);
-              mirror_ghosts<R>(a.pnm1, idx, y, a.ny, a.sy, a.bc[2], a.bc[3], pnew);
-              mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
-            }
+            lap = f2_fma(cx2[jj], f2_sub(f2_add(xp, xm), p2), lap);
+            const float2 ys = f2_add(*reinterpret_cast<const float2*>(c + jj * PW),
+                                     *reinterpret_cast<const float2*>(c - jj * PW));
+            lap = f2_fma(cy2[jj], f2_sub(ys, p2), lap);
+          }
+          const float2 po = Qs[i * (TX / 2)];
+          const float2 kp = Ks[i * (TX / 2)];
+          // damping coefficients (entry 0 of the table is (1, 0): no branch needed)
+          const float2 da = __ldg(&a.damp[dz2 + d2xy_a[i]]);
+          const float2 db = __ldg(&a.damp[dz2 + d2xy_b[i]]);
+          const float2 ca = make_float2(da.x, db.x), e = make_float2(da.y, db.y);
+          // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
+          const float2 pnew = f2_mul(ca, f2_add(pc, f2_fma(kp, lap, f2_fma(e, po, f2_sub(pc, po)))));
+          if (!(near & (1u << i))) {
+            *reinterpret_cast<float2*>(plane + rowoff[i]) = pnew;
+          } else {
+            const int y = y0 + r0 + i;
+            const int64_t idx = int64_t(z) * a.sz + rowoff[i];
+            store_near_face<R>(a, idx, x, y, z, pnew.x);
+            store_near_face<R>(a, idx + 1, x + 1, y, z, pnew.y);
           }
         }
       }
-      __syncthreads();  // slot m-R of the p ring and slot qi of the q ring are free
-      if (*abort_flag) {
-        aborted = true;
-        break;
+      __syncwarp();
+      if (lane == 0) {
+        if (consumed >= R) mbar_arrive(empty_p + 8u * cs);
+        if (compute) mbar_arrive(empty_q + 8u * qs);
       }
-      if (compute) ++qi;
-      ++m;
-      if (tid == 0) {
-        if (cp.valid()) issue_p();
-        if (compute && cq.valid()) issue_q();
+      if (producer) {
+        bool fine = true;
+        if (st->cp.valid()) fine = issue_p();
+        if (fine && compute && st->cq.valid()) fine = issue_q();
+        if (!fine) {
+          give_up();
+          return;
+        }
+      }
+      // advance ring positions
+      if (++ps == C::NP) {
+        ps = 0;
+        pph ^= 1u;
+      }
+      if (++cs == C::NP) cs = 0;  // centre slot tracks index m-R every iteration
+      if (consumed < R) ++consumed;
+      if (compute) {
+        if (++qs == NQ) {
+          qs = 0;
+          qph ^= 1u;
+        }
       }
     }
     u += len;
-  }
-
-  if (aborted && tid == 0) {
-    atomicOr(err_flag, 1);
-    // drain this CTA's outstanding copies (bounded) before its shared memory goes away
-    for (long long k = m; k < p_issued; ++k)
-      mbar_wait_bounded(bar_p0 + 8u * int(k % C::NP), uint32_t((k / C::NP) & 1), limit_ns);
-    for (long long k = qi; k < q_issued; ++k)
-      mbar_wait_bounded(bar_q0 + 8u * int(k % NQ), uint32_t((k / NQ) & 1), limit_ns);
   }
 }
 
