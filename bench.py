@@ -53,7 +53,7 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("stencil_plain.cuh",):
+    for name in ("stencil_plain.cuh", "stencil_tma.cuh", "tma.cuh", "layout.h"):
         with open(os.path.join(ROOT, "paper_2201_05278_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
