@@ -17,7 +17,7 @@
 //     with a plane, gate the refills; only the issuing lane waits on them, so
 //     there is no block-wide barrier inside the loop;
 //   - each lane computes two adjacent columns with 64-bit shared loads and
-//     packed FP32x2 arithmetic (same operation order as the scalar kernel);
+//     packed FP32x2 arithmetic, the Laplacian in three per-axis chains;
 //   - boundary work (Dirichlet nodes, face mirroring, ragged tails) only runs
 //     for nodes within R of a face, decided per lane, row and plane;
 //     per-segment and per-plane invariants are computed once.
@@ -122,6 +122,32 @@ __device__ __forceinline__ void store_near_face(const StencilArgs& a, int64_t id
 // finished with the plane in it.  p[n] plane index m is used by a consumer
 // warp as the queue front at its iteration m and as the in-plane centre at
 // iteration m+R, so the warp releases index m-R at the end of iteration m.
+// Face treatment of node index i along one axis of length n: whether it is a
+// Dirichlet face node (held at zero) and where its mirror image goes in the
+// ghost layer (offset in nodes along the axis, 0 = none) with which sign.
+// Assumes n > 2R+1, so a node is within R of at most one face.
+struct FaceTreat {
+  bool zero;
+  int mirror;
+  float sign;
+};
+
+template <int R>
+__device__ __forceinline__ FaceTreat face_treat(int i, int n, int bc_lo, int bc_hi) {
+  FaceTreat f;
+  f.zero = (i == 0 && bc_lo == kBcDirichlet) || (i == n - 1 && bc_hi == kBcDirichlet);
+  f.mirror = 0;
+  f.sign = 1.f;
+  if (bc_lo != kBcNone && i >= 1 && i <= R) {
+    f.mirror = -2 * i;
+    f.sign = (bc_lo == kBcDirichlet) ? -1.f : 1.f;
+  } else if (bc_hi != kBcNone && n - 1 - i >= 1 && n - 1 - i <= R) {
+    f.mirror = 2 * (n - 1 - i);
+    f.sign = (bc_hi == kBcDirichlet) ? -1.f : 1.f;
+  }
+  return f;
+}
+
 // Producer bookkeeping, kept in shared memory because one lane uses it.
 struct ProducerState {
   SegCursor cp, cq;
@@ -255,14 +281,20 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
     const int len = int((u1 - u) < (long long)(wk.nz - zb) ? (u1 - u) : (long long)(wk.nz - zb));
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
     const int x = x0 + 2 * lane;
-    // per-segment invariants; "near" = within R of a face (or past the last
-    // node), where Dirichlet zeroing, ghost mirroring or a tail check applies
-    const bool near_x = x <= R || x + 1 >= a.nx - 1 - R;
+    // per-segment invariants; a node is "near" when it is a Dirichlet face
+    // node, has a ghost mirror image, or lies past the last node (ragged tile)
+    const bool small = a.nx <= 2 * R + 1 || a.ny <= 2 * R + 1 || a.nz <= 2 * R + 1;
+    const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;
+    const FaceTreat fxa = face_treat<R>(x, a.nx, a.bc[4], a.bc[5]);
+    const FaceTreat fxb = face_treat<R>(x + 1, a.nx, a.bc[4], a.bc[5]);
+    const bool lane_near = !va_ok || !vb_ok || fxa.zero || fxb.zero || fxa.mirror || fxb.mirror;
+    bool seg_near = small || __any_sync(0xffffffffu, lane_near);
     const int dxa = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
     const int dxb = layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]);
     int d2xy_a[PPT], d2xy_b[PPT];
     int rowoff[PPT];  // in-plane offsets fit 32 bits (checked on the host)
-    unsigned near_rows = 0;  // bit i: row i is near a y face (or x is near an x face)
+    FaceTreat fy[PPT];
+    bool row_ok[PPT];
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int y = y0 + r0 + i;
@@ -270,7 +302,9 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
       d2xy_a[i] = dyl * dyl + dxa * dxa;
       d2xy_b[i] = dyl * dyl + dxb * dxb;
       rowoff[i] = y * int(a.sy) + x;
-      if (near_x || y <= R || y >= a.ny - 1 - R) near_rows |= 1u << i;
+      fy[i] = face_treat<R>(y, a.ny, a.bc[2], a.bc[3]);
+      row_ok[i] = y < a.ny;
+      seg_near = seg_near || !row_ok[i] || fy[i].zero || fy[i].mirror != 0;  // warp-uniform
     }
     const int nplanes = len + 2 * R;
     for (int j = 0; j < nplanes; ++j) {
@@ -299,7 +333,8 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
         float* plane = a.pnm1 + int64_t(z) * a.sz;
         const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
         const int dz2 = dzl * dzl;
-        const unsigned near = (z <= R || z >= a.nz - 1 - R) ? ~0u : near_rows;
+        const FaceTreat fz = face_treat<R>(z, a.nz, a.bc[0], a.bc[1]);
+        const bool near = seg_near || fz.zero || fz.mirror != 0;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
           const float* c = c0 + i * PW;
@@ -308,23 +343,24 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
           for (int mm = -H; mm <= H; ++mm) w[mm + H] = *reinterpret_cast<const float2*>(c + 2 * mm);
           const float2 pc = qz[i][R];
           const float2 p2 = f2_add(pc, pc);
-          float2 lap = make_float2(0.f, 0.f);
+          // three independent accumulation chains (one per axis) for latency
+          float2 lz = make_float2(0.f, 0.f), lx = lz, ly = lz;
 #pragma unroll
           for (int jj = 1; jj <= R; ++jj) {
-            lap = f2_fma(cz2[jj], f2_sub(f2_add(qz[i][R + jj], qz[i][R - jj]), p2), lap);
-            float2 xp, xm;  // x+jj and x-jj neighbours of both columns
+            lz = f2_fma(cz2[jj], f2_sub(f2_add(qz[i][R + jj], qz[i][R - jj]), p2), lz);
+            float2 xs;  // (x+jj) + (x-jj) for both columns
             if (jj % 2 == 0) {
-              xp = w[H + jj / 2];
-              xm = w[H - jj / 2];
-            } else {
-              xp = make_float2(w[H + (jj - 1) / 2].y, w[H + (jj + 1) / 2].x);
-              xm = make_float2(w[H - (jj + 1) / 2].y, w[H - (jj - 1) / 2].x);
+              xs = f2_add(w[H + jj / 2], w[H - jj / 2]);
+            } else {  // odd offsets straddle the pairs: two scalar adds into one pair
+              xs = make_float2(w[H + (jj - 1) / 2].y + w[H - (jj + 1) / 2].y,
+                               w[H + (jj + 1) / 2].x + w[H - (jj - 1) / 2].x);
             }
-            lap = f2_fma(cx2[jj], f2_sub(f2_add(xp, xm), p2), lap);
+            lx = f2_fma(cx2[jj], f2_sub(xs, p2), lx);
             const float2 ys = f2_add(*reinterpret_cast<const float2*>(c + jj * PW),
                                      *reinterpret_cast<const float2*>(c - jj * PW));
-            lap = f2_fma(cy2[jj], f2_sub(ys, p2), lap);
+            ly = f2_fma(cy2[jj], f2_sub(ys, p2), ly);
           }
+          const float2 lap = f2_add(f2_add(lz, lx), ly);
           const float2 po = Qs[i * (TX / 2)];
           const float2 kp = Ks[i * (TX / 2)];
           // damping coefficients (entry 0 of the table is (1, 0): no branch needed)
@@ -333,13 +369,36 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, D, NQ>::NT)
           const float2 ca = make_float2(da.x, db.x), e = make_float2(da.y, db.y);
           // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
           const float2 pnew = f2_mul(ca, f2_add(pc, f2_fma(kp, lap, f2_fma(e, po, f2_sub(pc, po)))));
-          if (!(near & (1u << i))) {
-            *reinterpret_cast<float2*>(plane + rowoff[i]) = pnew;
-          } else {
+          float* dst = plane + rowoff[i];
+          if (!near) {
+            *reinterpret_cast<float2*>(dst) = pnew;
+          } else if (small) {
             const int y = y0 + r0 + i;
             const int64_t idx = int64_t(z) * a.sz + rowoff[i];
             store_near_face<R>(a, idx, x, y, z, pnew.x);
             store_near_face<R>(a, idx + 1, x + 1, y, z, pnew.y);
+          } else if (row_ok[i]) {
+            // Dirichlet face nodes are held at zero; mirror images go to the ghosts
+            const bool zrow = fz.zero || fy[i].zero;
+            const float va = (zrow || fxa.zero) ? 0.f : pnew.x;
+            const float vb = (zrow || fxb.zero) ? 0.f : pnew.y;
+            if (va_ok && vb_ok) {
+              *reinterpret_cast<float2*>(dst) = make_float2(va, vb);
+            } else if (va_ok) {
+              dst[0] = va;
+            }
+            if (va_ok && fxa.mirror) dst[fxa.mirror] = fxa.sign * va;
+            if (vb_ok && fxb.mirror) dst[1 + fxb.mirror] = fxb.sign * vb;
+            if (fy[i].mirror) {
+              float* g = dst + fy[i].mirror * int(a.sy);
+              if (va_ok) g[0] = fy[i].sign * va;
+              if (vb_ok) g[1] = fy[i].sign * vb;
+            }
+            if (fz.mirror) {
+              float* g = dst + int64_t(fz.mirror) * a.sz;
+              if (va_ok) g[0] = fz.sign * va;
+              if (vb_ok) g[1] = fz.sign * vb;
+            }
           }
         }
       }
