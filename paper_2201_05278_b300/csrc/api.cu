@@ -318,10 +318,10 @@ sw_status build_tma_maps(sw_grid* g) {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
 
-template <int R, int TY, int PPT, int D, int NQ, int MINB, bool ISO>
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO>
 void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
-  using C = TmaConfig<R, TY, PPT, D, NQ>;
-  auto kern = stencil_tma_kernel<R, TY, PPT, D, NQ, MINB, ISO>;
+  using C = TmaConfig<R, TY, PPT, NB>;
+  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO>;
   static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
   if (!blocks_per_sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
@@ -335,32 +335,32 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   wk.total = (long long)wk.tiles_x * tiles_y * a.nz;
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
-  kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf ^ 1], g->map_kappa, a, wk,
-                                                g->dflag, kWaitLimitNs);
+  kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf], g->map_inner[buf ^ 1],
+                                                g->map_kappa, a, wk, g->dflag, kWaitLimitNs);
 }
 
-template <int R, int TY, int PPT, int D, int NQ, int MINB>
+template <int R, int TY, int PPT, int NB, int MINB>
 void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   if (g->h[0] == g->h[1] && g->h[1] == g->h[2])
-    launch_tma_iso<R, TY, PPT, D, NQ, MINB, true>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, true>(g, a, buf, st);
   else
-    launch_tma_iso<R, TY, PPT, D, NQ, MINB, false>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, false>(g, a, buf, st);
 }
 
-// Tile height / rows per warp / prefetch depth / q-ring depth / CTAs per SM for
-// each radius (tile width 64).  tma_tile() must give the same tile shape.
+// Tile height / rows per warp / ring depth / minimum CTAs per SM for each
+// radius (tile width 64).  tma_tile() must give the same tile shape.
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   switch (g->R) {
-    case 1: launch_tma_t<1, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 2: launch_tma_t<2, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 3: launch_tma_t<3, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 4: launch_tma_t<4, 16, 2, 3, 4, 1>(g, a, buf, st); break;
-    case 5: launch_tma_t<5, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 6: launch_tma_t<6, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 7: launch_tma_t<7, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 8: launch_tma_t<8, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 9: launch_tma_t<9, 16, 4, 3, 4, 1>(g, a, buf, st); break;
-    case 10: launch_tma_t<10, 16, 4, 3, 4, 1>(g, a, buf, st); break;
+    case 1: launch_tma_t<1, 16, 2, 5, 2>(g, a, buf, st); break;
+    case 2: launch_tma_t<2, 16, 2, 5, 2>(g, a, buf, st); break;
+    case 3: launch_tma_t<3, 16, 2, 5, 2>(g, a, buf, st); break;
+    case 4: launch_tma_t<4, 16, 2, 5, 2>(g, a, buf, st); break;
+    case 5: launch_tma_t<5, 16, 2, 4, 2>(g, a, buf, st); break;
+    case 6: launch_tma_t<6, 16, 2, 4, 2>(g, a, buf, st); break;
+    case 7: launch_tma_t<7, 16, 2, 4, 1>(g, a, buf, st); break;
+    case 8: launch_tma_t<8, 16, 2, 4, 1>(g, a, buf, st); break;
+    case 9: launch_tma_t<9, 16, 2, 4, 1>(g, a, buf, st); break;
+    case 10: launch_tma_t<10, 16, 2, 4, 1>(g, a, buf, st); break;
     default: break;
   }
 }
@@ -368,7 +368,10 @@ void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStr
 bool use_tma(const sw_grid* g) {
   if (g->variant == SW_STENCIL_PLAIN) return false;
   // the pipelined kernel keeps in-plane offsets in 32 bits
-  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31);
+  // and assumes every node is within R of at most one face per axis
+  const int64_t m = 2 * int64_t(g->R) + 1;
+  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && g->lay.n[0] > m &&
+         g->lay.n[1] > m && g->lay.n[2] > m;
 }
 
 PointSet point_set(const sw_grid* g, bool src) {
