@@ -332,7 +332,7 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   wk.tiles_x = (a.nx + C::TX - 1) / C::TX;
   const int tiles_y = (a.ny + TY - 1) / TY;
   wk.nz = a.nz;
-  wk.total = (long long)wk.tiles_x * tiles_y * a.nz;
+  wk.total = wk.tiles_x * tiles_y * a.nz;  // < 2^31: checked in use_tma
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf], g->map_inner[buf ^ 1],
@@ -369,9 +369,11 @@ bool use_tma(const sw_grid* g) {
   if (g->variant == SW_STENCIL_PLAIN) return false;
   // the pipelined kernel keeps in-plane offsets in 32 bits
   // and assumes every node is within R of at most one face per axis
+  // and counts its (64 x 16 tile, plane) work items in 32 bits
   const int64_t m = 2 * int64_t(g->R) + 1;
+  const int64_t items = (g->lay.n[2] + 63) / 64 * ((g->lay.n[1] + 15) / 16) * g->lay.n[0];
   return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && g->lay.n[0] > m &&
-         g->lay.n[1] > m && g->lay.n[2] > m;
+         g->lay.n[1] > m && g->lay.n[2] > m && items < (int64_t(1) << 31);
 }
 
 PointSet point_set(const sw_grid* g, bool src) {

@@ -40,42 +40,15 @@
 namespace sw {
 
 struct TmaWork {
-  int tiles_x;       // tiles along x
-  int nz;            // planes per tile column
-  long long total;   // tiles * nz work items
+  int tiles_x;  // tiles along x
+  int nz;       // planes per tile column
+  int total;    // tiles * nz work items (fits 32 bits: checked on the host)
 };
 
-// Walks the bundles of one CTA's work range: per segment (the part of one
-// tile column inside the range) 2R warm-up bundles, then one per plane.
-// Bundle j of the segment starting at plane zb carries front plane
-// zb - R + j and, for j >= 2R, computes plane zb + j - 2R.
-template <int R>
-struct BundleCursor {
-  long long u, u1;  // first item of the current segment, end of the range
-  int nz, len, j;
-  __device__ void init(long long a, long long b, int nz_) {
-    u = a;
-    u1 = b;
-    nz = nz_;
-    j = 0;
-    len = (u < u1) ? seg_len() : 0;
-  }
-  __device__ int seg_len() const {
-    const int zb = int(u % nz);
-    const long long rem = u1 - u;
-    return int(rem < (long long)(nz - zb) ? rem : (long long)(nz - zb));
-  }
-  __device__ bool valid() const { return u < u1; }
-  __device__ int tile() const { return int(u / nz); }
-  __device__ int zb() const { return int(u % nz); }
-  __device__ void advance() {
-    if (++j >= len + 2 * R) {
-      u += len;
-      j = 0;
-      len = (u < u1) ? seg_len() : 0;
-    }
-  }
-};
+// Segment of a CTA's work range: the part of one tile column inside it.
+// Its bundles j = 0 .. len+2R-1 carry front plane zb - R + j and, for
+// j >= 2R, compute plane zb + j - 2R (2R warm-up bundles, then one per plane).
+__device__ __forceinline__ int segment_len(int u, int u1, int nz) { return min(u1 - u, nz - u % nz); }
 
 template <int R, int TY, int PPT, int NB>
 struct TmaConfig {
@@ -153,32 +126,43 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const long long u0 = wk.total * blockIdx.x / gridDim.x;
-  const long long u1 = wk.total * (blockIdx.x + 1) / gridDim.x;
+  const int u0 = int((long long)wk.total * blockIdx.x / gridDim.x);
+  const int u1 = int((long long)wk.total * (blockIdx.x + 1) / gridDim.x);
   if (u0 >= u1) return;
   if (smem_addr(smem) & 127u) {  // tensor copies need 128-byte aligned destinations
     if (threadIdx.x == 0) atomicOr(err_flag, 2);
     return;
   }
   const uint32_t full0 = smem_addr(bars);
+  const int nz = wk.nz;
 
-  // one bundle into one slot (called by a single lane)
-  auto issue = [&](int slot, const BundleCursor<R>& b) {
-    const int t = b.tile();
+  // Bundle `jn` counted from the start of the segment (u, len) into `slot`
+  // (one lane); false when it lies past the end of the range.  `mark` > 0
+  // is recorded as the number of bundles issued before the copies start.
+  auto issue = [&](int slot, int u, int len, int jn, int mark) -> bool {
+    while (jn >= len + 2 * R) {
+      jn -= len + 2 * R;
+      u += len;
+      if (u >= u1) return false;
+      len = segment_len(u, u1, nz);
+    }
+    if (mark > 0) atomicMax(&ring->issued, mark);
+    const int t = u / nz;
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
-    const int zf = b.zb() + b.j;  // padded z of the front plane
-    float* s = slots + slot * C::SLOT_FLOATS;
+    const int zf = u % nz + jn;  // padded z of the front plane
+    float* sb = slots + slot * C::SLOT_FLOATS;
     const uint32_t bar = full0 + 8u * slot;
-    if (b.j < 2 * R) {
+    if (jn < 2 * R) {
       mbar_arrive_expect_tx(bar, C::I_BYTES);
-      tma_load_3d(smem_addr(s + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
+      tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
     } else {
       mbar_arrive_expect_tx(bar, C::C_BYTES + 3u * C::I_BYTES);
-      tma_load_3d(smem_addr(s), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
-      tma_load_3d(smem_addr(s + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
-      tma_load_3d(smem_addr(s + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar);
-      tma_load_3d(smem_addr(s + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar);
+      tma_load_3d(smem_addr(sb), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
+      tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
+      tma_load_3d(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar);
+      tma_load_3d(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar);
     }
+    return true;
   };
 
   if (threadIdx.x == 0) {
@@ -192,10 +176,9 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     prefetch_tensormap(&map_f);
     prefetch_tensormap(&map_o);
     prefetch_tensormap(&map_k);
-    BundleCursor<R> b;
-    b.init(u0, u1, wk.nz);
+    const int len0 = segment_len(u0, u1, nz);
     int n = 0;
-    for (; n < NB && b.valid(); ++n, b.advance()) issue(n, b);
+    while (n < NB && issue(n, u0, len0, n, 0)) ++n;
     ring->issued = n;
   }
   __syncthreads();
@@ -219,47 +202,42 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     cz2[j] = ISO ? cx2[j] : make_float2(a.cz[j], a.cz[j]);
   }
   const int r0 = warp * PPT;  // first tile row of this warp
-  float2 qz[PPT][QL];         // z-queue, shifted once per plane
+  // planes z <= zlo or z >= zhi hold Dirichlet nodes or have ghost images
+  const int zlo = (a.bc[0] != kBcNone) ? R : -1;
+  const int zhi = (a.bc[1] != kBcNone) ? a.nz - 1 - R : a.nz;
+  float2 qz[PPT][QL];  // z-queue, shifted once per plane
 
-  BundleCursor<R> cur, ahead;  // bundle being consumed, bundle NB later
-  cur.init(u0, u1, wk.nz);
-  ahead = cur;
-#pragma unroll 1
-  for (int i = 0; i < NB; ++i) ahead.advance();
   int k = 0;  // bundles consumed by this warp
   int s = 0;  // slot of bundle k
   uint32_t ph = 0;
-
-  while (cur.valid()) {
-    const int t = cur.tile();
-    const int zb = cur.zb();
-    const int len = cur.len;
+  for (int u = u0; u < u1;) {
+    const int len = segment_len(u, u1, nz);
+    const int t = u / nz;
+    const int zb = u % nz;
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
     const int x = x0 + 2 * lane;
-    // per-segment invariants; a row is "near" when one of its nodes is a
-    // Dirichlet face node, has a ghost mirror image, or lies past the last
-    // node (ragged tile)
-    bool seg_near;
-    {
-      const FaceTreat fxa = face_treat<R>(x, a.nx, a.bc[4], a.bc[5]);
-      const FaceTreat fxb = face_treat<R>(x + 1, a.nx, a.bc[4], a.bc[5]);
-      const bool lane_near = x + 1 >= a.nx || fxa.zero || fxb.zero || fxa.mirror || fxb.mirror;
-      seg_near = __any_sync(0xffffffffu, lane_near);
-    }
+    // per-segment invariants (warp-uniform unless noted)
+    const FaceTreat fxa = face_treat<R>(x, a.nx, a.bc[4], a.bc[5]);  // per lane
+    const FaceTreat fxb = face_treat<R>(x + 1, a.nx, a.bc[4], a.bc[5]);
+    const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;
+    // some lane has x-face work or lies past the last column
+    const bool xnear = __any_sync(0xffffffffu, !vb_ok || fxa.zero || fxb.zero || fxa.mirror || fxb.mirror);
     const int dxa = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
     const int dxb = layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]);
     int d2xy_a[PPT], d2xy_b[PPT];
-    bool xy_free[PPT];  // no node of the warp's row is in the absorbing layer (in x, y)
+    bool ynear = false;  // some row has y-face work or lies past the last row
+    bool xy_free = true;  // no node of the warp's rows is in the absorbing layer in x, y
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int y = y0 + r0 + i;
       const int dyl = layer_distance(y, a.ny, a.nbl[2], a.nbl[3]);
       d2xy_a[i] = dyl * dyl + dxa * dxa;
       d2xy_b[i] = dyl * dyl + dxb * dxb;
-      xy_free[i] = __all_sync(0xffffffffu, (d2xy_a[i] | d2xy_b[i]) == 0);
+      xy_free = xy_free && (d2xy_a[i] | d2xy_b[i]) == 0;
       const FaceTreat fy = face_treat<R>(y, a.ny, a.bc[2], a.bc[3]);
-      seg_near = seg_near || y >= a.ny || fy.zero || fy.mirror != 0;  // warp-uniform
+      ynear = ynear || y >= a.ny || fy.zero || fy.mirror != 0;
     }
+    xy_free = __all_sync(0xffffffffu, xy_free);
     const int rowoff0 = (y0 + r0) * int(a.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
     const int nb = len + 2 * R;
 #pragma unroll 1
@@ -285,13 +263,11 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
         const float* cc = S + (r0 + R) * PW + C::XH + 2 * lane;  // centre of output row 0
         const float2* O = reinterpret_cast<const float2*>(S + C::C_FLOATS + C::I_FLOATS) + r0 * (TX / 2) + lane;
         const float2* K = O + C::I_FLOATS / 2;
-        const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
-        const int dz2 = dzl * dzl;
         // y window: rows -R .. PPT-1+R around the warp's first row
         float2 yw[C::YW];
 #pragma unroll
         for (int q = 0; q < C::YW; ++q) yw[q] = *reinterpret_cast<const float2*>(cc + (q - R) * PW);
-        float2 pnew[PPT];
+        float2 kl[PPT];  // kappa L, then p[n+1]
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
           const float* c = cc + i * PW;
@@ -316,40 +292,63 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
             lx = f2_fma(cx2[jj], f2_sub(xs, p2), lx);
             ly = f2_fma(cy2[jj], f2_sub(f2_add(yw[i + R + jj], yw[i + R - jj]), p2), ly);
           }
-          const float2 lap = f2_add(f2_add(lz, lx), ly);
-          const float2 po = O[i * (TX / 2)];
-          const float2 kp = K[i * (TX / 2)];
-          // damping coefficients; (1, 0) outside the absorbing layer
-          float2 ca = make_float2(1.f, 1.f), e = make_float2(0.f, 0.f);
-          if (dz2 != 0 || !xy_free[i]) {
+          kl[i] = f2_add(f2_add(lz, lx), ly);
+        }
+        const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+        const int dz2 = dzl * dzl;
+        if (dz2 == 0 && xy_free) {
+          // outside the absorbing layer: a = 1, e = 0
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
+            kl[i] = f2_add(pc, f2_fma(kp, kl[i], f2_sub(pc, po)));
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
             const float2 da = __ldg(&a.damp[dz2 + d2xy_a[i]]);
             const float2 db = __ldg(&a.damp[dz2 + d2xy_b[i]]);
-            ca = make_float2(da.x, db.x);
-            e = make_float2(da.y, db.y);
+            const float2 ca = make_float2(da.x, db.x), e = make_float2(da.y, db.y);
+            // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
+            kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
-          // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
-          pnew[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, lap, f2_fma(e, po, f2_sub(pc, po)))));
         }
         float* plane = a.pnm1 + int64_t(z) * a.sz + rowoff0;
-        const FaceTreat fz = face_treat<R>(z, a.nz, a.bc[0], a.bc[1]);
-        if (!(seg_near || fz.zero || fz.mirror != 0)) {
+        const bool znear = z <= zlo || z >= zhi;
+        if (!(znear || ynear || xnear)) {
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) *reinterpret_cast<float2*>(plane + i * int(a.sy)) = pnew[i];
+          for (int i = 0; i < PPT; ++i) *reinterpret_cast<float2*>(plane + i * int(a.sy)) = kl[i];
+        } else if (!(znear || ynear)) {
+          // x-face work only: Dirichlet columns held at zero, mirror images
+          // into the x ghosts, nothing past the last column
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            float* dst = plane + i * int(a.sy);
+            const float va = fxa.zero ? 0.f : kl[i].x;
+            const float vb = fxb.zero ? 0.f : kl[i].y;
+            if (vb_ok) {
+              *reinterpret_cast<float2*>(dst) = make_float2(va, vb);
+            } else if (va_ok) {
+              dst[0] = va;
+            }
+            if (va_ok && fxa.mirror) dst[fxa.mirror] = fxa.sign * va;
+            if (vb_ok && fxb.mirror) dst[1 + fxb.mirror] = fxb.sign * vb;
+          }
         } else {
-          // Dirichlet face nodes are held at zero; mirror images go to the ghosts
-          const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;
-          const FaceTreat fxa = face_treat<R>(x, a.nx, a.bc[4], a.bc[5]);
-          const FaceTreat fxb = face_treat<R>(x + 1, a.nx, a.bc[4], a.bc[5]);
+          // general face work: Dirichlet nodes are held at zero; mirror
+          // images go to the ghosts along every axis
+          const FaceTreat fz = face_treat<R>(z, a.nz, a.bc[0], a.bc[1]);
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const int y = y0 + r0 + i;
             if (y >= a.ny) continue;
             const FaceTreat fy = face_treat<R>(y, a.ny, a.bc[2], a.bc[3]);
             const bool zrow = fz.zero || fy.zero;
-            const float va = (zrow || fxa.zero) ? 0.f : pnew[i].x;
-            const float vb = (zrow || fxb.zero) ? 0.f : pnew[i].y;
+            const float va = (zrow || fxa.zero) ? 0.f : kl[i].x;
+            const float vb = (zrow || fxb.zero) ? 0.f : kl[i].y;
             float* dst = plane + i * int(a.sy);
-            if (va_ok && vb_ok) {
+            if (vb_ok) {
               *reinterpret_cast<float2*>(dst) = make_float2(va, vb);
             } else if (va_ok) {
               dst[0] = va;
@@ -372,27 +371,21 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       // release the slot; the last warp to do so refills it with bundle k+NB
       __syncwarp();
       if (lane == 0) {
-        __threadfence_block();  // this warp's reads of the slot come first
+        asm volatile("fence.acq_rel.cta;" ::: "memory");  // this warp's reads of the slot come first
         if (atomicAdd(&cnt[s], 1) == NCW - 1) {
           cnt[s] = 0;
-          if (ahead.valid() && !*abort_flag) {
-            __threadfence_block();
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            atomicMax(&ring->issued, k + NB + 1);
-            issue(s, ahead);
-          }
+          asm volatile("fence.acq_rel.cta;" ::: "memory");
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (!*abort_flag) issue(s, u, len, j + NB, k + NB + 1);
         }
       }
-      ahead.advance();
       ++k;
       if (++s == NB) {
         s = 0;
         ph ^= 1u;
       }
     }
-    cur.u += len;
-    cur.j = 0;
-    cur.len = (cur.u < cur.u1) ? cur.seg_len() : 0;
+    u += len;
   }
 }
 
