@@ -371,9 +371,12 @@ bool use_tma(const sw_grid* g) {
   // and assumes every node is within R of at most one face per axis
   // and counts its (64 x 16 tile, plane) work items in 32 bits
   const int64_t m = 2 * int64_t(g->R) + 1;
-  const int64_t items = (g->lay.n[2] + 63) / 64 * ((g->lay.n[1] + 15) / 16) * g->lay.n[0];
-  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && g->lay.n[0] > m &&
-         g->lay.n[1] > m && g->lay.n[2] > m && items < (int64_t(1) << 31);
+  // (and the face-condition kernel numbers the lines of both sides of a face in 32 bits)
+  const int64_t* n = g->lay.n;
+  const int64_t items = (n[2] + 63) / 64 * ((n[1] + 15) / 16) * n[0];
+  const int64_t lines = 2 * std::max(n[0] * n[1] * int64_t(g->R), std::max(n[0] * n[2], n[1] * n[2]));
+  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && n[0] > m &&
+         n[1] > m && n[2] > m && items < (int64_t(1) << 31) && lines < (int64_t(1) << 31);
 }
 
 PointSet point_set(const sw_grid* g, bool src) {
@@ -726,25 +729,34 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   }
   int64_t launches = 0;
   const int src_threads = g->n_src * g->lz * g->ly * g->lx;
+  // threads of the face-condition kernel: z and y faces one per line, x faces R per line
+  const int64_t face_threads =
+      2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]), g->n[0] * g->n[1] * int64_t(g->R));
+  const unsigned face_blocks = unsigned((face_threads + 255) / 256);
   for (int step = 0; step < n_steps; ++step) {
     float* pn = g->u[step & 1];
     float* pnm1 = g->u[(step + 1) & 1];
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step], g->stream));
-    if (use_tma(g))
+    const bool tma = use_tma(g);
+    if (tma)
       launch_stencil_tma(g, a, step & 1, g->stream);
     else
       launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step + 1], g->stream));
     ++launches;
+    if (tma) {  // the pipelined kernel writes node values only; the face conditions follow
+      face_conditions_kernel<<<dim3(face_blocks, 3), 256, 0, g->stream>>>(a.pnm1, f, g->R);
+      ++launches;
+    }
     if (src_threads > 0) {
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(
           a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
     }
     if (g->n_rec > 0) {
-      sample_receivers_kernel<<<(g->n_rec * 32 + 255) / 256, 256, 0, g->stream>>>(a.pnm1, rec, f, seis_dev,
+      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, g->stream>>>(a.pnm1, rec, f, seis_dev,
                                                                                   step);
       ++launches;
     }
@@ -1149,7 +1161,7 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g.stream>>>(a.pnm1, a.kappa, g.damp, src, g.wavelet,
                                                                             g.sig_stride, step, f, ndim, g.R);
     if (n_rec > 0)
-      sample_receivers_kernel<<<(n_rec * 32 + 255) / 256, 256, 0, g.stream>>>(a.pnm1, rec, f, seismogram, step);
+      sample_receivers_kernel<<<(n_rec + 3) / 4, 128, 0, g.stream>>>(a.pnm1, rec, f, seismogram, step);
   }
   SW_CUDA(cudaGetLastError());
   if (final_field) {

@@ -77,23 +77,28 @@ __global__ void inject_sources_kernel(float* p, const float* kappa, const float2
   if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
 }
 
-// Eq. 12: rec[step][r] = sum_k d_k p[n+1]_k.  One warp per receiver.
+// Eq. 12: rec[step][r] = sum_k d_k p[n+1]_k.  One warp per receiver: lanes
+// run along x within a window row (lx <= 32 lanes per row, 32 / lx rows per
+// pass), so each load instruction reads a few contiguous row pieces, and the
+// row loop is unrolled so that several loads are in flight per lane.
 __global__ void sample_receivers_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= rec.count) return;
-  const int taps = rec.lz * rec.ly * rec.lx;
   const float* w = rec.w + int64_t(warp) * 3 * rec.L;
   const int z0 = rec.first[3 * warp], y0 = rec.first[3 * warp + 1], x0 = rec.first[3 * warp + 2];
+  const int rows = rec.lz * rec.ly, rpp = 32 / rec.lx;
+  const int ix = lane % rec.lx, rs = lane / rec.lx;
   float acc = 0.f;
-  for (int t = lane; t < taps; t += 32) {
-    int rem = t;
-    const int ix = rem % rec.lx;
-    rem /= rec.lx;
-    const int iy = rem % rec.ly;
-    const int iz = rem / rec.ly;
-    const float wgt = w[iz] * w[rec.L + iy] * w[2 * rec.L + ix];
-    acc = fmaf(wgt, p[int64_t(z0 + iz) * f.sz + int64_t(y0 + iy) * f.sy + (x0 + ix)], acc);
+  if (rs < rpp) {
+    const float* q = p + int64_t(z0) * f.sz + int64_t(y0) * f.sy + x0 + ix;
+    float s = 0.f;
+#pragma unroll 4
+    for (int row = rs; row < rows; row += rpp) {
+      const int iz = row / rec.ly, iy = row - (row / rec.ly) * rec.ly;
+      s = fmaf(w[iz] * w[rec.L + iy], q[int64_t(iz) * f.sz + int64_t(iy) * f.sy], s);
+    }
+    acc = w[2 * rec.L + ix] * s;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -169,6 +174,81 @@ __global__ void mirror_even_kernel(float* f_, FaceInfo f, int axis, int R) {
     const int m = side == 0 ? j : n[axis] - 1 - j;
     const int64_t base = int64_t(i1) * st[o1] + int64_t(i2) * st[o2];
     f_[base + int64_t(g) * st[axis]] = f_[base + int64_t(m) * st[axis]];
+  }
+}
+
+// Face conditions of a freshly computed 3D p[n+1], for the pipelined stencil
+// kernel, which writes node values only (Sec. 2.3): nodes on a Dirichlet face
+// are set to zero, and every node within R of a Dirichlet (odd) or Neumann
+// (even) face gets its mirror image in that face's ghost layer; a node on any
+// Dirichlet face is mirrored as zero.  z and y faces: one thread per (side,
+// position on the face), consecutive threads at consecutive x, walking the R
+// nodes next to the face.  x faces: one thread per (side, row, offset j), so
+// that a warp reads and writes whole runs of a few rows.  Ghost layers of
+// different axes are disjoint, and a node read for mirroring while another
+// thread zeroes it is taken as zero either way.  Needs every axis longer than
+// 2R+1 (a node is within R of one face only).
+template <int AX>
+__device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int R, int t) {
+  // the two axes spanning the face: a (slow) and b (fast)
+  const int na = AX == 0 ? f.ny : f.nz;
+  const int nb = AX == 2 ? f.ny : f.nx;
+  const int n = AX == 0 ? f.nz : (AX == 1 ? f.ny : f.nx);
+  const int64_t sa = AX == 0 ? f.sy : f.sz;
+  const int64_t sb = AX == 2 ? f.sy : 1;
+  const int64_t s = AX == 0 ? f.sz : (AX == 1 ? f.sy : 1);
+  const int face = na * nb;
+  const int side = t >= face ? 1 : 0;
+  const int e = t - side * face;
+  const int bc = side ? f.bc[2 * AX + 1] : f.bc[2 * AX];
+  if (bc == kBcNone) return;
+  const int ia = e / nb, ib = e - (e / nb) * nb;
+  // is the line on a Dirichlet face of another axis? (then every node of it is zero)
+  int cz = 0, cy = 0, cx = 0;
+  if (AX == 0) { cy = ia; cx = ib; }
+  if (AX == 1) { cz = ia; cx = ib; }
+  if (AX == 2) { cz = ia; cy = ib; }
+  const bool zero = (AX != 0 && ((cz == 0 && f.bc[0] == kBcDirichlet) || (cz == f.nz - 1 && f.bc[1] == kBcDirichlet))) ||
+                    (AX != 1 && ((cy == 0 && f.bc[2] == kBcDirichlet) || (cy == f.ny - 1 && f.bc[3] == kBcDirichlet))) ||
+                    (AX != 2 && ((cx == 0 && f.bc[4] == kBcDirichlet) || (cx == f.nx - 1 && f.bc[5] == kBcDirichlet)));
+  float* q = p + ia * sa + ib * sb + (side ? int64_t(n - 1) * s : 0);  // the face node
+  const int64_t in = side ? -s : s;                                    // inwards
+  const float sign = (bc == kBcDirichlet) ? -1.f : 1.f;
+  float v[kMaxR + 1];
+#pragma unroll
+  for (int j = 1; j <= kMaxR; ++j)
+    if (j <= R) v[j] = q[j * in];
+  if (bc == kBcDirichlet || zero) q[0] = 0.f;
+#pragma unroll
+  for (int j = 1; j <= kMaxR; ++j)
+    if (j <= R) q[-j * in] = zero ? 0.f : sign * v[j];
+}
+
+__device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int R, int t) {
+  const int line = t / R, j = t - line * R + 1;
+  const int face = f.nz * f.ny;
+  const int side = line >= face ? 1 : 0;
+  const int e = line - side * face;
+  const int bc = side ? f.bc[5] : f.bc[4];
+  if (bc == kBcNone) return;
+  const int z = e / f.ny, y = e - (e / f.ny) * f.ny;
+  const bool zero = (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
+                    (y == 0 && f.bc[2] == kBcDirichlet) || (y == f.ny - 1 && f.bc[3] == kBcDirichlet);
+  float* q = p + int64_t(z) * f.sz + int64_t(y) * f.sy + (side ? f.nx - 1 : 0);  // the face node
+  const int in = side ? -1 : 1;
+  const float v = q[j * in];
+  q[-j * in] = zero ? 0.f : ((bc == kBcDirichlet) ? -v : v);
+  if (j == 1 && (bc == kBcDirichlet || zero)) q[0] = 0.f;
+}
+
+__global__ void face_conditions_kernel(float* p, FaceInfo f, int R) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0) {
+    if (t < 2 * f.ny * f.nx) face_line<0>(p, f, R, t);
+  } else if (blockIdx.y == 1) {
+    if (t < 2 * f.nz * f.nx) face_line<1>(p, f, R, t);
+  } else {
+    if (t < 2 * f.nz * f.ny * R) face_x(p, f, R, t);
   }
 }
 

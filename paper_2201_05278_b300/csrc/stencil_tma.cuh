@@ -22,8 +22,9 @@
 //   - each lane computes two adjacent columns with 64-bit shared loads and
 //     packed FP32x2 arithmetic, the Laplacian in three per-axis chains;
 //     rows with no damping skip the damping lookup;
-//   - boundary work (Dirichlet nodes, face mirroring, ragged tails) runs only
-//     on planes where some node of the warp is within R of a face.
+//   - the kernel writes node values only (ragged tiles masked); Dirichlet
+//     face nodes and the ghost images of the face conditions are written by
+//     face_conditions_kernel right after it.
 // Every mbarrier wait is bounded (wall clock); on timeout the CTA raises the
 // device error flag, waits (bounded) for the copies it issued and exits.
 #pragma once
@@ -73,32 +74,6 @@ struct TmaConfig {
   static_assert(kTileXMax % TX == 0 && kTileYMax % TY == 0 && TY % PPT == 0, "tile shape");
   static_assert(PW <= 256 && PH <= 256 && XH % 2 == 0, "TMA box extent / float2 alignment");
 };
-
-// Face treatment of node index i along one axis of length n: whether it is a
-// Dirichlet face node (held at zero) and where its mirror image goes in the
-// ghost layer (offset in nodes along the axis, 0 = none) with which sign.
-// Assumes n > 2R+1, so a node is within R of at most one face.
-struct FaceTreat {
-  bool zero;
-  int mirror;
-  float sign;
-};
-
-template <int R>
-__device__ __forceinline__ FaceTreat face_treat(int i, int n, int bc_lo, int bc_hi) {
-  FaceTreat f;
-  f.zero = (i == 0 && bc_lo == kBcDirichlet) || (i == n - 1 && bc_hi == kBcDirichlet);
-  f.mirror = 0;
-  f.sign = 1.f;
-  if (bc_lo != kBcNone && i >= 1 && i <= R) {
-    f.mirror = -2 * i;
-    f.sign = (bc_lo == kBcDirichlet) ? -1.f : 1.f;
-  } else if (bc_hi != kBcNone && n - 1 - i >= 1 && n - 1 - i <= R) {
-    f.mirror = 2 * (n - 1 - i);
-    f.sign = (bc_hi == kBcDirichlet) ? -1.f : 1.f;
-  }
-  return f;
-}
 
 // Ring bookkeeping kept in shared memory after the slots.
 struct RingShared {
@@ -202,9 +177,6 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     cz2[j] = ISO ? cx2[j] : make_float2(a.cz[j], a.cz[j]);
   }
   const int r0 = warp * PPT;  // first tile row of this warp
-  // planes z <= zlo or z >= zhi hold Dirichlet nodes or have ghost images
-  const int zlo = (a.bc[0] != kBcNone) ? R : -1;
-  const int zhi = (a.bc[1] != kBcNone) ? a.nz - 1 - R : a.nz;
   float2 qz[PPT][QL];  // z-queue, shifted once per plane
 
   int k = 0;  // bundles consumed by this warp
@@ -217,15 +189,12 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
     const int x = x0 + 2 * lane;
     // per-segment invariants (warp-uniform unless noted)
-    const FaceTreat fxa = face_treat<R>(x, a.nx, a.bc[4], a.bc[5]);  // per lane
-    const FaceTreat fxb = face_treat<R>(x + 1, a.nx, a.bc[4], a.bc[5]);
-    const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;
-    // some lane has x-face work or lies past the last column
-    const bool xnear = __any_sync(0xffffffffu, !vb_ok || fxa.zero || fxb.zero || fxa.mirror || fxb.mirror);
+    const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;  // per lane
+    // some lane lies past the last column or some row past the last row
+    const bool ragged = __any_sync(0xffffffffu, !vb_ok) || y0 + r0 + PPT > a.ny;
     const int dxa = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
     const int dxb = layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]);
     int d2xy_a[PPT], d2xy_b[PPT];
-    bool ynear = false;  // some row has y-face work or lies past the last row
     bool xy_free = true;  // no node of the warp's rows is in the absorbing layer in x, y
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
@@ -234,14 +203,26 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       d2xy_a[i] = dyl * dyl + dxa * dxa;
       d2xy_b[i] = dyl * dyl + dxb * dxb;
       xy_free = xy_free && (d2xy_a[i] | d2xy_b[i]) == 0;
-      const FaceTreat fy = face_treat<R>(y, a.ny, a.bc[2], a.bc[3]);
-      ynear = ynear || y >= a.ny || fy.zero || fy.mirror != 0;
     }
     xy_free = __all_sync(0xffffffffu, xy_free);
     const int rowoff0 = (y0 + r0) * int(a.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
     const int nb = len + 2 * R;
 #pragma unroll 1
     for (int j = 0; j < nb; ++j) {
+      // damping coefficients of this plane's nodes, fetched before the wait
+      // so that their latency hides behind it; (1, 0) outside the layer
+      const int z = zb + j - 2 * R;
+      const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+      const int dz2 = dzl * dzl;
+      const bool damped = j >= 2 * R && (dz2 != 0 || !xy_free);
+      float2 da[PPT], db[PPT];
+      if (damped) {
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          da[i] = __ldg(&a.damp[dz2 + d2xy_a[i]]);
+          db[i] = __ldg(&a.damp[dz2 + d2xy_b[i]]);
+        }
+      }
       // the decision to go on is taken by the whole warp, so its lanes never split
       const bool bad = *abort_flag || !mbar_wait_bounded(full0 + 8u * s, ph, limit_ns);
       if (__any_sync(0xffffffffu, bad)) {
@@ -259,7 +240,6 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
         }
       }
       if (j >= 2 * R) {
-        const int z = zb + j - 2 * R;
         const float* cc = S + (r0 + R) * PW + C::XH + 2 * lane;  // centre of output row 0
         const float2* O = reinterpret_cast<const float2*>(S + C::C_FLOATS + C::I_FLOATS) + r0 * (TX / 2) + lane;
         const float2* K = O + C::I_FLOATS / 2;
@@ -294,9 +274,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
           }
           kl[i] = f2_add(f2_add(lz, lx), ly);
         }
-        const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
-        const int dz2 = dzl * dzl;
-        if (dz2 == 0 && xy_free) {
+        if (!damped) {
           // outside the absorbing layer: a = 1, e = 0
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
@@ -307,63 +285,24 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
-            const float2 da = __ldg(&a.damp[dz2 + d2xy_a[i]]);
-            const float2 db = __ldg(&a.damp[dz2 + d2xy_b[i]]);
-            const float2 ca = make_float2(da.x, db.x), e = make_float2(da.y, db.y);
+            const float2 ca = make_float2(da[i].x, db[i].x), e = make_float2(da[i].y, db[i].y);
             // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
             kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
         }
         float* plane = a.pnm1 + int64_t(z) * a.sz + rowoff0;
-        const bool znear = z <= zlo || z >= zhi;
-        if (!(znear || ynear || xnear)) {
+        if (!ragged) {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) *reinterpret_cast<float2*>(plane + i * int(a.sy)) = kl[i];
-        } else if (!(znear || ynear)) {
-          // x-face work only: Dirichlet columns held at zero, mirror images
-          // into the x ghosts, nothing past the last column
-#pragma unroll
-          for (int i = 0; i < PPT; ++i) {
-            float* dst = plane + i * int(a.sy);
-            const float va = fxa.zero ? 0.f : kl[i].x;
-            const float vb = fxb.zero ? 0.f : kl[i].y;
-            if (vb_ok) {
-              *reinterpret_cast<float2*>(dst) = make_float2(va, vb);
-            } else if (va_ok) {
-              dst[0] = va;
-            }
-            if (va_ok && fxa.mirror) dst[fxa.mirror] = fxa.sign * va;
-            if (vb_ok && fxb.mirror) dst[1 + fxb.mirror] = fxb.sign * vb;
-          }
         } else {
-          // general face work: Dirichlet nodes are held at zero; mirror
-          // images go to the ghosts along every axis
-          const FaceTreat fz = face_treat<R>(z, a.nz, a.bc[0], a.bc[1]);
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
-            const int y = y0 + r0 + i;
-            if (y >= a.ny) continue;
-            const FaceTreat fy = face_treat<R>(y, a.ny, a.bc[2], a.bc[3]);
-            const bool zrow = fz.zero || fy.zero;
-            const float va = (zrow || fxa.zero) ? 0.f : kl[i].x;
-            const float vb = (zrow || fxb.zero) ? 0.f : kl[i].y;
+            if (y0 + r0 + i >= a.ny) break;
             float* dst = plane + i * int(a.sy);
             if (vb_ok) {
-              *reinterpret_cast<float2*>(dst) = make_float2(va, vb);
+              *reinterpret_cast<float2*>(dst) = kl[i];
             } else if (va_ok) {
-              dst[0] = va;
-            }
-            if (va_ok && fxa.mirror) dst[fxa.mirror] = fxa.sign * va;
-            if (vb_ok && fxb.mirror) dst[1 + fxb.mirror] = fxb.sign * vb;
-            if (fy.mirror) {
-              float* g = dst + fy.mirror * int(a.sy);
-              if (va_ok) g[0] = fy.sign * va;
-              if (vb_ok) g[1] = fy.sign * vb;
-            }
-            if (fz.mirror) {
-              float* g = dst + int64_t(fz.mirror) * a.sz;
-              if (va_ok) g[0] = fz.sign * va;
-              if (vb_ok) g[1] = fz.sign * vb;
+              dst[0] = kl[i].x;
             }
           }
         }
