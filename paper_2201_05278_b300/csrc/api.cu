@@ -729,35 +729,31 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   }
   int64_t launches = 0;
   const int src_threads = g->n_src * g->lz * g->ly * g->lx;
-  // threads of the face-condition kernel: z and y faces one per line, x faces R per line
-  const int64_t face_threads =
-      2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]), g->n[0] * g->n[1] * int64_t(g->R));
-  const unsigned face_blocks = unsigned((face_threads + 255) / 256);
+  const bool tma = use_tma(g);
   for (int step = 0; step < n_steps; ++step) {
     float* pn = g->u[step & 1];
     float* pnm1 = g->u[(step + 1) & 1];
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step], g->stream));
-    const bool tma = use_tma(g);
     if (tma)
       launch_stencil_tma(g, a, step & 1, g->stream);
     else
       launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
     if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step + 1], g->stream));
     ++launches;
-    if (tma) {  // the pipelined kernel writes node values only; the face conditions follow
-      face_conditions_kernel<<<dim3(face_blocks, 3), 256, 0, g->stream>>>(a.pnm1, f, g->R);
-      ++launches;
-    }
-    if (src_threads > 0) {
+    if (src_threads > 0) {  // before the face conditions, which mirror its increments
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(
           a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
     }
-    if (g->n_rec > 0) {
-      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, g->stream>>>(a.pnm1, rec, f, seis_dev,
-                                                                                  step);
+    if (tma) {
+      // the pipelined kernel writes node values only: the face conditions
+      // follow, with the receiver samples in the same launch
+      launch_face_conditions(a.pnm1, f, g->R, rec, seis_dev, step, g->stream);
+      ++launches;
+    } else if (g->n_rec > 0) {
+      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, g->stream>>>(a.pnm1, rec, f, seis_dev, step);
       ++launches;
     }
   }

@@ -77,32 +77,55 @@ __global__ void inject_sources_kernel(float* p, const float* kappa, const float2
   if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
 }
 
-// Eq. 12: rec[step][r] = sum_k d_k p[n+1]_k.  One warp per receiver: lanes
+// Eq. 12: rec[step][r] = sum_k d_k p[n+1]_k, receiver r by one warp: lanes
 // run along x within a window row (lx <= 32 lanes per row, 32 / lx rows per
 // pass), so each load instruction reads a few contiguous row pieces, and the
-// row loop is unrolled so that several loads are in flight per lane.
-__global__ void sample_receivers_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= rec.count) return;
-  const float* w = rec.w + int64_t(warp) * 3 * rec.L;
-  const int z0 = rec.first[3 * warp], y0 = rec.first[3 * warp + 1], x0 = rec.first[3 * warp + 2];
+// row loop is unrolled so that several loads are in flight per lane.  With
+// `dirichlet_zero` a node on a Dirichlet face counts as zero whatever is
+// stored there (for sampling while the face conditions are being applied).
+__device__ __forceinline__ void sample_receiver(const float* p, const PointSet& rec, const FaceInfo& f, float* out,
+                                                int step, int r, int lane, bool dirichlet_zero) {
+  const float* w = rec.w + int64_t(r) * 3 * rec.L;
+  const int z0 = rec.first[3 * r], y0 = rec.first[3 * r + 1], x0 = rec.first[3 * r + 2];
   const int rows = rec.lz * rec.ly, rpp = 32 / rec.lx;
   const int ix = lane % rec.lx, rs = lane / rec.lx;
   float acc = 0.f;
-  if (rs < rpp) {
-    const float* q = p + int64_t(z0) * f.sz + int64_t(y0) * f.sy + x0 + ix;
+  if (rs < rows && rs < rpp) {
+    const int x = x0 + ix;
+    const bool xd = dirichlet_zero && ((x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet));
+    // window rows rs, rs + rpp, ... as (iz, iy), stepped without divisions
+    const int ly = rec.ly, dz = rpp / ly, dy = rpp - dz * ly;
+    int iz = rs / ly, iy = rs - (rs / ly) * ly;
+    const float* q = p + int64_t(z0) * f.sz + int64_t(y0) * f.sy + x;
     float s = 0.f;
 #pragma unroll 4
-    for (int row = rs; row < rows; row += rpp) {
-      const int iz = row / rec.ly, iy = row - (row / rec.ly) * rec.ly;
-      s = fmaf(w[iz] * w[rec.L + iy], q[int64_t(iz) * f.sz + int64_t(iy) * f.sy], s);
+    while (iz < rec.lz) {
+      float v = q[int64_t(iz) * f.sz + int64_t(iy) * f.sy];
+      if (dirichlet_zero) {
+        const int z = z0 + iz, y = y0 + iy;
+        if (xd || (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
+            (y == 0 && f.bc[2] == kBcDirichlet) || (y == f.ny - 1 && f.bc[3] == kBcDirichlet))
+          v = 0.f;
+      }
+      s = fmaf(w[iz] * w[rec.L + iy], v, s);
+      iz += dz;
+      iy += dy;
+      if (iy >= ly) {
+        iy -= ly;
+        ++iz;
+      }
     }
     acc = w[2 * rec.L + ix] * s;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[int64_t(step) * rec.count + warp] = acc;
+  if (lane == 0) out[int64_t(step) * rec.count + r] = acc;
+}
+
+__global__ void sample_receivers_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= rec.count) return;
+  sample_receiver(p, rec, f, out, step, warp, threadIdx.x & 31, false);
 }
 
 // ---- model set-up -----------------------------------------------------------
@@ -188,8 +211,8 @@ __global__ void mirror_even_kernel(float* f_, FaceInfo f, int axis, int R) {
 // different axes are disjoint, and a node read for mirroring while another
 // thread zeroes it is taken as zero either way.  Needs every axis longer than
 // 2R+1 (a node is within R of one face only).
-template <int AX>
-__device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int R, int t) {
+template <int AX, int R>
+__device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int t) {
   // the two axes spanning the face: a (slow) and b (fast)
   const int na = AX == 0 ? f.ny : f.nz;
   const int nb = AX == 2 ? f.ny : f.nx;
@@ -214,17 +237,16 @@ __device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int R, in
   float* q = p + ia * sa + ib * sb + (side ? int64_t(n - 1) * s : 0);  // the face node
   const int64_t in = side ? -s : s;                                    // inwards
   const float sign = (bc == kBcDirichlet) ? -1.f : 1.f;
-  float v[kMaxR + 1];
+  float v[R + 1];
 #pragma unroll
-  for (int j = 1; j <= kMaxR; ++j)
-    if (j <= R) v[j] = q[j * in];
+  for (int j = 1; j <= R; ++j) v[j] = q[j * in];
   if (bc == kBcDirichlet || zero) q[0] = 0.f;
 #pragma unroll
-  for (int j = 1; j <= kMaxR; ++j)
-    if (j <= R) q[-j * in] = zero ? 0.f : sign * v[j];
+  for (int j = 1; j <= R; ++j) q[-j * in] = zero ? 0.f : sign * v[j];
 }
 
-__device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int R, int t) {
+template <int R>
+__device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int t) {
   const int line = t / R, j = t - line * R + 1;
   const int face = f.nz * f.ny;
   const int side = line >= face ? 1 : 0;
@@ -241,14 +263,63 @@ __device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int R, int t
   if (j == 1 && (bc == kBcDirichlet || zero)) q[0] = 0.f;
 }
 
-__global__ void face_conditions_kernel(float* p, FaceInfo f, int R) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) {
-    if (t < 2 * f.ny * f.nx) face_line<0>(p, f, R, t);
-  } else if (blockIdx.y == 1) {
-    if (t < 2 * f.nz * f.nx) face_line<1>(p, f, R, t);
-  } else {
-    if (t < 2 * f.nz * f.ny * R) face_x(p, f, R, t);
+// One launch per step after the pipelined stencil: the receiver samples of
+// the step (Eq. 12; receiver windows hold nodes only, and Dirichlet face
+// nodes are read as zero) and the face conditions.  The 1D grid is cut into
+// consecutive block ranges: receivers (8 per block) first, so that their
+// longer load chains start early, then z faces, y faces and x faces.
+struct FaceGrid {
+  int rec, z, y, x;  // blocks per part
+  int total() const { return rec + z + y + x; }
+};
+
+template <int R>
+__global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg) {
+  int b = blockIdx.x;
+  if (b < fg.rec) {
+    const int r = b * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r < rec.count) sample_receiver(p, rec, f, out, step, r, threadIdx.x & 31, true);
+    return;
+  }
+  b -= fg.rec;
+  if (b < fg.z) {
+    const int t = b * blockDim.x + threadIdx.x;
+    if (t < 2 * f.ny * f.nx) face_line<0, R>(p, f, t);
+    return;
+  }
+  b -= fg.z;
+  if (b < fg.y) {
+    const int t = b * blockDim.x + threadIdx.x;
+    if (t < 2 * f.nz * f.nx) face_line<1, R>(p, f, t);
+    return;
+  }
+  b -= fg.y;
+  const int t = b * blockDim.x + threadIdx.x;
+  if (t < 2 * f.nz * f.ny * R) face_x<R>(p, f, t);
+}
+
+// Face conditions of p (3D, pipelined stencil) and, if rec.count > 0, the
+// receiver samples of this step, in one launch of 256-thread blocks.
+inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
+                                   cudaStream_t st) {
+  FaceGrid fg;
+  fg.rec = (rec.count + 7) / 8;
+  fg.z = int((2 * int64_t(f.ny) * f.nx + 255) / 256);
+  fg.y = int((2 * int64_t(f.nz) * f.nx + 255) / 256);
+  fg.x = int((2 * int64_t(f.nz) * f.ny * R + 255) / 256);
+  const unsigned grid = unsigned(fg.total());
+  switch (R) {
+    case 1: face_conditions_kernel<1><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 2: face_conditions_kernel<2><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 3: face_conditions_kernel<3><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 4: face_conditions_kernel<4><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 5: face_conditions_kernel<5><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 6: face_conditions_kernel<6><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 7: face_conditions_kernel<7><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 8: face_conditions_kernel<8><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 9: face_conditions_kernel<9><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 10: face_conditions_kernel<10><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    default: break;
   }
 }
 
