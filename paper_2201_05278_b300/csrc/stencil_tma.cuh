@@ -134,8 +134,11 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       mbar_arrive_expect_tx(bar, C::C_BYTES + 3u * C::I_BYTES);
       tma_load_3d(smem_addr(sb), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
       tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
-      tma_load_3d(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar);
-      tma_load_3d(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar);
+      // p[n-1] and kappa are read once: they leave L2 first, so that p[n]
+      // planes stay there for the halo rows neighbouring tiles read later
+      const uint64_t once = make_policy_evict_first();
+      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar, once);
+      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar, once);
     }
     return true;
   };
@@ -205,18 +208,33 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       xy_free = xy_free && (d2xy_a[i] | d2xy_b[i]) == 0;
     }
     xy_free = __all_sync(0xffffffffu, xy_free);
+    // damping coefficients of the warp's nodes on planes outside the z layer
+    // (the same for every such plane of the segment): ca0 = 1/(1+e), e0 = e
+    float2 ca0[PPT], e0[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      ca0[i] = make_float2(1.f, 1.f);
+      e0[i] = make_float2(0.f, 0.f);
+      if (!xy_free) {
+        const float2 da = __ldg(&a.damp[d2xy_a[i]]), db = __ldg(&a.damp[d2xy_b[i]]);
+        ca0[i] = make_float2(da.x, db.x);
+        e0[i] = make_float2(da.y, db.y);
+      }
+    }
     const int rowoff0 = (y0 + r0) * int(a.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
     const int nb = len + 2 * R;
 #pragma unroll 1
     for (int j = 0; j < nb; ++j) {
-      // damping coefficients of this plane's nodes, fetched before the wait
-      // so that their latency hides behind it; (1, 0) outside the layer
+      // damping coefficients of this plane's nodes: per segment outside the
+      // z layer, else fetched here, before the wait, so that their latency
+      // hides behind it
       const int z = zb + j - 2 * R;
       const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
       const int dz2 = dzl * dzl;
-      const bool damped = j >= 2 * R && (dz2 != 0 || !xy_free);
+      const bool zlayer = j >= 2 * R && dz2 != 0;
+      const bool damped = zlayer || (j >= 2 * R && !xy_free);
       float2 da[PPT], db[PPT];
-      if (damped) {
+      if (zlayer) {
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
           da[i] = __ldg(&a.damp[dz2 + d2xy_a[i]]);
@@ -281,19 +299,25 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
             const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
             kl[i] = f2_add(pc, f2_fma(kp, kl[i], f2_sub(pc, po)));
           }
+        } else if (!zlayer) {
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
+            // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
+            kl[i] = f2_mul(ca0[i], f2_add(pc, f2_fma(kp, kl[i], f2_fma(e0[i], po, f2_sub(pc, po)))));
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
             const float2 ca = make_float2(da[i].x, db[i].x), e = make_float2(da[i].y, db[i].y);
-            // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
             kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
         }
         float* plane = a.pnm1 + int64_t(z) * a.sz + rowoff0;
         if (!ragged) {
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) *reinterpret_cast<float2*>(plane + i * int(a.sy)) = kl[i];
+          for (int i = 0; i < PPT; ++i) __stcs(reinterpret_cast<float2*>(plane + i * int(a.sy)), kl[i]);  // streaming
         } else {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
