@@ -149,6 +149,17 @@ sw_status sw_set_stencil_variant(sw_grid* g, int variant);
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
 
 /*
+ * Failure-path test hook (no counterpart in the paper).  With starve != 0
+ * the TMA-pipelined kernel issues no tensor copies, so every mbarrier wait
+ * in it runs into its bound: the kernel raises the device error flag and
+ * returns, and sw_forward reports SW_ETIMEOUT with the CUDA context intact.
+ * wait_limit_ns bounds each wait (0 restores the default of 2 s); it also
+ * applies with starve = 0.  Nothing faults or hangs: the test only shows
+ * that a stalled pipeline ends with an error status.
+ */
+sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_limit_ns);
+
+/*
  * Kernel timing.  With profiling on, sw_forward records CUDA events around
  * every stencil launch on the grid's stream; sw_get_profile returns the
  * summed stencil time and launch count of the last sw_forward and the

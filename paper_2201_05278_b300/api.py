@@ -139,6 +139,12 @@ def sw_ricker(f_peak: float, t0: float, dt: float, nt: int) -> np.ndarray:
     return out
 
 
+def sw_set_pipeline_test(g: Grid, starve: bool, wait_limit_ns: int = 0) -> None:
+    """Failure-path test hook: with `starve` the pipelined kernel issues no
+    copies, so its bounded waits give up and sw_forward raises SW_ETIMEOUT."""
+    _check(_lib.load().sw_set_pipeline_test(g.handle, int(bool(starve)), int(wait_limit_ns)))
+
+
 def sw_set_stencil_variant(g: Grid, variant: int) -> None:
     _check(_lib.load().sw_set_stencil_variant(g.handle, int(variant)))
 

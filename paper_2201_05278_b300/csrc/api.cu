@@ -109,6 +109,8 @@ struct sw_grid {
   // interior box for each of the two wavefield buffers, kappa interior box
   int variant = SW_STENCIL_AUTO;
   bool tma_ready = false;
+  bool starve = false;                               // failure-path test: no tensor copies
+  unsigned long long wait_limit_ns = 2000000000ull;  // bound of every mbarrier wait
   int sm_count = 0;
   CUtensorMap map_halo[2], map_inner[2], map_kappa;
 
@@ -316,7 +318,7 @@ sw_status build_tma_maps(sw_grid* g) {
   return SW_OK;
 }
 
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per mbarrier wait
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // default bound of an mbarrier wait (2 s)
 
 template <int R, int TY, int PPT, int NB, int MINB, bool ISO>
 void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
@@ -333,10 +335,11 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   const int tiles_y = (a.ny + TY - 1) / TY;
   wk.nz = a.nz;
   wk.total = wk.tiles_x * tiles_y * a.nz;  // < 2^31: checked in use_tma
+  wk.starve = g->starve ? 1 : 0;
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf], g->map_inner[buf ^ 1],
-                                                g->map_kappa, a, wk, g->dflag, kWaitLimitNs);
+                                                g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
 }
 
 template <int R, int TY, int PPT, int NB, int MINB>
@@ -815,6 +818,13 @@ sw_status sw_set_stencil_variant(sw_grid* g, int variant) {
     return fail(SW_EINVAL, "unknown stencil variant %d", variant);
   if (variant == SW_STENCIL_TMA && g->ndim != 3) return fail(SW_EINVAL, "the pipelined stencil is 3D only");
   g->variant = variant;
+  return SW_OK;
+}
+
+sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_limit_ns) {
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  g->starve = starve != 0;
+  g->wait_limit_ns = wait_limit_ns ? wait_limit_ns : kWaitLimitNs;
   return SW_OK;
 }
 

@@ -44,6 +44,7 @@ struct TmaWork {
   int tiles_x;  // tiles along x
   int nz;       // planes per tile column
   int total;    // tiles * nz work items (fits 32 bits: checked on the host)
+  int starve;   // failure-path test: issue no copies, so every wait runs into its bound
 };
 
 // Segment of a CTA's work range: the part of one tile column inside it.
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     prefetch_tensormap(&map_k);
     const int len0 = segment_len(u0, u1, nz);
     int n = 0;
-    while (n < NB && issue(n, u0, len0, n, 0)) ++n;
+    while (!wk.starve && n < NB && issue(n, u0, len0, n, 0)) ++n;
     ring->issued = n;
   }
   __syncthreads();

@@ -187,3 +187,30 @@ def test_error_statuses(cuda_device):
     with pytest.raises(api.SimwaveError) as e:
         api.sw_create_grid(2, w.shape, w.spacing, 7, w.nbl, w.bc, 0.0, 3, 0.0)
     assert e.value.status == api.SW_EINVAL
+
+
+def test_stalled_pipeline_reports_timeout(cuda_device):
+    """Failure path without a fault: a pipeline whose copies are never issued
+    runs every bounded mbarrier wait out; sw_forward returns SW_ETIMEOUT, and
+    the same grid then runs normally and matches the oracle."""
+    w = small_case(3, 8, False, seed=11, n_steps=20)
+    import torch
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+        assert api.sw_get_stencil_variant(g) == api.SW_STENCIL_TMA
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps),
+                               window_radius=w.window_radius)
+        seis = torch.zeros((w.n_steps, len(w.rec_pos)), dtype=torch.float32, device=dev)
+        api.sw_set_pipeline_test(g, True, 1_000_000)  # 1 ms per wait
+        with pytest.raises(api.SimwaveError) as e:
+            api.sw_forward(g, 3, seis)
+        assert e.value.status == api.SW_ETIMEOUT
+        assert "bounded wait" in api.sw_last_error()
+        api.sw_set_pipeline_test(g, False, 0)
+        api.sw_forward(g, w.n_steps, seis)
+        s_ref, _ = run_oracle(w)
+        assert rel_l2(seis.cpu().numpy(), s_ref) <= FP32_SEIS_TOL
+    finally:
+        g.close()
