@@ -113,6 +113,10 @@ struct sw_grid {
   unsigned long long wait_limit_ns = 2000000000ull;  // bound of every mbarrier wait
   int sm_count = 0;
   CUtensorMap map_halo[2], map_inner[2], map_kappa;
+  // variable density on the pipelined path: D_z, D_y, D_x ln(rho) fields and their maps
+  float* glr[3] = {nullptr, nullptr, nullptr};
+  CUtensorMap map_g[3];
+  bool grad_ready = false;
 
   // profiling
   bool profiling = false;
@@ -320,10 +324,10 @@ sw_status build_tma_maps(sw_grid* g) {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // default bound of an mbarrier wait (2 s)
 
-template <int R, int TY, int PPT, int NB, int MINB, bool ISO>
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
 void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
-  using C = TmaConfig<R, TY, PPT, NB>;
-  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO>;
+  using C = TmaConfig<R, TY, PPT, NB, VD>;
+  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO, VD>;
   static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
   if (!blocks_per_sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
@@ -338,32 +342,51 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   wk.starve = g->starve ? 1 : 0;
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
+  const CUtensorMap* gm = VD ? g->map_g : nullptr;  // unused maps: kappa's
   kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf], g->map_inner[buf ^ 1],
-                                                g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
+                                                g->map_kappa, VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa,
+                                                VD ? gm[2] : g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
 }
 
-template <int R, int TY, int PPT, int NB, int MINB>
+template <int R, int TY, int PPT, int NB, int MINB, bool VD>
 void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   if (g->h[0] == g->h[1] && g->h[1] == g->h[2])
-    launch_tma_iso<R, TY, PPT, NB, MINB, true>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, true, VD>(g, a, buf, st);
   else
-    launch_tma_iso<R, TY, PPT, NB, MINB, false>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, false, VD>(g, a, buf, st);
 }
 
 // Tile height / rows per warp / ring depth / minimum CTAs per SM for each
-// radius (tile width 64).  tma_tile() must give the same tile shape.
+// radius (tile width 64), constant and variable density.  tma_tile() must
+// give the same tile shape.
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  if (g->has_density) {
+    switch (g->R) {
+      case 1: launch_tma_t<1, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 2: launch_tma_t<2, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 3: launch_tma_t<3, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 4: launch_tma_t<4, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 5: launch_tma_t<5, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 6: launch_tma_t<6, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 7: launch_tma_t<7, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 8: launch_tma_t<8, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 9: launch_tma_t<9, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 10: launch_tma_t<10, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      default: break;
+    }
+    return;
+  }
   switch (g->R) {
-    case 1: launch_tma_t<1, 16, 2, 5, 2>(g, a, buf, st); break;
-    case 2: launch_tma_t<2, 16, 2, 5, 2>(g, a, buf, st); break;
-    case 3: launch_tma_t<3, 16, 2, 5, 2>(g, a, buf, st); break;
-    case 4: launch_tma_t<4, 16, 2, 5, 2>(g, a, buf, st); break;
-    case 5: launch_tma_t<5, 16, 2, 4, 2>(g, a, buf, st); break;
-    case 6: launch_tma_t<6, 16, 2, 4, 2>(g, a, buf, st); break;
-    case 7: launch_tma_t<7, 16, 2, 4, 1>(g, a, buf, st); break;
-    case 8: launch_tma_t<8, 16, 2, 4, 1>(g, a, buf, st); break;
-    case 9: launch_tma_t<9, 16, 2, 4, 1>(g, a, buf, st); break;
-    case 10: launch_tma_t<10, 16, 2, 4, 1>(g, a, buf, st); break;
+    case 1: launch_tma_t<1, 16, 2, 5, 2, false>(g, a, buf, st); break;
+    case 2: launch_tma_t<2, 16, 2, 5, 2, false>(g, a, buf, st); break;
+    case 3: launch_tma_t<3, 16, 2, 5, 2, false>(g, a, buf, st); break;
+    case 4: launch_tma_t<4, 16, 2, 5, 2, false>(g, a, buf, st); break;
+    case 5: launch_tma_t<5, 16, 2, 4, 2, false>(g, a, buf, st); break;
+    case 6: launch_tma_t<6, 16, 2, 4, 2, false>(g, a, buf, st); break;
+    case 7: launch_tma_t<7, 16, 2, 4, 1, false>(g, a, buf, st); break;
+    case 8: launch_tma_t<8, 16, 2, 4, 1, false>(g, a, buf, st); break;
+    case 9: launch_tma_t<9, 16, 2, 4, 1, false>(g, a, buf, st); break;
+    case 10: launch_tma_t<10, 16, 2, 4, 1, false>(g, a, buf, st); break;
     default: break;
   }
 }
@@ -378,7 +401,7 @@ bool use_tma(const sw_grid* g) {
   const int64_t* n = g->lay.n;
   const int64_t items = (n[2] + 63) / 64 * ((n[1] + 15) / 16) * n[0];
   const int64_t lines = 2 * std::max(n[0] * n[1] * int64_t(g->R), std::max(n[0] * n[2], n[1] * n[2]));
-  return g->ndim == 3 && !g->has_density && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && n[0] > m &&
+  return g->ndim == 3 && (!g->has_density || g->grad_ready) && g->tma_ready && g->lay.sz < (int64_t(1) << 31) && n[0] > m &&
          n[1] > m && n[2] > m && items < (int64_t(1) << 31) && lines < (int64_t(1) << 31);
 }
 
@@ -640,6 +663,30 @@ sw_status sw_set_model(sw_grid* g, const float* velocity, const float* density) 
       mirror_even_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(g->at0(g->lnrho), f, axis, g->R);
       SW_CUDA(cudaGetLastError());
     }
+    if (g->ndim == 3 && g->tma_ready) {
+      // ln(rho) gradient fields for the pipelined kernel (Eq. 10 weights, FP64 sums)
+      for (int i = 0; i < 3; ++i)
+        if (!g->glr[i]) {
+          SW_TRY(dev_alloc(g, (void**)&g->glr[i], fbytes));
+          SW_CUDA(cudaMemsetAsync(g->glr[i], 0, fbytes, g->stream));  // ghosts and padding stay zero
+        }
+      GradWeights gw;
+      double wj[kMaxR + 1];
+      fd_first_weights(g->order, wj);
+      for (int j = 0; j <= kMaxR; ++j) {
+        const bool in = j >= 1 && j <= g->R;
+        gw.z[j] = in ? wj[j] / (2.0 * g->h[0]) : 0.0;
+        gw.y[j] = in ? wj[j] / (2.0 * g->h[1]) : 0.0;
+        gw.x[j] = in ? wj[j] / (2.0 * g->h[2]) : 0.0;
+      }
+      lnrho_gradient_kernel<<<grid_blocks(nn, 256), 256, 0, g->stream>>>(
+          g->at0(g->lnrho), g->at0(g->glr[0]), g->at0(g->glr[1]), g->at0(g->glr[2]), f, gw, g->R);
+      SW_CUDA(cudaGetLastError());
+      int tx, ty;
+      tma_tile(g->R, &tx, &ty);
+      for (int i = 0; i < 3; ++i) SW_TRY(make_map(g, g->glr[i], uint32_t(tx), uint32_t(ty), &g->map_g[i]));
+      g->grad_ready = true;
+    }
     g->has_density = true;
   } else {
     g->has_density = false;
@@ -864,6 +911,7 @@ void sw_destroy_grid(sw_grid* g) {
   dev_free(g, g->u[1], fbytes);
   dev_free(g, g->kappa, fbytes);
   dev_free(g, g->lnrho, fbytes);
+  for (int i = 0; i < 3; ++i) dev_free(g, g->glr[i], fbytes);
   dev_free(g, g->damp, size_t(g->damp_len) * sizeof(float2));
   dev_free(g, g->dflag, 64);
   dev_free(g, g->dscratch, 64);

@@ -179,6 +179,38 @@ __global__ void lnrho_kernel(const float* rho, float* lr, FaceInfo f) {
   }
 }
 
+// First-derivative weights w_j / (2 h) per axis (FP64), for the ln(rho)
+// gradient fields of the pipelined variable-density stencil.
+struct GradWeights {
+  double z[kMaxR + 1], y[kMaxR + 1], x[kMaxR + 1];
+};
+
+// g_axis = D_axis ln(rho) = sum_j w_j / (2 h) (lnrho(+j) - lnrho(-j)) (Eq. 10)
+// at every node of a 3D grid, from ln(rho) with its even-mirrored ghosts,
+// summed in FP64 and stored in FP32 in the padded layout.  Computed once per
+// model; the pipelined stencil then reads the three gradients instead of
+// differentiating ln(rho) every step.
+__global__ void lnrho_gradient_kernel(const float* lr, float* gz, float* gy, float* gx, FaceInfo f, GradWeights w,
+                                      int R) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    double dz = 0.0, dy = 0.0, dx = 0.0;
+    for (int j = 1; j <= R; ++j) {
+      dz += w.z[j] * (double(lr[k + j * f.sz]) - double(lr[k - j * f.sz]));
+      dy += w.y[j] * (double(lr[k + j * f.sy]) - double(lr[k - j * f.sy]));
+      dx += w.x[j] * (double(lr[k + j]) - double(lr[k - j]));
+    }
+    gz[k] = float(dz);
+    gy[k] = float(dy);
+    gx[k] = float(dx);
+  }
+}
+
 // Even mirror of a padded field into its R ghost layers along one axis
 // (axis 0 = z, 1 = y, 2 = x), over the node range of the two other axes.
 __global__ void mirror_even_kernel(float* f_, FaceInfo f, int axis, int R) {

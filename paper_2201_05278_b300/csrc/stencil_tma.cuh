@@ -1,16 +1,18 @@
 // Leapfrog stencil step for 3D grids, TMA-pipelined persistent version.
 //
 // Same arithmetic as stencil_plain.cuh (Eq. 7 with the damped coefficients,
-// Eq. 9 Laplacian in constant-annihilating form, fused face mirroring), but
-// the data movement is built for B300:
+// Eq. 9 Laplacian in constant-annihilating form; with VD the Eq. 10 term
+// - grad(ln rho) . grad(p), ln rho's gradient read from three precomputed
+// fields), but the data movement is built for B300:
 //   - persistent grid (SMs x resident CTAs); CTA b owns the contiguous range
 //     [total*b/G, total*(b+1)/G) of (xy-tile, z-plane) work items, so every
 //     CTA gets the same number of planes to within one;
 //   - the work of one plane arrives as a "bundle" of tensor copies
 //     (cp.async.bulk.tensor.3d) into one slot of an NB-deep shared-memory
 //     ring, completing on the slot's mbarrier: the centre plane p[n](c) with
-//     an R-row / XH-column halo, p[n-1](c), kappa(c), and the interior of the
-//     front plane p[n](c+R) that feeds the register z-queue.  A tile column
+//     an R-row / XH-column halo, p[n-1](c), kappa(c), the interior of the
+//     front plane p[n](c+R) that feeds the register z-queue, and with VD the
+//     three ln(rho) gradient components at plane c.  A tile column
 //     starts with 2R bundles that carry only a front plane (queue warm-up);
 //   - each thread keeps its columns' 2R+1 planes of p[n] in a register queue
 //     (shifted once per plane); the in-plane neighbours come from the centre
@@ -52,7 +54,7 @@ struct TmaWork {
 // j >= 2R, compute plane zb + j - 2R (2R warm-up bundles, then one per plane).
 __device__ __forceinline__ int segment_len(int u, int u1, int nz) { return min(u1 - u, nz - u % nz); }
 
-template <int R, int TY, int PPT, int NB>
+template <int R, int TY, int PPT, int NB, bool VD>
 struct TmaConfig {
   static constexpr int TX = 64;               // 32 lanes x 2 adjacent columns
   static constexpr int XH = (R + 3) / 4 * 4;  // x halo rounded to 16 bytes (TMA x alignment)
@@ -69,7 +71,8 @@ struct TmaConfig {
   // destination must be 128-byte aligned.
   static constexpr int C_FLOATS = int((C_BYTES + 127u) / 128u * 128u) / 4;
   static constexpr int I_FLOATS = int((I_BYTES + 127u) / 128u * 128u) / 4;
-  static constexpr int SLOT_FLOATS = C_FLOATS + 3 * I_FLOATS;  // centre, front, p[n-1], kappa
+  static constexpr int NI = VD ? 6 : 3;  // interior boxes: front, p[n-1], kappa (+ d/dz, d/dy, d/dx ln rho)
+  static constexpr int SLOT_FLOATS = C_FLOATS + NI * I_FLOATS;
   static constexpr size_t SMEM = size_t(NB) * SLOT_FLOATS * 4 + size_t(NB) * 8 + size_t(NB) * 4 + 16;
   static_assert((C_FLOATS * 4) % 128 == 0 && (I_FLOATS * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
   static_assert(kTileXMax % TX == 0 && kTileYMax % TY == 0 && TY % PPT == 0, "tile shape");
@@ -86,12 +89,14 @@ struct RingShared {
 // handled as a float2 with packed FP32x2 arithmetic.
 // ISO: all three spacings are equal, so one coefficient per j serves every
 // axis (fewer registers; same arithmetic).
-template <int R, int TY, int PPT, int NB, int MINB, bool ISO>
-__global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
+__global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     stencil_tma_kernel(const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_f,
                        const __grid_constant__ CUtensorMap map_o, const __grid_constant__ CUtensorMap map_k,
-                       const StencilArgs a, const TmaWork wk, int* err_flag, unsigned long long limit_ns) {
-  using C = TmaConfig<R, TY, PPT, NB>;
+                       const __grid_constant__ CUtensorMap map_gz, const __grid_constant__ CUtensorMap map_gy,
+                       const __grid_constant__ CUtensorMap map_gx, const StencilArgs a, const TmaWork wk,
+                       int* err_flag, unsigned long long limit_ns) {
+  using C = TmaConfig<R, TY, PPT, NB, VD>;
   constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW, NCW = C::NCW;
   extern __shared__ __align__(128) unsigned char smem[];
   float* slots = reinterpret_cast<float*>(smem);
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       mbar_arrive_expect_tx(bar, C::I_BYTES);
       tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
     } else {
-      mbar_arrive_expect_tx(bar, C::C_BYTES + 3u * C::I_BYTES);
+      mbar_arrive_expect_tx(bar, C::C_BYTES + uint32_t(C::NI) * C::I_BYTES);
       tma_load_3d(smem_addr(sb), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
       tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
       // p[n-1] and kappa are read once: they leave L2 first, so that p[n]
@@ -140,6 +145,11 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
       const uint64_t once = make_policy_evict_first();
       tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar, once);
       tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar, once);
+      if constexpr (VD) {
+        tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 3 * C::I_FLOATS), &map_gz, x0 + kXOff, y0 + R, zf - R, bar, once);
+        tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 4 * C::I_FLOATS), &map_gy, x0 + kXOff, y0 + R, zf - R, bar, once);
+        tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 5 * C::I_FLOATS), &map_gx, x0 + kXOff, y0 + R, zf - R, bar, once);
+      }
     }
     return true;
   };
@@ -155,6 +165,11 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
     prefetch_tensormap(&map_f);
     prefetch_tensormap(&map_o);
     prefetch_tensormap(&map_k);
+    if constexpr (VD) {
+      prefetch_tensormap(&map_gz);
+      prefetch_tensormap(&map_gy);
+      prefetch_tensormap(&map_gx);
+    }
     const int len0 = segment_len(u0, u1, nz);
     int n = 0;
     while (!wk.starve && n < NB && issue(n, u0, len0, n, 0)) ++n;
@@ -174,11 +189,17 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
   };
 
   float2 cz2[R + 1], cy2[R + 1], cx2[R + 1];  // coefficient pairs (ISO: one set)
+  float2 gz2[VD ? R + 1 : 1], gy2[VD ? R + 1 : 1], gx2[VD ? R + 1 : 1];  // first-derivative weights
 #pragma unroll
   for (int j = 1; j <= R; ++j) {
     cx2[j] = make_float2(a.cx[j], a.cx[j]);
     cy2[j] = ISO ? cx2[j] : make_float2(a.cy[j], a.cy[j]);
     cz2[j] = ISO ? cx2[j] : make_float2(a.cz[j], a.cz[j]);
+    if constexpr (VD) {
+      gx2[j] = make_float2(a.gx[j], a.gx[j]);
+      gy2[j] = ISO ? gx2[j] : make_float2(a.gy[j], a.gy[j]);
+      gz2[j] = ISO ? gx2[j] : make_float2(a.gz[j], a.gz[j]);
+    }
   }
   const int r0 = warp * PPT;  // first tile row of this warp
   float2 qz[PPT][QL];  // z-queue, shifted once per plane
@@ -292,6 +313,29 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB>::NT, MINB)
             ly = f2_fma(cy2[jj], f2_sub(f2_add(yw[i + R + jj], yw[i + R - jj]), p2), ly);
           }
           kl[i] = f2_add(f2_add(lz, lx), ly);
+          if constexpr (VD) {
+            // - grad(ln rho) . grad(p): first derivatives of p from the same
+            // neighbours (Eq. 10), ln rho's from the gradient boxes
+            float2 dz = make_float2(0.f, 0.f), dx = dz, dy = dz;
+#pragma unroll
+            for (int jj = 1; jj <= R; ++jj) {
+              dz = f2_fma(gz2[jj], f2_sub(qz[i][R + jj], qz[i][R - jj]), dz);
+              float2 xd;  // (x+jj) - (x-jj) for both columns
+              if (jj % 2 == 0) {
+                xd = f2_sub(w[H + jj / 2], w[H - jj / 2]);
+              } else {
+                xd = make_float2(w[H + (jj - 1) / 2].y - w[H - (jj + 1) / 2].y,
+                                 w[H + (jj + 1) / 2].x - w[H - (jj - 1) / 2].x);
+              }
+              dx = f2_fma(gx2[jj], xd, dx);
+              dy = f2_fma(gy2[jj], f2_sub(yw[i + R + jj], yw[i + R - jj]), dy);
+            }
+            const float2* G = reinterpret_cast<const float2*>(S + C::C_FLOATS + 3 * C::I_FLOATS) + r0 * (TX / 2) + lane;
+            const float2 lgz = G[i * (TX / 2)], lgy = G[C::I_FLOATS / 2 + i * (TX / 2)],
+                         lgx = G[C::I_FLOATS + i * (TX / 2)];
+            const float2 adv = f2_fma(lgy, dy, f2_fma(lgx, dx, f2_mul(lgz, dz)));
+            kl[i] = f2_sub(kl[i], adv);
+          }
         }
         if (!damped) {
           // outside the absorbing layer: a = 1, e = 0

@@ -56,11 +56,12 @@ def test_small_grids_all_orders(cuda_device, ndim, order, density):
     assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
 
 
+@pytest.mark.parametrize("density", [False, True])
 @pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20])
-def test_3d_both_stencil_kernels(cuda_device, order):
-    """The TMA-pipelined kernel (chosen automatically for 3D constant density) and the
-    shared-memory-plane kernel both match the oracle."""
-    w = small_case(3, order, False, seed=100 + order)
+def test_3d_both_stencil_kernels(cuda_device, order, density):
+    """The TMA-pipelined kernel (chosen automatically in 3D, constant or variable
+    density) and the shared-memory-plane kernel both match the oracle."""
+    w = small_case(3, order, density, seed=100 + order)
     s_ref, p_ref = run_oracle(w)
     s_tma, p_tma = run_gpu(w, expect_variant=api.SW_STENCIL_TMA)
     s_pl, p_pl = run_gpu(w, variant=api.SW_STENCIL_PLAIN, expect_variant=api.SW_STENCIL_PLAIN)
