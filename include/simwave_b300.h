@@ -160,12 +160,14 @@ sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
 sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_limit_ns);
 
 /*
- * Kernel timing.  With profiling on, sw_forward records CUDA events around
- * every stencil launch on the grid's stream; sw_get_profile returns the
- * summed stencil time and launch count of the last sw_forward and the
- * number of kernels it launched in total.
+ * Kernel timing.  With every = N > 0, sw_forward records CUDA events around
+ * every N-th stencil launch (time steps 0, N, 2N, ...) on the grid's stream
+ * (N = 1: all of them; a sample keeps the events' own cost out of the run);
+ * every = 0 turns timing off.  sw_get_profile returns, for the last
+ * sw_forward, the summed time of the timed stencil launches, how many were
+ * timed, and the number of kernels it launched in total.
  */
-sw_status sw_set_profiling(sw_grid* g, int enable);
+sw_status sw_set_profiling(sw_grid* g, int every);
 sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_launches,
                          int64_t* kernel_launches);
 

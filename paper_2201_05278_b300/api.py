@@ -155,12 +155,13 @@ def sw_get_stencil_variant(g: Grid) -> int:
     return v.value
 
 
-def sw_set_profiling(g: Grid, enable: bool = True) -> None:
-    _check(_lib.load().sw_set_profiling(g.handle, int(bool(enable))))
+def sw_set_profiling(g: Grid, every=1) -> None:
+    """Time every `every`-th stencil launch of sw_forward (True: all, False/0: none)."""
+    _check(_lib.load().sw_set_profiling(g.handle, int(every)))
 
 
 def sw_get_profile(g: Grid):
-    """(summed stencil ms, stencil launches, kernel launches) of the last sw_forward."""
+    """(summed ms of the timed stencil launches, timed launches, kernel launches) of the last sw_forward."""
     ms = ctypes.c_double()
     n1 = ctypes.c_int64()
     n2 = ctypes.c_int64()

@@ -102,6 +102,8 @@ struct sw_grid {
   int* src_first = nullptr;
   float* src_w = nullptr;
   float* wavelet = nullptr;
+  int64_t* tap_off = nullptr;  // source tap table of the pipelined path (n_src * taps)
+  float* tap_coef = nullptr;
   int* rec_first = nullptr;
   float* rec_w = nullptr;
 
@@ -119,7 +121,7 @@ struct sw_grid {
   bool grad_ready = false;
 
   // profiling
-  bool profiling = false;
+  int profiling = 0;  // time every profiling-th stencil launch (0: none)
   std::vector<cudaEvent_t> events;
   double stencil_ms = 0.0;
   int64_t stencil_launches = 0, kernel_launches = 0;
@@ -343,9 +345,9 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   const CUtensorMap* gm = VD ? g->map_g : nullptr;  // unused maps: kappa's
-  kern<<<unsigned(grid), C::NT, C::SMEM, st>>>(g->map_halo[buf], g->map_inner[buf], g->map_inner[buf ^ 1],
-                                                g->map_kappa, VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa,
-                                                VD ? gm[2] : g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
+  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, g->map_halo[buf], g->map_inner[buf],
+                   g->map_inner[buf ^ 1], g->map_kappa, VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa,
+                   VD ? gm[2] : g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
 }
 
 template <int R, int TY, int PPT, int NB, int MINB, bool VD>
@@ -418,6 +420,11 @@ PointSet point_set(const sw_grid* g, bool src) {
 }
 
 void free_acquisition(sw_grid* g) {
+  const size_t ntaps = size_t(g->n_src) * g->lz * g->ly * g->lx;
+  dev_free(g, g->tap_off, ntaps * sizeof(int64_t));
+  dev_free(g, g->tap_coef, ntaps * sizeof(float));
+  g->tap_off = nullptr;
+  g->tap_coef = nullptr;
   dev_free(g, g->src_first, size_t(g->n_src) * 3 * sizeof(int));
   dev_free(g, g->src_w, size_t(g->n_src) * 3 * g->L * sizeof(float));
   dev_free(g, g->rec_first, size_t(g->n_rec) * 3 * sizeof(int));
@@ -772,27 +779,45 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
 
   StencilArgs a = stencil_args(g);
   const PointSet src = point_set(g, true), rec = point_set(g, false);
-  if (g->profiling && g->events.size() < size_t(2 * n_steps)) {
+  const int timed = g->profiling ? (n_steps + g->profiling - 1) / g->profiling : 0;  // launches timed
+  if (timed && g->events.size() < size_t(2 * timed)) {
     size_t old = g->events.size();
-    g->events.resize(size_t(2 * n_steps));
+    g->events.resize(size_t(2 * timed));
     for (size_t i = old; i < g->events.size(); ++i) SW_CUDA(cudaEventCreate(&g->events[i]));
   }
   int64_t launches = 0;
   const int src_threads = g->n_src * g->lz * g->ly * g->lx;
   const bool tma = use_tma(g);
+  if (tma && src_threads > 0) {  // tap table of the sources (model and dt are fixed for the run)
+    if (!g->tap_off) {
+      SW_TRY(dev_alloc(g, (void**)&g->tap_off, size_t(src_threads) * sizeof(int64_t)));
+      SW_TRY(dev_alloc(g, (void**)&g->tap_coef, size_t(src_threads) * sizeof(float)));
+    }
+    source_taps_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(a.kappa, g->damp, src, f, g->tap_off,
+                                                                         g->tap_coef);
+    SW_CUDA(cudaGetLastError());
+    ++launches;
+  }
   for (int step = 0; step < n_steps; ++step) {
     float* pn = g->u[step & 1];
     float* pnm1 = g->u[(step + 1) & 1];
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
-    if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step], g->stream));
+    const bool time_it = g->profiling && step % g->profiling == 0;
+    const int ev = time_it ? 2 * (step / g->profiling) : 0;
+    if (time_it) SW_CUDA(cudaEventRecord(g->events[ev], g->stream));
     if (tma)
       launch_stencil_tma(g, a, step & 1, g->stream);
     else
       launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
-    if (g->profiling) SW_CUDA(cudaEventRecord(g->events[2 * step + 1], g->stream));
+    if (time_it) SW_CUDA(cudaEventRecord(g->events[ev + 1], g->stream));
     ++launches;
-    if (src_threads > 0) {  // before the face conditions, which mirror its increments
+    if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
+      launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, g->stream, a.pnm1,
+                       (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
+                       (const float*)g->wavelet, g->sig_stride, step);
+      ++launches;
+    } else if (src_threads > 0) {
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(
           a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
@@ -828,14 +853,12 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
                             g->stream));
   SW_TRY(check_device_flag(g));
   g->kernel_launches = launches;
-  g->stencil_launches = n_steps;
+  g->stencil_launches = timed;
   g->stencil_ms = 0.0;
-  if (g->profiling) {
-    for (int step = 0; step < n_steps; ++step) {
-      float ms = 0.f;
-      SW_CUDA(cudaEventElapsedTime(&ms, g->events[2 * step], g->events[2 * step + 1]));
-      g->stencil_ms += ms;
-    }
+  for (int i = 0; i < timed; ++i) {
+    float ms = 0.f;
+    SW_CUDA(cudaEventElapsedTime(&ms, g->events[2 * i], g->events[2 * i + 1]));
+    g->stencil_ms += ms;
   }
   return SW_OK;
 }
@@ -881,9 +904,10 @@ sw_status sw_get_stencil_variant(const sw_grid* g, int* variant) {
   return SW_OK;
 }
 
-sw_status sw_set_profiling(sw_grid* g, int enable) {
+sw_status sw_set_profiling(sw_grid* g, int every) {
   if (!g) return fail(SW_EINVAL, "NULL grid");
-  g->profiling = enable != 0;
+  if (every < 0) return fail(SW_EINVAL, "negative profiling stride");
+  g->profiling = every;
   return SW_OK;
 }
 

@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "layout.h"
+#include "tma.cuh"
 
 namespace sw {
 
@@ -75,6 +77,50 @@ __global__ void inject_sources_kernel(float* p, const float* kappa, const float2
   add_with_mirrors(p, idx, z, f.nz, f.sz, f.bc[0], f.bc[1], R, d);
   add_with_mirrors(p, idx, x, f.nx, 1, f.bc[4], f.bc[5], R, d);
   if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
+}
+
+// Tap table of the sources for the pipelined path, built once per forward
+// run: for every window node the offset of the node and kappa_k a_k d_k /
+// prod(h), the step-independent part of the Eq. 11 increment, as
+// inject_sources_kernel forms it.  Dirichlet face nodes get offset -1 (never
+// incremented).  No ghost images: the face conditions follow the injection.
+__global__ void source_taps_kernel(const float* kappa, const float2* damp, PointSet src, FaceInfo f,
+                                   int64_t* tap_off, float* tap_coef) {
+  const int taps = src.lz * src.ly * src.lx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= src.count * taps) return;
+  const int s = t / taps;
+  int rem = t % taps;
+  const int ix = rem % src.lx;
+  rem /= src.lx;
+  const int iy = rem % src.ly;
+  const int iz = rem / src.ly;
+  const float* w = src.w + int64_t(s) * 3 * src.L;
+  const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
+  const int z = src.first[3 * s] + iz, y = src.first[3 * s + 1] + iy, x = src.first[3 * s + 2] + ix;
+  const bool dir = (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
+                   (y == 0 && f.bc[2] == kBcDirichlet) || (y == f.ny - 1 && f.bc[3] == kBcDirichlet) ||
+                   (x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet);
+  const int64_t idx = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+  const int dz = face_distance(z, f.nz, f.nbl[0], f.nbl[1]);
+  const int dy = face_distance(y, f.ny, f.nbl[2], f.nbl[3]);
+  const int dx = face_distance(x, f.nx, f.nbl[4], f.nbl[5]);
+  const int d2 = dz * dz + dy * dy + dx * dx;
+  const float ca = d2 ? damp[d2].x : 1.f;
+  tap_off[t] = (dir || wgt == 0.f) ? -1 : idx;
+  tap_coef[t] = kappa[idx] * ca * wgt;
+}
+
+// Eq. 11 from the tap table: p[n+1]_k += coef_k S_s(t_n), one thread per tap.
+__global__ void inject_taps_kernel(float* p, const int64_t* tap_off, const float* tap_coef, int taps, int count,
+                                   const float* sig, int sig_stride, int step) {
+  griddep_launch_dependents();
+  griddep_wait();  // p[n+1] of the stencil launched before
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count * taps) return;
+  const int64_t k = tap_off[t];
+  if (k < 0) return;
+  atomicAdd(&p[k], tap_coef[t] * sig[int64_t(t / taps) * sig_stride + step]);
 }
 
 // Eq. 12: rec[step][r] = sum_k d_k p[n+1]_k, receiver r by one warp: lanes
@@ -307,6 +353,8 @@ struct FaceGrid {
 
 template <int R>
 __global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg) {
+  griddep_launch_dependents();
+  griddep_wait();  // p[n+1] of the stencil and the injection launched before
   int b = blockIdx.x;
   if (b < fg.rec) {
     const int r = b * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -330,6 +378,23 @@ __global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float
   if (t < 2 * f.nz * f.ny * R) face_x<R>(p, f, t);
 }
 
+// Launch with programmatic stream serialization: the kernel may start before
+// the previous kernel of the stream ends (it calls griddep_wait() first).
+template <typename... P, typename... A>
+inline void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 // Face conditions of p (3D, pipelined stencil) and, if rec.count > 0, the
 // receiver samples of this step, in one launch of 256-thread blocks.
 inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
@@ -341,16 +406,16 @@ inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const Poi
   fg.x = int((2 * int64_t(f.nz) * f.ny * R + 255) / 256);
   const unsigned grid = unsigned(fg.total());
   switch (R) {
-    case 1: face_conditions_kernel<1><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 2: face_conditions_kernel<2><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 3: face_conditions_kernel<3><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 4: face_conditions_kernel<4><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 5: face_conditions_kernel<5><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 6: face_conditions_kernel<6><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 7: face_conditions_kernel<7><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 8: face_conditions_kernel<8><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 9: face_conditions_kernel<9><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
-    case 10: face_conditions_kernel<10><<<grid, 256, 0, st>>>(p, f, rec, out, step, fg); break;
+    case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 2: launch_dependent(face_conditions_kernel<2>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 3: launch_dependent(face_conditions_kernel<3>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 4: launch_dependent(face_conditions_kernel<4>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 5: launch_dependent(face_conditions_kernel<5>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 6: launch_dependent(face_conditions_kernel<6>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 7: launch_dependent(face_conditions_kernel<7>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 8: launch_dependent(face_conditions_kernel<8>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 9: launch_dependent(face_conditions_kernel<9>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 10: launch_dependent(face_conditions_kernel<10>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
     default: break;
   }
 }

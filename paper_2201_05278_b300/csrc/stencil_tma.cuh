@@ -105,6 +105,10 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
   RingShared* ring = reinterpret_cast<RingShared*>(cnt + NB);
   volatile int* abort_flag = &ring->abort;
 
+  // launched after the previous step's kernels: wait for them before any
+  // global access (the next kernel may start as soon as every CTA is here)
+  griddep_launch_dependents();
+  griddep_wait();
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int u0 = int((long long)wk.total * blockIdx.x / gridDim.x);
