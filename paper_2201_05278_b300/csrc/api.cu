@@ -122,6 +122,24 @@ struct sw_grid {
 
   // profiling
   int profiling = 0;  // time every profiling-th stencil launch (0: none)
+  // the time loop of sw_forward as a CUDA graph: captured on the second call
+  // with an unchanged configuration, replayed while it stays unchanged
+  uint64_t config_gen = 0;  // bumped by every call that changes what sw_forward launches
+  struct ForwardKey {
+    int n_steps = -1;
+    const float* seis = nullptr;
+    int profiling = 0;
+    bool tma = false;
+    uint64_t gen = 0;
+    bool operator==(const ForwardKey& o) const {
+      return n_steps == o.n_steps && seis == o.seis && profiling == o.profiling && tma == o.tma && gen == o.gen;
+    }
+  };
+  ForwardKey last_key, graph_key;
+  bool last_key_valid = false;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_launches = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
   std::vector<cudaEvent_t> events;
   double stencil_ms = 0.0;
   int64_t stencil_launches = 0, kernel_launches = 0;
@@ -597,6 +615,7 @@ sw_status sw_create_grid(sw_grid** out, int ndim, const int64_t* shape, const do
 sw_status sw_set_model(sw_grid* g, const float* velocity, const float* density) {
   g_last_error.clear();
   if (!g || !velocity) return fail(SW_EINVAL, "NULL argument");
+  ++g->config_gen;
   const FaceInfo f = g->faces();
   const int64_t nn = g->nodes();
   const float* vdev = nullptr;
@@ -707,6 +726,7 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
                              int nt, const float* wavelet, int wavelet_per_source, int window_radius) {
   g_last_error.clear();
   if (!g) return fail(SW_EINVAL, "NULL grid");
+  ++g->config_gen;
   if (n_src < 0 || n_rec < 0 || nt < 0) return fail(SW_EINVAL, "negative count");
   if ((n_src > 0 && (!src_pos || !wavelet || nt == 0)) || (n_rec > 0 && !rec_pos))
     return fail(SW_EINVAL, "NULL positions or wavelet");
@@ -788,12 +808,17 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   int64_t launches = 0;
   const int src_threads = g->n_src * g->lz * g->ly * g->lx;
   const bool tma = use_tma(g);
+  // everything the time loop launches, in stream order
+  auto enqueue = [&](cudaStream_t st, bool capturing, int64_t* nl) -> sw_status {
+  // timing events become real event nodes of a captured graph
+  const unsigned evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  int64_t launches = 0;
   if (tma && src_threads > 0) {  // tap table of the sources (model and dt are fixed for the run)
     if (!g->tap_off) {
       SW_TRY(dev_alloc(g, (void**)&g->tap_off, size_t(src_threads) * sizeof(int64_t)));
       SW_TRY(dev_alloc(g, (void**)&g->tap_coef, size_t(src_threads) * sizeof(float)));
     }
-    source_taps_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(a.kappa, g->damp, src, f, g->tap_off,
+    source_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(a.kappa, g->damp, src, f, g->tap_off,
                                                                          g->tap_coef);
     SW_CUDA(cudaGetLastError());
     ++launches;
@@ -805,34 +830,73 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     a.pnm1 = g->at0(pnm1);
     const bool time_it = g->profiling && step % g->profiling == 0;
     const int ev = time_it ? 2 * (step / g->profiling) : 0;
-    if (time_it) SW_CUDA(cudaEventRecord(g->events[ev], g->stream));
+    if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
     if (tma)
-      launch_stencil_tma(g, a, step & 1, g->stream);
+      launch_stencil_tma(g, a, step & 1, st);
     else
-      launch_stencil(g->R, g->ndim, g->has_density, a, g->stream);
-    if (time_it) SW_CUDA(cudaEventRecord(g->events[ev + 1], g->stream));
+      launch_stencil(g->R, g->ndim, g->has_density, a, st);
+    if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev + 1], st, evflags));
     ++launches;
     if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
-      launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, g->stream, a.pnm1,
+      launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pnm1,
                        (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
                        (const float*)g->wavelet, g->sig_stride, step);
       ++launches;
     } else if (src_threads > 0) {
-      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g->stream>>>(
+      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
           a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
     }
     if (tma) {
       // the pipelined kernel writes node values only: the face conditions
       // follow, with the receiver samples in the same launch
-      launch_face_conditions(a.pnm1, f, g->R, rec, seis_dev, step, g->stream);
+      launch_face_conditions(a.pnm1, f, g->R, rec, seis_dev, step, st);
       ++launches;
     } else if (g->n_rec > 0) {
-      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, g->stream>>>(a.pnm1, rec, f, seis_dev, step);
+      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pnm1, rec, f, seis_dev, step);
       ++launches;
     }
   }
   SW_CUDA(cudaGetLastError());
+  *nl = launches;
+  return SW_OK;
+  };
+  const sw_grid::ForwardKey key{n_steps, seis_dev, g->profiling, tma, g->config_gen};
+  if (n_steps > 0 && g->graph && g->graph_key == key) {
+    SW_CUDA(cudaGraphLaunch(g->graph, g->stream));
+    launches = g->graph_launches;
+  } else if (n_steps > 0 && g->last_key_valid && g->last_key == key) {
+    // second call with this configuration: capture the time loop once
+    if (g->graph) {
+      cudaGraphExecDestroy(g->graph);
+      g->graph = nullptr;
+    }
+    // captured on a private stream (the grid's stream may be the legacy
+    // default stream, which cannot be captured), launched on the grid's
+    if (!g->cap_stream) SW_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    SW_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const sw_status st = enqueue(g->cap_stream, true, &launches);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (st != SW_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != SW_OK ? st : fail(SW_ECUDA, "capturing the time loop failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      g->graph = nullptr;
+      return fail(SW_ECUDA, "instantiating the time loop failed: %s", cudaGetErrorString(ei));
+    }
+    g->graph_key = key;
+    g->graph_launches = launches;
+    SW_CUDA(cudaGraphLaunch(g->graph, g->stream));
+  } else if (n_steps > 0) {
+    SW_TRY(enqueue(g->stream, false, &launches));
+  }
+  g->last_key = key;
+  g->last_key_valid = true;
   if (final_field) {
     float* last = g->at0(g->u[n_steps & 1]);
     const bool fh = !is_device_pointer(final_field);
@@ -888,6 +952,7 @@ sw_status sw_set_stencil_variant(sw_grid* g, int variant) {
     return fail(SW_EINVAL, "unknown stencil variant %d", variant);
   if (variant == SW_STENCIL_TMA && g->ndim != 3) return fail(SW_EINVAL, "the pipelined stencil is 3D only");
   g->variant = variant;
+  ++g->config_gen;
   return SW_OK;
 }
 
@@ -895,6 +960,7 @@ sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_l
   if (!g) return fail(SW_EINVAL, "NULL grid");
   g->starve = starve != 0;
   g->wait_limit_ns = wait_limit_ns ? wait_limit_ns : kWaitLimitNs;
+  ++g->config_gen;
   return SW_OK;
 }
 
@@ -908,6 +974,7 @@ sw_status sw_set_profiling(sw_grid* g, int every) {
   if (!g) return fail(SW_EINVAL, "NULL grid");
   if (every < 0) return fail(SW_EINVAL, "negative profiling stride");
   g->profiling = every;
+  ++g->config_gen;
   return SW_OK;
 }
 
@@ -929,6 +996,8 @@ sw_status sw_get_device_bytes(const sw_grid* g, int64_t* bytes) {
 void sw_destroy_grid(sw_grid* g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   free_acquisition(g);
   const size_t fbytes = size_t(g->lay.total) * sizeof(float);
   dev_free(g, g->u[0], fbytes);
