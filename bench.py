@@ -290,7 +290,10 @@ def main():
             "config": {"workload": args.workload, "grid": list(w.shape), "space_order": w.order,
                        "time_steps_per_forward": w.n_steps, "receivers": n_rec, "sources": len(w.src_pos),
                        "variable_density": vd, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+                       "l2": ("inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6))
+                       if alg_bytes > 126e6 else
+                       ("working set fits in L2 (%.1f MB per time step): latency-bound, HBM is not the bound"
+                        % (alg_bytes / 1e6))},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "stencil (CUDA events around every %dth launch, %d launches timed)" % (

@@ -242,15 +242,8 @@ void launch_stencil_t(StencilArgs a, cudaStream_t st) {
     dim3 grid(tiles_x, tiles_y, (a.nz + zc - 1) / zc);
     stencil_plain_kernel<R, 3, VD, TX, TY, PPT><<<grid, TX * (TY / PPT), 0, st>>>(a);
   } else {
-    constexpr int TX = 128;
-    const int tiles_x = (a.nx + TX - 1) / TX;
-    const int target = 148 * 4;
-    int chunks = (target + tiles_x - 1) / tiles_x;
-    int zc = (a.nz + chunks - 1) / chunks;
-    if (zc < 4 * R) zc = 4 * R;
-    a.zchunk = zc;
-    dim3 grid(tiles_x, 1, (a.nz + zc - 1) / zc);
-    stencil_plain_kernel<R, 2, VD, TX, 1, 1><<<grid, TX, 0, st>>>(a);
+    const dim3 grid((a.nx + 127) / 128, std::min(a.nz, 65535));  // one thread per node
+    stencil_2d_kernel<R, VD><<<grid, 128, 0, st>>>(a);
   }
 }
 

@@ -208,4 +208,68 @@ __global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const Sten
   }
 }
 
+// 2D: one thread per node, every neighbour read from global memory (the
+// fields of a 2D grid are a few MB and stay in L2; marching along z with a
+// shared plane would leave most SMs idle on such grids).  Same arithmetic
+// and face handling as stencil_plain_kernel; one block row of 128 nodes
+// per (x tile, z) pair.
+template <int R, bool VD>
+__device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int x) {
+  const int64_t sz = a.sz;
+  const int64_t idx = int64_t(z) * sz + x;
+  const float* p = a.pn;
+  float qz[2 * R + 1], qx[2 * R + 1];
+#pragma unroll
+  for (int j = -R; j <= R; ++j) {
+    qz[j + R] = __ldg(&p[idx + j * sz]);
+    qx[j + R] = __ldg(&p[idx + j]);
+  }
+  const float po = a.pnm1[idx];
+  const float kp = __ldg(&a.kappa[idx]);
+  const float pc = qz[R];
+  const float p2 = 2.f * pc;
+  float lap = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    lap = fmaf(a.cz[j], (qz[R + j] + qz[R - j]) - p2, lap);
+    lap = fmaf(a.cx[j], (qx[R + j] + qx[R - j]) - p2, lap);
+  }
+  if constexpr (VD) {
+    const float* l = a.lnrho;
+    float dpz = 0.f, dlz = 0.f, dpx = 0.f, dlx = 0.f;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      dpz = fmaf(a.gz[j], qz[R + j] - qz[R - j], dpz);
+      dlz = fmaf(a.gz[j], __ldg(&l[idx + j * sz]) - __ldg(&l[idx - j * sz]), dlz);
+      dpx = fmaf(a.gx[j], qx[R + j] - qx[R - j], dpx);
+      dlx = fmaf(a.gx[j], __ldg(&l[idx + j]) - __ldg(&l[idx - j]), dlx);
+    }
+    lap -= dlz * dpz + dlx * dpx;
+  }
+  const int dz = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+  const int dx = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
+  const int d2 = dz * dz + dx * dx;
+  float ca = 1.f, e = 0.f;
+  if (d2 != 0) {
+    const float2 c = __ldg(&a.damp[d2]);
+    ca = c.x;
+    e = c.y;
+  }
+  const float dp = pc - po;
+  float pnew = ca * (pc + fmaf(kp, lap, fmaf(e, po, dp)));
+  const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
+                   (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet);
+  if (dir) pnew = 0.f;
+  a.pnm1[idx] = pnew;
+  mirror_ghosts<R>(a.pnm1, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
+  mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
+}
+
+template <int R, bool VD>
+__global__ void __launch_bounds__(128) stencil_2d_kernel(const StencilArgs a) {
+  const int x = blockIdx.x * 128 + threadIdx.x;
+  if (x >= a.nx) return;
+  for (int z = blockIdx.y; z < a.nz; z += gridDim.y) stencil_2d_node<R, VD>(a, z, x);
+}
+
 }  // namespace sw
