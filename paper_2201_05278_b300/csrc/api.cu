@@ -371,7 +371,10 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t 
 
 // Tile height / rows per warp / ring depth / minimum CTAs per SM for each
 // radius (tile width 64), constant and variable density.  tma_tile() must
-// give the same tile shape.
+// give the same tile shape.  Radii up to 4: four rows per thread in 4-warp
+// CTAs, three per SM, three bundles in flight each (fastest on the order-8
+// bench workload: 70.8 against 80.2 us for two rows per thread in 8-warp
+// CTAs); larger radii keep two rows per thread (four would spill).
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   if (g->has_density) {
     switch (g->R) {
@@ -390,10 +393,10 @@ void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStr
     return;
   }
   switch (g->R) {
-    case 1: launch_tma_t<1, 16, 2, 5, 2, false>(g, a, buf, st); break;
-    case 2: launch_tma_t<2, 16, 2, 5, 2, false>(g, a, buf, st); break;
-    case 3: launch_tma_t<3, 16, 2, 5, 2, false>(g, a, buf, st); break;
-    case 4: launch_tma_t<4, 16, 2, 5, 2, false>(g, a, buf, st); break;
+    case 1: launch_tma_t<1, 16, 4, 3, 3, false>(g, a, buf, st); break;
+    case 2: launch_tma_t<2, 16, 4, 3, 3, false>(g, a, buf, st); break;
+    case 3: launch_tma_t<3, 16, 4, 3, 3, false>(g, a, buf, st); break;
+    case 4: launch_tma_t<4, 16, 4, 3, 3, false>(g, a, buf, st); break;
     case 5: launch_tma_t<5, 16, 2, 4, 2, false>(g, a, buf, st); break;
     case 6: launch_tma_t<6, 16, 2, 4, 2, false>(g, a, buf, st); break;
     case 7: launch_tma_t<7, 16, 2, 4, 1, false>(g, a, buf, st); break;
