@@ -375,17 +375,20 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t 
 // CTAs, three per SM, three bundles in flight each (fastest on the order-8
 // bench workload: 70.8 against 80.2 us for two rows per thread in 8-warp
 // CTAs); larger radii keep two rows per thread (four would spill).
+// Variable density: four rows per thread in 4-warp CTAs with three bundles
+// (730 against 863 us per launch at order 16 on 512 x 512 x 384) up to
+// radius 8, two rows in 8-warp CTAs above.
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   if (g->has_density) {
     switch (g->R) {
-      case 1: launch_tma_t<1, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 2: launch_tma_t<2, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 3: launch_tma_t<3, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 4: launch_tma_t<4, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 5: launch_tma_t<5, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 6: launch_tma_t<6, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 7: launch_tma_t<7, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 8: launch_tma_t<8, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 1: launch_tma_t<1, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 2: launch_tma_t<2, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 3: launch_tma_t<3, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 4: launch_tma_t<4, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 5: launch_tma_t<5, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 6: launch_tma_t<6, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 7: launch_tma_t<7, 16, 4, 3, 1, true>(g, a, buf, st); break;
+      case 8: launch_tma_t<8, 16, 4, 3, 1, true>(g, a, buf, st); break;
       case 9: launch_tma_t<9, 16, 2, 5, 1, true>(g, a, buf, st); break;
       case 10: launch_tma_t<10, 16, 2, 5, 1, true>(g, a, buf, st); break;
       default: break;
