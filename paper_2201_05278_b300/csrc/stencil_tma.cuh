@@ -75,7 +75,9 @@ struct TmaConfig {
   static constexpr int SLOT_FLOATS = C_FLOATS + NI * I_FLOATS;
   static constexpr size_t SMEM = size_t(NB) * SLOT_FLOATS * 4 + size_t(NB) * 8 + size_t(NB) * 4 + 16;
   static_assert((C_FLOATS * 4) % 128 == 0 && (I_FLOATS * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
-  static_assert(kTileXMax % TX == 0 && kTileYMax % TY == 0 && TY % PPT == 0, "tile shape");
+  // tiles past the last row read zero-filled rows (tensor copies clip at the
+  // field's extent) and store nothing there
+  static_assert(kTileXMax % TX == 0 && TY <= kTileYMax && TY % PPT == 0, "tile shape");
   static_assert(PW <= 256 && PH <= 256 && XH % 2 == 0, "TMA box extent / float2 alignment");
 };
 
@@ -221,14 +223,16 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;  // per lane
     // some lane lies past the last column or some row past the last row
     const bool ragged = __any_sync(0xffffffffu, !vb_ok) || y0 + r0 + PPT > a.ny;
-    const int dxa = layer_distance(x, a.nx, a.nbl[4], a.nbl[5]);
-    const int dxb = layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]);
+    // nodes past the last column or row (ragged tiles; never stored) take
+    // distance 0, so every damping-table index stays inside the table
+    const int dxa = va_ok ? layer_distance(x, a.nx, a.nbl[4], a.nbl[5]) : 0;
+    const int dxb = vb_ok ? layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]) : 0;
     int d2xy_a[PPT], d2xy_b[PPT];
     bool xy_free = true;  // no node of the warp's rows is in the absorbing layer in x, y
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int y = y0 + r0 + i;
-      const int dyl = layer_distance(y, a.ny, a.nbl[2], a.nbl[3]);
+      const int dyl = y < a.ny ? layer_distance(y, a.ny, a.nbl[2], a.nbl[3]) : 0;
       d2xy_a[i] = dyl * dyl + dxa * dxa;
       d2xy_b[i] = dyl * dyl + dxb * dxb;
       xy_free = xy_free && (d2xy_a[i] | d2xy_b[i]) == 0;
