@@ -43,6 +43,24 @@ def _dist():
     return world, rank, local
 
 
+def job_seconds(local_seconds, world, device=None):
+    """Wall time of the whole job: the slowest rank's (all ranks run their own
+    replica and finish when the last one does).  Needs an initialised process
+    group when world > 1 (NCCL on the GPUs, gloo in the CPU tests)."""
+    if world == 1:
+        return float(local_seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(updates_per_replica, replicas_per_rank, world, seconds):
+    """Whole-job Gpts/s: every rank's updates over the job's wall time."""
+    return updates_per_replica * replicas_per_rank * world / seconds / 1e9
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -242,15 +260,9 @@ def main():
     stop.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = start.elapsed_time(stop)
-    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms = job_seconds(start.elapsed_time(stop) * 1e-3, world, dev) * 1e3
     api.sw_set_profiling(g, False)
-
-    updates = w.updates * args.steps * world
-    value = updates / (elapsed_ms * 1e-3) / 1e9
+    value = job_throughput(w.updates, args.steps, world, elapsed_ms * 1e-3)
 
     # e2e through the C ABI with host buffers: H2D of the velocity model every step
     # (sw_set_model from pinned host memory) and D2H of the seismogram.
@@ -266,11 +278,8 @@ def main():
             api.sw_forward(g, w.n_steps, seis_h, None)
             _ = float(seis_h[-1, 0])
         barrier()
-        e2e_s = time.perf_counter() - t0
-        e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e_value = w.updates * args.e2e_steps * world / float(e2e_t.item()) / 1e9
+        e2e_s = job_seconds(time.perf_counter() - t0, world, dev)
+        e2e_value = job_throughput(w.updates, args.e2e_steps, world, e2e_s)
         h2d = w.velocity.nbytes + (0 if w.density is None else w.density.nbytes)
         e2e = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": seis_h.numel() * 4}
