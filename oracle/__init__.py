@@ -12,6 +12,8 @@ Contents (paper section / equation):
   damping.py  absorbing-layer profile eta = alpha d^p (Eq. 4)
   oracle.c    leapfrog loop of Eq. 7 with ghost nodes and face conditions
   solver.py   forward(): setup + call into oracle.c
+  adjoint.py  exact discrete adjoint of the same recurrence and the misfit
+              gradient w.r.t. velocity (beyond the paper: its FWI use)
 
 Pins: every function is checked against something other than itself in
 tests/test_oracle_*.py (closed forms, textbook values, the paper's printed
