@@ -126,6 +126,33 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
 sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_field);
 
 /* Time step in use (after sw_set_model when dt was automatic). */
+/*
+ * Misfit gradient by the adjoint-state method.  The paper names full-waveform
+ * inversion as the solver's use but prints no adjoint; this is the exact
+ * discrete adjoint of the forward recurrence sw_forward runs (constant
+ * density only).  sw_gradient runs the forward simulation of the current
+ * model and acquisition for n_steps, the misfit
+ *   J = 1/2 sum_n sum_r (d[n][r] - observed[n][r])^2
+ * of its seismogram d against `observed`, and the adjoint sweep backwards in
+ * time, and returns J and dJ/dc, the derivative with respect to the velocity
+ * at every node.
+ *   observed         [n_steps][n_rec] FP32, device or host (copied)
+ *   misfit           host, one double
+ *   grad_vel         [nz][ny][nx] FP32 (2D: [nz][nx]), device or host
+ *   checkpoint_every forward states kept every K time steps (0: K about
+ *                    sqrt(2 n_steps)); each segment is recomputed during the
+ *                    adjoint sweep.  Device memory for the call, freed before
+ *                    it returns: (2 n_steps / K + K + 4) padded wavefields
+ *                    plus three [n_steps][n_rec] arrays.
+ * Errors: SW_ESTATE before sw_set_model / sw_set_acquisition; SW_EINVAL with
+ * a density model, without receivers, for n_steps < 1 or beyond the
+ * wavelet, or with 2R+1 nodes or fewer along an axis; SW_ENOMEM when the
+ * buffers do not fit.  The grid's wavefields
+ * hold the forward run's last two levels afterwards.
+ */
+sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
+                      int checkpoint_every);
+
 sw_status sw_get_dt(const sw_grid* g, double* dt);
 
 /*

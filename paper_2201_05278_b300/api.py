@@ -127,6 +127,15 @@ def sw_forward(g: Grid, n_steps: int, seismogram=None, final_field=None) -> None
     _check(_lib.load().sw_forward(g.handle, int(n_steps), _ptr(seismogram), _ptr(final_field)))
 
 
+def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int = 0) -> float:
+    """Misfit J = 1/2 |d - observed|^2 of a forward run and dJ/dvelocity into
+    grad_vel (adjoint-state method, constant density); returns J."""
+    j = ctypes.c_double()
+    _check(_lib.load().sw_gradient(g.handle, int(n_steps), _ptr(observed), ctypes.byref(j), _ptr(grad_vel),
+                                   int(checkpoint_every)))
+    return j.value
+
+
 def sw_get_dt(g: Grid) -> float:
     v = ctypes.c_double()
     _check(_lib.load().sw_get_dt(g.handle, ctypes.byref(v)))

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -337,8 +338,16 @@ sw_status build_tma_maps(sw_grid* g) {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // default bound of an mbarrier wait (2 s)
 
+// Tensor maps of one stencil launch: p[n] with halo and interior, p[n-1]
+// interior.
+struct StepMaps {
+  const CUtensorMap* halo;
+  const CUtensorMap* inner;
+  const CUtensorMap* old;
+};
+
 template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
-void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+void launch_tma_iso(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
   using C = TmaConfig<R, TY, PPT, NB, VD>;
   auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO, VD>;
   static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
@@ -356,17 +365,17 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   const CUtensorMap* gm = VD ? g->map_g : nullptr;  // unused maps: kappa's
-  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, g->map_halo[buf], g->map_inner[buf],
-                   g->map_inner[buf ^ 1], g->map_kappa, VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa,
-                   VD ? gm[2] : g->map_kappa, a, wk, g->dflag, g->wait_limit_ns);
+  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, *m.halo, *m.inner, *m.old, g->map_kappa,
+                   VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa, VD ? gm[2] : g->map_kappa, a, wk, g->dflag,
+                   g->wait_limit_ns);
 }
 
 template <int R, int TY, int PPT, int NB, int MINB, bool VD>
-void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+void launch_tma_t(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
   if (g->h[0] == g->h[1] && g->h[1] == g->h[2])
-    launch_tma_iso<R, TY, PPT, NB, MINB, true, VD>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, true, VD>(g, a, m, st);
   else
-    launch_tma_iso<R, TY, PPT, NB, MINB, false, VD>(g, a, buf, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, false, VD>(g, a, m, st);
 }
 
 // Tile height / rows per warp / ring depth / minimum CTAs per SM for each
@@ -378,36 +387,59 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t 
 // Variable density: four rows per thread in 4-warp CTAs with three bundles
 // (730 against 863 us per launch at order 16 on 512 x 512 x 384) up to
 // radius 8, two rows in 8-warp CTAs above.
-void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
   if (g->has_density) {
     switch (g->R) {
-      case 1: launch_tma_t<1, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 2: launch_tma_t<2, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 3: launch_tma_t<3, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 4: launch_tma_t<4, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 5: launch_tma_t<5, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 6: launch_tma_t<6, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 7: launch_tma_t<7, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 8: launch_tma_t<8, 16, 4, 3, 1, true>(g, a, buf, st); break;
-      case 9: launch_tma_t<9, 16, 2, 5, 1, true>(g, a, buf, st); break;
-      case 10: launch_tma_t<10, 16, 2, 5, 1, true>(g, a, buf, st); break;
+      case 1: launch_tma_t<1, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 2: launch_tma_t<2, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 3: launch_tma_t<3, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 4: launch_tma_t<4, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 5: launch_tma_t<5, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 6: launch_tma_t<6, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 7: launch_tma_t<7, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 8: launch_tma_t<8, 16, 4, 3, 1, true>(g, a, m, st); break;
+      case 9: launch_tma_t<9, 16, 2, 5, 1, true>(g, a, m, st); break;
+      case 10: launch_tma_t<10, 16, 2, 5, 1, true>(g, a, m, st); break;
       default: break;
     }
     return;
   }
   switch (g->R) {
-    case 1: launch_tma_t<1, 16, 4, 3, 3, false>(g, a, buf, st); break;
-    case 2: launch_tma_t<2, 16, 4, 3, 3, false>(g, a, buf, st); break;
-    case 3: launch_tma_t<3, 16, 4, 3, 3, false>(g, a, buf, st); break;
-    case 4: launch_tma_t<4, 16, 4, 3, 3, false>(g, a, buf, st); break;
-    case 5: launch_tma_t<5, 16, 2, 4, 2, false>(g, a, buf, st); break;
-    case 6: launch_tma_t<6, 16, 2, 4, 2, false>(g, a, buf, st); break;
-    case 7: launch_tma_t<7, 16, 2, 4, 1, false>(g, a, buf, st); break;
-    case 8: launch_tma_t<8, 16, 2, 4, 1, false>(g, a, buf, st); break;
-    case 9: launch_tma_t<9, 16, 2, 4, 1, false>(g, a, buf, st); break;
-    case 10: launch_tma_t<10, 16, 2, 4, 1, false>(g, a, buf, st); break;
+    case 1: launch_tma_t<1, 16, 4, 3, 3, false>(g, a, m, st); break;
+    case 2: launch_tma_t<2, 16, 4, 3, 3, false>(g, a, m, st); break;
+    case 3: launch_tma_t<3, 16, 4, 3, 3, false>(g, a, m, st); break;
+    case 4: launch_tma_t<4, 16, 4, 3, 3, false>(g, a, m, st); break;
+    case 5: launch_tma_t<5, 16, 2, 4, 2, false>(g, a, m, st); break;
+    case 6: launch_tma_t<6, 16, 2, 4, 2, false>(g, a, m, st); break;
+    case 7: launch_tma_t<7, 16, 2, 4, 1, false>(g, a, m, st); break;
+    case 8: launch_tma_t<8, 16, 2, 4, 1, false>(g, a, m, st); break;
+    case 9: launch_tma_t<9, 16, 2, 4, 1, false>(g, a, m, st); break;
+    case 10: launch_tma_t<10, 16, 2, 4, 1, false>(g, a, m, st); break;
     default: break;
   }
+}
+
+// The time loop's step: p[n] in u[buf], p[n-1] and p[n+1] in u[buf ^ 1].
+void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
+  const StepMaps m{&g->map_halo[buf], &g->map_inner[buf], &g->map_inner[buf ^ 1]};
+  launch_stencil_tma_maps(g, a, m, st);
+}
+
+void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, const float* kappa, float* gk,
+                  const FaceInfo& f, const LapCoef& lc, cudaStream_t st) {
+#define SW_IMAGE(RR)                                                                            \
+  case RR:                                                                                       \
+    if (ndim == 3)                                                                               \
+      image_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, kappa, gk, f, lc);                       \
+    else                                                                                         \
+      image_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, kappa, gk, f, lc);                       \
+    break;
+  switch (R) {
+    SW_IMAGE(1) SW_IMAGE(2) SW_IMAGE(3) SW_IMAGE(4) SW_IMAGE(5)
+    SW_IMAGE(6) SW_IMAGE(7) SW_IMAGE(8) SW_IMAGE(9) SW_IMAGE(10)
+    default: break;
+  }
+#undef SW_IMAGE
 }
 
 bool use_tma(const sw_grid* g) {
@@ -827,6 +859,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     float* pnm1 = g->u[(step + 1) & 1];
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
+    a.pout = g->at0(pnm1);
     const bool time_it = g->profiling && step % g->profiling == 0;
     const int ev = time_it ? 2 * (step / g->profiling) : 0;
     if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
@@ -837,22 +870,22 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev + 1], st, evflags));
     ++launches;
     if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
-      launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pnm1,
+      launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pout,
                        (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
                        (const float*)g->wavelet, g->sig_stride, step);
       ++launches;
     } else if (src_threads > 0) {
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
-          a.pnm1, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
+          a.pout, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
     }
     if (tma) {
       // the pipelined kernel writes node values only: the face conditions
       // follow, with the receiver samples in the same launch
-      launch_face_conditions(a.pnm1, f, g->R, rec, seis_dev, step, st);
+      launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st);
       ++launches;
     } else if (g->n_rec > 0) {
-      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pnm1, rec, f, seis_dev, step);
+      sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pout, rec, f, seis_dev, step);
       ++launches;
     }
   }
@@ -923,6 +956,179 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     SW_CUDA(cudaEventElapsedTime(&ms, g->events[2 * i], g->events[2 * i + 1]));
     g->stencil_ms += ms;
   }
+  return SW_OK;
+}
+
+sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
+                      int checkpoint_every) {
+  g_last_error.clear();
+  if (!g || !observed || !misfit || !grad_vel) return fail(SW_EINVAL, "NULL argument");
+  if (!g->has_model) return fail(SW_ESTATE, "sw_gradient before sw_set_model");
+  if (!g->has_acq) return fail(SW_ESTATE, "sw_gradient before sw_set_acquisition");
+  if (g->has_density) return fail(SW_EINVAL, "the gradient is built for constant density only");
+  if (g->n_rec <= 0) return fail(SW_EINVAL, "the gradient needs receivers");
+  if (n_steps < 1) return fail(SW_EINVAL, "n_steps < 1");
+  if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
+  if (checkpoint_every < 0) return fail(SW_EINVAL, "checkpoint_every < 0");
+  if (g->n[0] > 65535 || g->n[1] > 65535) return fail(SW_EINVAL, "axis longer than 65535 nodes");
+  for (int ax = 0; ax < 3; ++ax)  // the face passes need every node within R of one face only
+    if ((g->ndim == 3 || ax != 1) && g->n[ax] <= 2 * int64_t(g->R) + 1)
+      return fail(SW_EINVAL, "the gradient needs more than 2R+1 nodes along every axis");
+  const int N = n_steps;
+  int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, int(std::lround(std::sqrt(2.0 * N))));
+  K = std::min(K, N);
+  const int nseg = (N + K - 1) / K;
+  const FaceInfo f = g->faces();
+  const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+  const bool tma = use_tma(g);
+  cudaStream_t st = g->stream;
+
+  // device memory of this call: checkpoint pairs, segment states, psi, dJ/dkappa
+  const int nfields = 2 * nseg + (K + 1) + 2 + 1;
+  std::vector<float*> F(size_t(nfields), nullptr);
+  float *syn = nullptr, *obs = nullptr, *res = nullptr;
+  double* macc = nullptr;
+  const size_t sbytes = size_t(N) * g->n_rec * sizeof(float);
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    for (float*& p : F) {
+      dev_free(g, p, fbytes);
+      p = nullptr;
+    }
+    dev_free(g, syn, sbytes);
+    dev_free(g, obs, sbytes);
+    dev_free(g, res, sbytes);
+    dev_free(g, macc, sizeof(double));
+  };
+  struct Guard {
+    std::function<void()> fn;
+    ~Guard() { fn(); }
+  } guard{release};
+  for (float*& p : F) {
+    SW_TRY(dev_alloc(g, (void**)&p, fbytes));
+    SW_CUDA(cudaMemsetAsync(p, 0, fbytes, st));
+  }
+  SW_TRY(dev_alloc(g, (void**)&syn, sbytes));
+  SW_TRY(dev_alloc(g, (void**)&obs, sbytes));
+  SW_TRY(dev_alloc(g, (void**)&res, sbytes));
+  SW_TRY(dev_alloc(g, (void**)&macc, sizeof(double)));
+  SW_CUDA(cudaMemcpyAsync(obs, observed, sbytes, cudaMemcpyDefault, st));
+  SW_CUDA(cudaMemsetAsync(macc, 0, sizeof(double), st));
+  auto ck = [&](int sgm, int i) { return F[size_t(2 * sgm + i)]; };  // i = 0: p[k0-1], 1: p[k0]
+  auto B = [&](int j) { return F[size_t(2 * nseg + j)]; };            // p[k0 + j - 1]
+  auto PSI = [&](int i) { return F[size_t(2 * nseg + K + 1 + i)]; };
+  float* GK = F[size_t(nfields - 1)];
+  std::vector<CUtensorMap> halo(static_cast<size_t>(nfields)), inner(static_cast<size_t>(nfields));
+  if (tma) {
+    int tx, ty;
+    tma_tile(g->R, &tx, &ty);
+    const uint32_t xh = uint32_t((g->R + 3) / 4 * 4);
+    for (int i = 2 * nseg; i < nfields - 1; ++i) {  // segment states and psi
+      SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &halo[size_t(i)]));
+      SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &inner[size_t(i)]));
+    }
+  }
+  auto idx = [&](float* p) { return size_t(std::find(F.begin(), F.end(), p) - F.begin()); };
+
+  StencilArgs a = stencil_args(g);
+  const PointSet src = point_set(g, true), rec = point_set(g, false);
+  PointSet none = rec;
+  none.count = 0;
+  const int src_threads = g->n_src * g->lz * g->ly * g->lx;
+  LapCoef lc;
+  for (int j = 0; j <= kMaxR; ++j) {
+    lc.c[0][j] = a.cz[j];
+    lc.c[1][j] = a.cy[j];
+    lc.c[2][j] = a.cx[j];
+  }
+  // one step p[n] (pn), p[n-1] (pm) -> p[n+1] (po), with sources at step n
+  auto step = [&](float* pn, float* pm, float* po, const StepMaps* m, int n, const float* sig, int sig_stride,
+                  const PointSet& pts, const PointSet& recs, float* seis) -> sw_status {
+    a.pn = g->at0(pn);
+    a.pnm1 = g->at0(pm);
+    a.pout = g->at0(po);
+    if (m)
+      launch_stencil_tma_maps(g, a, *m, st);
+    else
+      launch_stencil(g->R, g->ndim, false, a, st);
+    const int taps = pts.count * pts.lz * pts.ly * pts.lx;
+    if (taps > 0)
+      inject_sources_kernel<<<(taps + 127) / 128, 128, 0, st>>>(a.pout, a.kappa, g->damp, pts, sig, sig_stride, n,
+                                                                f, g->ndim, g->R);
+    launch_face_conditions(a.pout, f, g->R, recs, seis, n, st);
+    SW_CUDA(cudaGetLastError());
+    return SW_OK;
+  };
+
+  // forward, keeping (p[k0-1], p[k0]) at every segment start
+  SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
+  SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
+  for (int n = 0; n < N; ++n) {
+    float* pn = g->u[n & 1];
+    float* pm = g->u[(n + 1) & 1];
+    if (n % K == 0) {
+      SW_CUDA(cudaMemcpyAsync(ck(n / K, 0), pm, fbytes, cudaMemcpyDeviceToDevice, st));
+      SW_CUDA(cudaMemcpyAsync(ck(n / K, 1), pn, fbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    const StepMaps m{&g->map_halo[n & 1], &g->map_inner[n & 1], &g->map_inner[(n + 1) & 1]};
+    SW_TRY(step(pn, pm, pm, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, rec, syn));
+  }
+  residual_kernel<<<256, 256, 0, st>>>(syn, obs, res, macc, N, g->n_rec);
+  SW_CUDA(cudaGetLastError());
+
+  // backward: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
+  for (int sgm = nseg - 1; sgm >= 0; --sgm) {
+    const int k0 = sgm * K, k1 = std::min(N, k0 + K);
+    SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
+    SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
+    for (int n = k0; n <= k1 - 2; ++n) {
+      const int j = n - k0 + 1;
+      const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))]};
+      SW_TRY(step(B(j), B(j - 1), B(j + 1), tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
+    }
+    for (int k = k1; k >= k0 + 1; --k) {
+      float* p1 = PSI((k + 1) & 1);  // psi[k+1]
+      float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
+      const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)]};
+      a.pn = g->at0(p1);
+      a.pnm1 = g->at0(p2);
+      a.pout = g->at0(p2);
+      if (tma)
+        launch_stencil_tma_maps(g, a, m, st);
+      else
+        launch_stencil(g->R, g->ndim, false, a, st);
+      neumann_adjoint_kernel<<<dim3(unsigned((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]),
+                                                       g->n[0] * g->n[1]) + 255) / 256), 3), 256, 0, st>>>(
+          g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R);
+      const int rtaps = rec.count * rec.lz * rec.ly * rec.lx;
+      inject_sources_kernel<<<(rtaps + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, res, N, k - 1,
+                                                                 f, g->ndim, g->R);
+      launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
+      const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
+      if (g->ndim == 3)
+        launch_image(g->R, 3, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+      else
+        launch_image(g->R, 2, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+      if (src_threads > 0)
+        image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->at0(GK), src,
+                                                                        g->wavelet, g->sig_stride, k - 1, f);
+      SW_CUDA(cudaGetLastError());
+    }
+  }
+
+  // dJ/dc, densely per node
+  float* out = grad_vel;
+  const bool host_out = !is_device_pointer(grad_vel);
+  if (host_out) {
+    if (!g->staging) SW_TRY(dev_alloc(g, (void**)&g->staging, size_t(g->nodes()) * sizeof(float)));
+    out = g->staging;
+  }
+  gradient_velocity_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(GK), a.kappa, out, f, float(g->dt));
+  SW_CUDA(cudaGetLastError());
+  if (host_out)
+    SW_CUDA(cudaMemcpyAsync(grad_vel, out, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(cudaMemcpyAsync(misfit, macc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SW_TRY(check_device_flag(g));
   return SW_OK;
 }
 
@@ -1302,12 +1508,13 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
   for (int step = 0; step < n_steps; ++step) {
     a.pn = g.at0(g.u[step & 1]);
     a.pnm1 = g.at0(g.u[(step + 1) & 1]);
+    a.pout = g.at0(g.u[(step + 1) & 1]);
     launch_stencil(g.R, ndim, g.has_density, a, g.stream);
     if (src_threads > 0)
-      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g.stream>>>(a.pnm1, a.kappa, g.damp, src, g.wavelet,
+      inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, g.stream>>>(a.pout, a.kappa, g.damp, src, g.wavelet,
                                                                             g.sig_stride, step, f, ndim, g.R);
     if (n_rec > 0)
-      sample_receivers_kernel<<<(n_rec + 3) / 4, 128, 0, g.stream>>>(a.pnm1, rec, f, seismogram, step);
+      sample_receivers_kernel<<<(n_rec + 3) / 4, 128, 0, g.stream>>>(a.pout, rec, f, seismogram, step);
   }
   SW_CUDA(cudaGetLastError());
   if (final_field) {

@@ -420,6 +420,146 @@ inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const Poi
   }
 }
 
+// ---- misfit gradient (adjoint-state method) ---------------------------------
+//
+// Extension beyond the paper, which names FWI as the solver's use: the exact
+// discrete adjoint of the forward recurrence.  In psi = kappa a lambda
+// (lambda the adjoint state, a = 1/(1+e)) one adjoint step is the forward
+// update with the transposed Laplacian L^T and the residuals injected
+// through the receiver weights; L^T is L with the same ghost mirrors except
+// along a Neumann face, where the even mirror makes L non-symmetric.
+
+// L^T psi - L psi along the Neumann faces, scaled as the update uses it:
+// out += a kappa (v_k / h^2) psi1[face] at the nodes k = 1..R from the face,
+// out -= a kappa sum_k (v_k / h^2) psi1[k] at the face node.  psi1 is the
+// level the stencil just read, out the level it wrote (before the face
+// conditions).  One thread per (axis, side, face line); nodes near two
+// Neumann faces get both corrections (atomics).
+struct LapCoef {
+  float c[3][kMaxR + 1];  // v_j / h^2 per axis (z, y, x)
+};
+
+__global__ void neumann_adjoint_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
+                                       FaceInfo f, LapCoef lc, int R) {
+  const int axis = blockIdx.y;
+  const int n[3] = {f.nz, f.ny, f.nx};
+  const int64_t st[3] = {f.sz, f.sy, 1};
+  const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+  const int64_t face = int64_t(n[o1]) * n[o2];
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= 2 * face) return;
+  const int side = int(t / face);
+  if (f.bc[2 * axis + side] != kBcNeumann) return;
+  const int64_t e = t % face;
+  int c[3];
+  c[o1] = int(e / n[o2]);
+  c[o2] = int(e % n[o2]);
+  const int64_t base = int64_t(c[o1]) * st[o1] + int64_t(c[o2]) * st[o2];
+  auto node = [&](int k) {  // the node k in from this face; also sets c[axis]
+    c[axis] = side == 0 ? k : n[axis] - 1 - k;
+    return base + int64_t(c[axis]) * st[axis];
+  };
+  auto damped_a = [&]() {  // 1/(1+e) of the node at c
+    const int dz = face_distance(c[0], f.nz, f.nbl[0], f.nbl[1]);
+    const int dy = face_distance(c[1], f.ny, f.nbl[2], f.nbl[3]);
+    const int dx = face_distance(c[2], f.nx, f.nbl[4], f.nbl[5]);
+    const int d2 = dz * dz + dy * dy + dx * dx;
+    return d2 ? damp[d2].x : 1.f;
+  };
+  const int64_t k0 = node(0);
+  const float a0 = damped_a();
+  const float pf = psi1[k0];
+  float back = 0.f;
+  for (int k = 1; k <= R; ++k) {
+    const int64_t kk = node(k);
+    const float ak = damped_a();
+    atomicAdd(&out[kk], ak * kappa[kk] * lc.c[axis][k] * pf);
+    back = fmaf(lc.c[axis][k], psi1[kk], back);
+  }
+  atomicAdd(&out[k0], -a0 * kappa[k0] * back);
+}
+
+// One term of dJ/dkappa per node: gk += psi (L p) / kappa, L the Eq. 9
+// Laplacian of p (whose ghosts hold the face conditions), in the same
+// constant-annihilating form as the stencils.  Block (128 x, y, z).
+template <int R, int NDIM>
+__global__ void image_kernel(const float* p, const float* psi, const float* kappa, float* gk, FaceInfo f,
+                             LapCoef lc) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= f.nx) return;
+  const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+  const float ps = psi[k];
+  if (ps == 0.f) return;
+  const float pc = p[k], p2 = 2.f * pc;
+  float lap = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    lap = fmaf(lc.c[0][j], (p[k + j * f.sz] + p[k - j * f.sz]) - p2, lap);
+    lap = fmaf(lc.c[2][j], (p[k + j] + p[k - j]) - p2, lap);
+    if constexpr (NDIM == 3) lap = fmaf(lc.c[1][j], (p[k + j * f.sy] + p[k - j * f.sy]) - p2, lap);
+  }
+  gk[k] += ps * lap / kappa[k];
+}
+
+// The source part of the same term: gk += psi s / kappa over the source
+// windows (s = window weights / prod(h) times S(t_n)), one thread per tap.
+__global__ void image_sources_kernel(const float* psi, const float* kappa, float* gk, PointSet src,
+                                     const float* sig, int sig_stride, int step, FaceInfo f) {
+  const int taps = src.lz * src.ly * src.lx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= src.count * taps) return;
+  const int s = t / taps;
+  int rem = t % taps;
+  const int ix = rem % src.lx;
+  rem /= src.lx;
+  const int iy = rem % src.ly;
+  const int iz = rem / src.ly;
+  const float* w = src.w + int64_t(s) * 3 * src.L;
+  const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
+  const int64_t k = int64_t(src.first[3 * s] + iz) * f.sz + int64_t(src.first[3 * s + 1] + iy) * f.sy +
+                    (src.first[3 * s + 2] + ix);
+  atomicAdd(&gk[k], psi[k] * wgt * sig[int64_t(s) * sig_stride + step] / kappa[k]);
+}
+
+// Residual r = synthetic - observed, transposed to [receiver][step] (the
+// layout inject_sources_kernel reads a per-source signal in), and the misfit
+// 1/2 sum r^2 accumulated in FP64.
+__global__ void residual_kernel(const float* syn, const float* obs, float* res_t, double* misfit, int n_steps,
+                                int n_rec) {
+  __shared__ double part[8];
+  double acc = 0.0;
+  const int64_t total = int64_t(n_steps) * n_rec;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int n = int(i / n_rec), r = int(i % n_rec);
+    const float d = syn[i] - obs[i];
+    res_t[int64_t(r) * n_steps + n] = d;
+    acc += double(d) * double(d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) s += part[i];
+    atomicAdd(misfit, 0.5 * s);
+  }
+}
+
+// dJ/dc = 2 c dt^2 dJ/dkappa = 2 sqrt(kappa) dt dJ/dkappa, densely per node.
+__global__ void gradient_velocity_kernel(const float* gk, const float* kappa, float* out, FaceInfo f, float dt) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    out[i] = 2.f * sqrtf(kappa[k]) * dt * gk[k];
+  }
+}
+
 // Dense copy of the nodes of a padded field.
 __global__ void extract_kernel(const float* p, float* out, FaceInfo f) {
   const int64_t n = int64_t(f.nz) * f.ny * f.nx;

@@ -26,7 +26,8 @@ namespace sw {
 
 struct StencilArgs {
   const float* pn;      // p[n] at node (0,0,0) of the padded layout
-  float* pnm1;          // p[n-1] in, p[n+1] out
+  const float* pnm1;    // p[n-1]
+  float* pout;          // p[n+1] (== pnm1 for the in-place update of the time loop)
   const float* kappa;   // (c dt)^2
   const float* lnrho;   // ln(rho) with mirrored ghosts, or nullptr
   const float2* damp;   // (a, e) = (1/(1+eta dt), eta dt) by squared distance (cells^2)
@@ -199,10 +200,10 @@ __global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const Sten
                                         (y == a.ny - 1 && a.bc[3] == kBcDirichlet)));
         if (dir) pnew = 0.f;
         const int64_t idx = zoff + col[i];
-        a.pnm1[idx] = pnew;
-        mirror_ghosts<R>(a.pnm1, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
-        mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
-        if constexpr (NDIM == 3) mirror_ghosts<R>(a.pnm1, idx, y, a.ny, sy, a.bc[2], a.bc[3], pnew);
+        a.pout[idx] = pnew;
+        mirror_ghosts<R>(a.pout, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
+        mirror_ghosts<R>(a.pout, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
+        if constexpr (NDIM == 3) mirror_ghosts<R>(a.pout, idx, y, a.ny, sy, a.bc[2], a.bc[3], pnew);
       }
     }
   }
@@ -260,9 +261,9 @@ __device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int
   const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
                    (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet);
   if (dir) pnew = 0.f;
-  a.pnm1[idx] = pnew;
-  mirror_ghosts<R>(a.pnm1, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
-  mirror_ghosts<R>(a.pnm1, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
+  a.pout[idx] = pnew;
+  mirror_ghosts<R>(a.pout, idx, z, a.nz, sz, a.bc[0], a.bc[1], pnew);
+  mirror_ghosts<R>(a.pout, idx, x, a.nx, 1, a.bc[4], a.bc[5], pnew);
 }
 
 template <int R, bool VD>

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
             kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
         }
-        float* plane = a.pnm1 + int64_t(z) * a.sz + rowoff0;
+        float* plane = a.pout + int64_t(z) * a.sz + rowoff0;
         if (!ragged) {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) __stcs(reinterpret_cast<float2*>(plane + i * int(a.sy)), kl[i]);  // streaming
