@@ -141,17 +141,26 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  *   grad_vel         [nz][ny][nx] FP32 (2D: [nz][nx]), device or host
  *   checkpoint_every forward states kept every K time steps (0: K about
  *                    sqrt(2 n_steps)); each segment is recomputed during the
- *                    adjoint sweep.  Device memory for the call, freed before
- *                    it returns: (2 n_steps / K + K + 4) padded wavefields
- *                    plus three [n_steps][n_rec] arrays.
+ *                    adjoint sweep.
+ *   checkpoint_format SW_CKPT_FP32: each checkpoint is a copy of the two
+ *                    padded FP32 levels; SW_CKPT_BF16 / SW_CKPT_FP16: the
+ *                    levels' nodes in 16 bits, divided by the level's largest
+ *                    magnitude (kept per snapshot), so the recomputed
+ *                    segments start from rounded states and the gradient
+ *                    carries that rounding.  Device memory for the call,
+ *                    freed before it returns: (2 n_steps / K + K + 4) padded
+ *                    FP32 wavefields (K + 4 with 16-bit checkpoints, plus
+ *                    2 n_steps / K node arrays of 2 bytes per node) and three
+ *                    [n_steps][n_rec] arrays.
  * Errors: SW_ESTATE before sw_set_model / sw_set_acquisition; SW_EINVAL with
  * a density model, without receivers, for n_steps < 1 or beyond the
  * wavelet, or with 2R+1 nodes or fewer along an axis; SW_ENOMEM when the
  * buffers do not fit.  The grid's wavefields
  * hold the forward run's last two levels afterwards.
  */
+enum { SW_CKPT_FP32 = 0, SW_CKPT_BF16 = 1, SW_CKPT_FP16 = 2 };
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
-                      int checkpoint_every);
+                      int checkpoint_every, int checkpoint_format);
 
 sw_status sw_get_dt(const sw_grid* g, double* dt);
 

@@ -960,7 +960,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
 }
 
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
-                      int checkpoint_every) {
+                      int checkpoint_every, int checkpoint_format) {
   g_last_error.clear();
   if (!g || !observed || !misfit || !grad_vel) return fail(SW_EINVAL, "NULL argument");
   if (!g->has_model) return fail(SW_ESTATE, "sw_gradient before sw_set_model");
@@ -970,6 +970,8 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   if (n_steps < 1) return fail(SW_EINVAL, "n_steps < 1");
   if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
   if (checkpoint_every < 0) return fail(SW_EINVAL, "checkpoint_every < 0");
+  if (checkpoint_format != SW_CKPT_FP32 && checkpoint_format != SW_CKPT_BF16 && checkpoint_format != SW_CKPT_FP16)
+    return fail(SW_EINVAL, "unknown checkpoint format %d", checkpoint_format);
   if (g->n[0] > 65535 || g->n[1] > 65535) return fail(SW_EINVAL, "axis longer than 65535 nodes");
   for (int ax = 0; ax < 3; ++ax)  // the face passes need every node within R of one face only
     if ((g->ndim == 3 || ax != 1) && g->n[ax] <= 2 * int64_t(g->R) + 1)
@@ -983,8 +985,14 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   const bool tma = use_tma(g);
   cudaStream_t st = g->stream;
 
-  // device memory of this call: checkpoint pairs, segment states, psi, dJ/dkappa
-  const int nfields = 2 * nseg + (K + 1) + 2 + 1;
+  // device memory of this call: checkpoint pairs (padded FP32 fields, or
+  // 16-bit node arrays with their scales), segment states, psi, dJ/dkappa
+  const bool packed = checkpoint_format != SW_CKPT_FP32;
+  const int nck = packed ? 0 : 2 * nseg;
+  const int nfields = nck + (K + 1) + 2 + 1;
+  const size_t pbytes = size_t(g->nodes()) * 2;  // one packed checkpoint
+  void* packs = nullptr;
+  unsigned* scales = nullptr;
   std::vector<float*> F(size_t(nfields), nullptr);
   float *syn = nullptr, *obs = nullptr, *res = nullptr;
   double* macc = nullptr;
@@ -999,6 +1007,8 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     dev_free(g, obs, sbytes);
     dev_free(g, res, sbytes);
     dev_free(g, macc, sizeof(double));
+    dev_free(g, packs, packed ? pbytes * 2 * nseg : 0);
+    dev_free(g, scales, packed ? sizeof(unsigned) * 2 * nseg : 0);
   };
   struct Guard {
     std::function<void()> fn;
@@ -1012,18 +1022,23 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   SW_TRY(dev_alloc(g, (void**)&obs, sbytes));
   SW_TRY(dev_alloc(g, (void**)&res, sbytes));
   SW_TRY(dev_alloc(g, (void**)&macc, sizeof(double)));
+  if (packed) {
+    SW_TRY(dev_alloc(g, &packs, pbytes * 2 * nseg));
+    SW_TRY(dev_alloc(g, (void**)&scales, sizeof(unsigned) * 2 * nseg));
+    SW_CUDA(cudaMemsetAsync(scales, 0, sizeof(unsigned) * 2 * nseg, st));
+  }
   SW_CUDA(cudaMemcpyAsync(obs, observed, sbytes, cudaMemcpyDefault, st));
   SW_CUDA(cudaMemsetAsync(macc, 0, sizeof(double), st));
-  auto ck = [&](int sgm, int i) { return F[size_t(2 * sgm + i)]; };  // i = 0: p[k0-1], 1: p[k0]
-  auto B = [&](int j) { return F[size_t(2 * nseg + j)]; };            // p[k0 + j - 1]
-  auto PSI = [&](int i) { return F[size_t(2 * nseg + K + 1 + i)]; };
+  auto ck = [&](int sgm, int i) { return F[size_t(2 * sgm + i)]; };  // FP32: i = 0: p[k0-1], 1: p[k0]
+  auto B = [&](int j) { return F[size_t(nck + j)]; };                 // p[k0 + j - 1]
+  auto PSI = [&](int i) { return F[size_t(nck + K + 1 + i)]; };
   float* GK = F[size_t(nfields - 1)];
   std::vector<CUtensorMap> halo(static_cast<size_t>(nfields)), inner(static_cast<size_t>(nfields));
   if (tma) {
     int tx, ty;
     tma_tile(g->R, &tx, &ty);
     const uint32_t xh = uint32_t((g->R + 3) / 4 * 4);
-    for (int i = 2 * nseg; i < nfields - 1; ++i) {  // segment states and psi
+    for (int i = nck; i < nfields - 1; ++i) {  // segment states and psi
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &halo[size_t(i)]));
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &inner[size_t(i)]));
     }
@@ -1067,8 +1082,25 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     float* pn = g->u[n & 1];
     float* pm = g->u[(n + 1) & 1];
     if (n % K == 0) {
-      SW_CUDA(cudaMemcpyAsync(ck(n / K, 0), pm, fbytes, cudaMemcpyDeviceToDevice, st));
-      SW_CUDA(cudaMemcpyAsync(ck(n / K, 1), pn, fbytes, cudaMemcpyDeviceToDevice, st));
+      if (packed) {
+        for (int i = 0; i < 2; ++i) {
+          const int slot = 2 * (n / K) + i;
+          const float* src_f = g->at0(i == 0 ? pm : pn);
+          unsigned* sc = scales + slot;
+          absmax_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(src_f, f, sc);
+          char* dst = static_cast<char*>(packs) + pbytes * slot;
+          if (checkpoint_format == SW_CKPT_BF16)
+            pack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+                src_f, f, sc, reinterpret_cast<__nv_bfloat16*>(dst));
+          else
+            pack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(src_f, f, sc,
+                                                                                     reinterpret_cast<__half*>(dst));
+        }
+        SW_CUDA(cudaGetLastError());
+      } else {
+        SW_CUDA(cudaMemcpyAsync(ck(n / K, 0), pm, fbytes, cudaMemcpyDeviceToDevice, st));
+        SW_CUDA(cudaMemcpyAsync(ck(n / K, 1), pn, fbytes, cudaMemcpyDeviceToDevice, st));
+      }
     }
     const StepMaps m{&g->map_halo[n & 1], &g->map_inner[n & 1], &g->map_inner[(n + 1) & 1]};
     SW_TRY(step(pn, pm, pm, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, rec, syn));
@@ -1079,8 +1111,23 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // backward: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
   for (int sgm = nseg - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * K, k1 = std::min(N, k0 + K);
-    SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
-    SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
+    if (packed) {
+      for (int i = 0; i < 2; ++i) {
+        const int slot = 2 * sgm + i;
+        const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
+        if (checkpoint_format == SW_CKPT_BF16)
+          unpack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+              reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, g->at0(B(i)));
+        else
+          unpack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+              reinterpret_cast<const __half*>(src_p), scales + slot, f, g->at0(B(i)));
+        launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored level
+      }
+      SW_CUDA(cudaGetLastError());
+    } else {
+      SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
+      SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
+    }
     for (int n = k0; n <= k1 - 2; ++n) {
       const int j = n - k0 + 1;
       const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))]};

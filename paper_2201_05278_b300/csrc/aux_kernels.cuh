@@ -1,6 +1,8 @@
 // Source injection, receiver sampling and model set-up kernels.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -557,6 +559,60 @@ __global__ void gradient_velocity_kernel(const float* gk, const float* kappa, fl
     const int z = int(zy / f.ny);
     const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
     out[i] = 2.f * sqrtf(kappa[k]) * dt * gk[k];
+  }
+}
+
+// ---- compressed checkpoints ---------------------------------------------------
+// A checkpointed wavefield is stored as its nodes only, in 16 bits, divided by
+// the field's largest magnitude (its per-snapshot scale); restoring
+// multiplies back and leaves the ghosts to the face conditions.
+
+// max |p| over the nodes, as the bit pattern of a non-negative float
+// (order-preserving as an unsigned integer).
+__global__ void absmax_kernel(const float* p, FaceInfo f, unsigned* out) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  unsigned m = 0u;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
+    m = max(m, __float_as_uint(fabsf(p[k])));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__device__ __forceinline__ float snapshot_scale(const unsigned* bits) {
+  const float s = __uint_as_float(*bits);
+  return s > 0.f ? s : 1.f;
+}
+
+template <typename T>
+__device__ __forceinline__ T to_half_kind(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_half_kind<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_half_kind<__half>(float v) { return __float2half_rn(v); }
+
+template <typename T>
+__global__ void pack_snapshot_kernel(const float* p, FaceInfo f, const unsigned* scale_bits, T* out) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  const float inv = 1.f / snapshot_scale(scale_bits);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    out[i] = to_half_kind<T>(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] * inv);
+  }
+}
+
+template <typename T>
+__global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, FaceInfo f, float* p) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  const float sc = snapshot_scale(scale_bits);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] = float(in[i]) * sc;
   }
 }
 

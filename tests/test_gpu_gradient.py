@@ -28,7 +28,7 @@ def _setup(ndim, order, n_steps, seed):
     return w, wav, obs.astype(np.float32), kw
 
 
-def _gpu_gradient(w, wav, obs, n_steps, checkpoint_every=0):
+def _gpu_gradient(w, wav, obs, n_steps, checkpoint_every=0, fmt=api.SW_CKPT_FP32):
     import torch
     dev = torch.device("cuda:0")
     g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
@@ -36,7 +36,7 @@ def _gpu_gradient(w, wav, obs, n_steps, checkpoint_every=0):
         api.sw_set_model(g, torch.from_numpy(np.ascontiguousarray(w.velocity, np.float32)).to(dev))
         api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
         grad = torch.zeros(w.shape, dtype=torch.float32, device=dev)
-        J = api.sw_gradient(g, n_steps, torch.from_numpy(obs).to(dev), grad, checkpoint_every)
+        J = api.sw_gradient(g, n_steps, torch.from_numpy(obs).to(dev), grad, checkpoint_every, fmt)
         return J, grad.cpu().numpy()
     finally:
         g.close()
@@ -78,3 +78,43 @@ def test_gradient_rejects_what_it_does_not_cover(cuda_device):
         assert e.value.status == api.SW_EINVAL
     finally:
         g.close()
+
+
+def test_autograd_misfit_backward_gives_the_adjoint_gradient(cuda_device):
+    import torch
+    from paper_2201_05278_b300 import autograd
+    n = 40
+    w, wav, obs, kw = _setup(3, 8, n, seed=9)
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        vel = torch.from_numpy(np.ascontiguousarray(w.velocity, np.float32)).to(dev).requires_grad_(True)
+        api.sw_set_model(g, vel.detach())
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        J = autograd.misfit(vel, g, torch.from_numpy(obs).to(dev), n)
+        (2.0 * J).backward()
+        pb = A.make_problem(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, **kw)
+        J_ref, g_ref, _ = A.adjoint_gradient(pb, wav.astype(np.float64), obs.astype(np.float64), n)
+        assert float(J.detach()) == pytest.approx(J_ref, rel=1e-4)
+        assert rel_l2(vel.grad.cpu().numpy(), 2.0 * g_ref) <= GRAD_TOL
+    finally:
+        g.close()
+
+
+# Gradient error against the FP64 oracle with 16-bit checkpoints (the
+# recomputed segments start from rounded states); bounds from the mantissa
+# widths (8 bits BF16, 11 bits FP16).
+CKPT_TOL = {api.SW_CKPT_BF16: 3e-2, api.SW_CKPT_FP16: 5e-3}
+
+
+@pytest.mark.parametrize("fmt", [api.SW_CKPT_BF16, api.SW_CKPT_FP16])
+def test_gradient_with_16_bit_checkpoints(cuda_device, fmt):
+    n = 60
+    w, wav, obs, kw = _setup(3, 8, n, seed=12)
+    J, grad = _gpu_gradient(w, wav, obs, n, 8, fmt)
+    pb = A.make_problem(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, **kw)
+    J_ref, g_ref, _ = A.adjoint_gradient(pb, wav.astype(np.float64), obs.astype(np.float64), n)
+    err = rel_l2(grad, g_ref)
+    print("checkpoint format %d: gradient rel-L2 error %.3e against the FP64 oracle" % (fmt, err))
+    assert J == pytest.approx(J_ref, rel=1e-4)  # the forward pass itself is not rounded
+    assert err <= CKPT_TOL[fmt]
