@@ -185,6 +185,43 @@ sw_status sw_set_stencil_variant(sw_grid* g, int variant);
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
 
 /*
+ * Distributed forcing (the forcing term of Eq. 5, used by the manufactured
+ * solutions of Sec. 2.5): every later sw_forward adds
+ * f(x, t_n) = sum_m F_m(x) T_m(t_n) at step n the way a source enters Eq. 7,
+ * p[n+1] += kappa a f, except at Dirichlet face nodes.  fields is
+ * [n_force][nodes] (dense, (z, [y,] x) order, the grid's full shape),
+ * signatures is [n_force][n_sig] (T_m at t_n = n dt); both FP32, host or
+ * device, copied (the caller keeps ownership).  n_force = 0 removes the
+ * forcing.  A later sw_forward longer than n_sig steps fails with SW_EINVAL.
+ * Errors: SW_EINVAL for NULL arrays or n_sig < 1 with n_force > 0,
+ * SW_ENOMEM.
+ */
+sw_status sw_set_forcing(sw_grid* g, int n_force, const float* fields, const float* signatures, int n_sig);
+
+/*
+ * Initial levels p[0] = p0 and p[-1] = pm1 of every later sw_forward (dense
+ * [nodes] FP32, host or device, copied; NULL = zero, the default).  This
+ * resumes a run from a saved pair of levels (two are needed, Eq. 7) and sets
+ * up standing-wave tests.  Dirichlet face nodes are taken as 0 and the ghost
+ * nodes follow the face conditions.  Errors: SW_ENOMEM.  sw_gradient
+ * refuses to run (SW_ESTATE) while initial levels or forcing are set.
+ */
+sw_status sw_set_initial_state(sw_grid* g, const float* p0, const float* pm1);
+
+/*
+ * Wavefield snapshots (the solver's saving stride, Sec. 4): with
+ * saving_stride = s > 0, every later sw_forward writes p after s, 2s, 3s, ...
+ * time steps into consecutive frames of `snapshots` (frame k = p after
+ * (k+1) s steps, laid out like final_field), stopping after max_frames
+ * frames; s = 1 saves every step.  s = 0 turns saving off (the last level is
+ * still available through sw_forward's final_field).  `snapshots` is
+ * caller-owned device memory of max_frames x (nodes) floats; the grid only
+ * keeps the pointer.  Errors: SW_EINVAL for a negative stride or count, a
+ * missing or host buffer with s > 0.
+ */
+sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t max_frames);
+
+/*
  * Failure-path test hook (no counterpart in the paper).  With starve != 0
  * the TMA-pipelined kernel issues no tensor copies, so every mbarrier wait
  * in it runs into its bound: the kernel raises the device error flag and

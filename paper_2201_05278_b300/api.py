@@ -140,6 +140,41 @@ def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int
     return j.value
 
 
+def _f32(a):
+    """A contiguous FP32 view of a tensor or array (tensors pass through)."""
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def sw_set_forcing(g: Grid, fields=None, signatures=None) -> None:
+    """Distributed forcing sum_m F_m(x) T_m(t_n): fields [n_force, *grid], signatures
+    [n_force, n_sig] (host or device, copied).  None removes the forcing."""
+    if fields is None:
+        _check(_lib.load().sw_set_forcing(g.handle, 0, None, None, 0))
+        return
+    F, T = _f32(fields), _f32(signatures)
+    n_force = int(F.shape[0])
+    if tuple(F.shape[1:]) != g.shape or T.ndim != 2 or int(T.shape[0]) != n_force:
+        raise ValueError("expected fields [n_force, *grid] and signatures [n_force, n_sig]")
+    _check(_lib.load().sw_set_forcing(g.handle, n_force, _ptr(F), _ptr(T), int(T.shape[1])))
+
+
+def sw_set_initial_state(g: Grid, p0=None, pm1=None) -> None:
+    """Initial levels p[0], p[-1] of later forwards (grid-shaped; None = zero)."""
+    a, b = _f32(p0), _f32(pm1)
+    for x in (a, b):
+        if x is not None and tuple(x.shape) != g.shape:
+            raise ValueError("expected a field of the grid's shape")
+    _check(_lib.load().sw_set_initial_state(g.handle, _ptr(a), _ptr(b)))
+
+
+def sw_set_saving(g: Grid, saving_stride: int, snapshots=None, max_frames: int = 0) -> None:
+    """Every later sw_forward writes p after saving_stride, 2 saving_stride, ...
+    steps into the frames of `snapshots` (device, [max_frames, *grid]); 0 turns it off."""
+    _check(_lib.load().sw_set_saving(g.handle, int(saving_stride), _ptr(snapshots), int(max_frames)))
+
+
 def sw_get_dt(g: Grid) -> float:
     v = ctypes.c_double()
     _check(_lib.load().sw_get_dt(g.handle, ctypes.byref(v)))

@@ -121,6 +121,17 @@ struct sw_grid {
   CUtensorMap map_g[3];
   bool grad_ready = false;
 
+  // distributed forcing (sw_set_forcing): dense fields and signatures
+  int n_force = 0, force_len = 0;
+  float* force_F = nullptr;
+  float* force_T = nullptr;
+  // initial levels p[0], p[-1] (sw_set_initial_state), dense, or NULL for 0
+  float* init_p0 = nullptr;
+  float* init_pm1 = nullptr;
+  // wavefield snapshots written by sw_forward (sw_set_saving)
+  int saving_stride = 0;
+  float* snapshots = nullptr;
+  int64_t snapshot_frames = 0;
   // profiling
   int profiling = 0;  // time every profiling-th stencil launch (0: none)
   // the time loop of sw_forward as a CUDA graph: captured on the second call
@@ -804,11 +815,19 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   if (n_steps < 0) return fail(SW_EINVAL, "n_steps < 0");
   if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
   if (g->n_rec > 0 && n_steps > 0 && !seismogram) return fail(SW_EINVAL, "seismogram is NULL");
+  if (g->n_force > 0 && n_steps > g->force_len)
+    return fail(SW_EINVAL, "n_steps (%d) exceeds the forcing signatures (%d)", n_steps, g->force_len);
 
   const FaceInfo f = g->faces();
   const size_t fbytes = size_t(g->lay.total) * sizeof(float);
   SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, g->stream));
   SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, g->stream));
+  if (g->init_p0)
+    insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, g->stream>>>(g->init_p0, g->at0(g->u[0]), f, g->ndim, g->R);
+  if (g->init_pm1)
+    insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, g->stream>>>(g->init_pm1, g->at0(g->u[1]), f, g->ndim,
+                                                                       g->R);
+  SW_CUDA(cudaGetLastError());
 
   float* seis_dev = nullptr;
   const bool seis_host = seismogram && !is_device_pointer(seismogram);
@@ -879,6 +898,12 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
           a.pout, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
     }
+    if (g->n_force > 0) {
+      forcing_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(a.pout, a.kappa, g->damp, g->force_F, g->force_T,
+                                                                   g->n_force, g->force_len, step, f, g->ndim, g->R,
+                                                                   tma ? 0 : 1);
+      ++launches;
+    }
     if (tma) {
       // the pipelined kernel writes node values only: the face conditions
       // follow, with the receiver samples in the same launch
@@ -887,6 +912,13 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     } else if (g->n_rec > 0) {
       sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pout, rec, f, seis_dev, step);
       ++launches;
+    }
+    if (g->snapshots && (step + 1) % g->saving_stride == 0) {  // frame k holds p after (k+1) * stride steps
+      const int64_t frame = (step + 1) / g->saving_stride - 1;
+      if (frame < g->snapshot_frames) {
+        extract_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(a.pout, g->snapshots + frame * g->nodes(), f);
+        ++launches;
+      }
     }
   }
   SW_CUDA(cudaGetLastError());
@@ -966,6 +998,8 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   if (!g->has_model) return fail(SW_ESTATE, "sw_gradient before sw_set_model");
   if (!g->has_acq) return fail(SW_ESTATE, "sw_gradient before sw_set_acquisition");
   if (g->has_density) return fail(SW_EINVAL, "the gradient is built for constant density only");
+  if (g->n_force > 0 || g->init_p0 || g->init_pm1)
+    return fail(SW_ESTATE, "the gradient assumes zero initial levels and no distributed forcing");
   if (g->n_rec <= 0) return fail(SW_EINVAL, "the gradient needs receivers");
   if (n_steps < 1) return fail(SW_EINVAL, "n_steps < 1");
   if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
@@ -1222,6 +1256,69 @@ sw_status sw_get_stencil_variant(const sw_grid* g, int* variant) {
   return SW_OK;
 }
 
+sw_status sw_set_forcing(sw_grid* g, int n_force, const float* fields, const float* signatures, int n_sig) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (n_force < 0) return fail(SW_EINVAL, "n_force < 0");
+  if (n_force > 0 && (!fields || !signatures || n_sig < 1))
+    return fail(SW_EINVAL, "forcing needs fields, signatures and n_sig >= 1");
+  ++g->config_gen;
+  const int64_t nn = g->nodes();
+  dev_free(g, g->force_F, size_t(g->n_force) * nn * sizeof(float));
+  dev_free(g, g->force_T, size_t(g->n_force) * g->force_len * sizeof(float));
+  g->force_F = g->force_T = nullptr;
+  g->n_force = g->force_len = 0;
+  if (n_force == 0) return SW_OK;
+  float *F = nullptr, *T = nullptr;
+  SW_TRY(dev_alloc(g, (void**)&F, size_t(n_force) * nn * sizeof(float)));
+  const sw_status st = dev_alloc(g, (void**)&T, size_t(n_force) * n_sig * sizeof(float));
+  if (st != SW_OK) {
+    dev_free(g, F, size_t(n_force) * nn * sizeof(float));
+    return st;
+  }
+  g->force_F = F;
+  g->force_T = T;
+  g->n_force = n_force;
+  g->force_len = n_sig;
+  SW_CUDA(cudaMemcpyAsync(F, fields, size_t(n_force) * nn * sizeof(float), cudaMemcpyDefault, g->stream));
+  SW_CUDA(cudaMemcpyAsync(T, signatures, size_t(n_force) * n_sig * sizeof(float), cudaMemcpyDefault, g->stream));
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  return SW_OK;
+}
+
+sw_status sw_set_initial_state(sw_grid* g, const float* p0, const float* pm1) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  const size_t bytes = size_t(g->nodes()) * sizeof(float);
+  const float* src[2] = {p0, pm1};
+  float** dst[2] = {&g->init_p0, &g->init_pm1};
+  for (int i = 0; i < 2; ++i) {
+    if (!src[i]) {
+      dev_free(g, *dst[i], bytes);
+      *dst[i] = nullptr;
+      continue;
+    }
+    if (!*dst[i]) SW_TRY(dev_alloc(g, (void**)dst[i], bytes));
+    SW_CUDA(cudaMemcpyAsync(*dst[i], src[i], bytes, cudaMemcpyDefault, g->stream));
+  }
+  SW_CUDA(cudaStreamSynchronize(g->stream));
+  return SW_OK;
+}
+
+sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t max_frames) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (saving_stride < 0 || max_frames < 0) return fail(SW_EINVAL, "negative saving stride or frame count");
+  if (saving_stride > 0 && (!snapshots || max_frames == 0))
+    return fail(SW_EINVAL, "a saving stride needs a snapshot buffer and a frame count");
+  if (snapshots && !is_device_pointer(snapshots)) return fail(SW_EINVAL, "the snapshot buffer must be device memory");
+  g->saving_stride = saving_stride;
+  g->snapshots = saving_stride > 0 ? snapshots : nullptr;
+  g->snapshot_frames = saving_stride > 0 ? max_frames : 0;
+  ++g->config_gen;
+  return SW_OK;
+}
+
 sw_status sw_set_profiling(sw_grid* g, int every) {
   if (!g) return fail(SW_EINVAL, "NULL grid");
   if (every < 0) return fail(SW_EINVAL, "negative profiling stride");
@@ -1258,6 +1355,10 @@ void sw_destroy_grid(sw_grid* g) {
   dev_free(g, g->lnrho, fbytes);
   for (int i = 0; i < 3; ++i) dev_free(g, g->glr[i], fbytes);
   dev_free(g, g->damp, size_t(g->damp_len) * sizeof(float2));
+  dev_free(g, g->force_F, size_t(g->n_force) * g->nodes() * sizeof(float));
+  dev_free(g, g->force_T, size_t(g->n_force) * g->force_len * sizeof(float));
+  dev_free(g, g->init_p0, size_t(g->nodes()) * sizeof(float));
+  dev_free(g, g->init_pm1, size_t(g->nodes()) * sizeof(float));
   dev_free(g, g->dflag, 64);
   dev_free(g, g->dscratch, 64);
   dev_free(g, g->staging, size_t(g->nodes()) * sizeof(float));

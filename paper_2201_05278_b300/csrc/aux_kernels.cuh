@@ -616,6 +616,71 @@ __global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, 
   }
 }
 
+// Distributed forcing f(x, t_n) = sum_m F_m(x) T_m(t_n), added like a source
+// term (Eq. 7 and 11 with a dense source): p[n+1]_k += kappa_k a_k f_k.  The
+// nodes are dense ([n_force][nz][ny][nx] fields, [n_force][n_sig] signatures);
+// Dirichlet face nodes stay 0; with `mirrors` the ghost images get the same
+// increment (the face conditions do not follow on that path).
+__global__ void forcing_kernel(float* p, const float* kappa, const float2* damp, const float* F, const float* T,
+                               int n_force, int n_sig, int step, FaceInfo f, int ndim, int R, int mirrors) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const bool dir = (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
+                     (x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet) ||
+                     (ndim == 3 && ((y == 0 && f.bc[2] == kBcDirichlet) ||
+                                    (y == f.ny - 1 && f.bc[3] == kBcDirichlet)));
+    if (dir) continue;
+    float s = 0.f;
+    for (int m = 0; m < n_force; ++m) s = fmaf(F[int64_t(m) * n + i], T[int64_t(m) * n_sig + step], s);
+    const int64_t idx = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    const int dz = face_distance(z, f.nz, f.nbl[0], f.nbl[1]);
+    const int dy = ndim == 3 ? face_distance(y, f.ny, f.nbl[2], f.nbl[3]) : 0;
+    const int dx = face_distance(x, f.nx, f.nbl[4], f.nbl[5]);
+    const int d2 = dz * dz + dy * dy + dx * dx;
+    const float d = kappa[idx] * (d2 ? damp[d2].x : 1.f) * s;
+    p[idx] += d;
+    if (mirrors) {
+      add_with_mirrors(p, idx, z, f.nz, f.sz, f.bc[0], f.bc[1], R, d);
+      add_with_mirrors(p, idx, x, f.nx, 1, f.bc[4], f.bc[5], R, d);
+      if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
+    }
+  }
+}
+
+// Writes a dense field into the nodes of a zeroed padded field, with the
+// ghost images the face conditions give (odd mirror on a Dirichlet face, even
+// on a Neumann face, none stays 0).  Dirichlet face nodes are set to 0.
+__device__ __forceinline__ void set_with_mirrors(float* p, int64_t idx, int i, int n, int64_t stride, int bc_lo,
+                                                 int bc_hi, int R, float v) {
+  if (bc_lo != kBcNone && i >= 1 && i <= R) p[idx - int64_t(2 * i) * stride] = bc_lo == kBcDirichlet ? -v : v;
+  const int m = n - 1 - i;
+  if (bc_hi != kBcNone && m >= 1 && m <= R) p[idx + int64_t(2 * m) * stride] = bc_hi == kBcDirichlet ? -v : v;
+}
+
+__global__ void insert_kernel(const float* in, float* p, FaceInfo f, int ndim, int R) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const bool dir = (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
+                     (x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet) ||
+                     (ndim == 3 && ((y == 0 && f.bc[2] == kBcDirichlet) ||
+                                    (y == f.ny - 1 && f.bc[3] == kBcDirichlet)));
+    const float v = dir ? 0.f : in[i];
+    const int64_t idx = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    p[idx] = v;
+    set_with_mirrors(p, idx, z, f.nz, f.sz, f.bc[0], f.bc[1], R, v);
+    set_with_mirrors(p, idx, x, f.nx, 1, f.bc[4], f.bc[5], R, v);
+    if (ndim == 3) set_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, v);
+  }
+}
+
 // Dense copy of the nodes of a padded field.
 __global__ void extract_kernel(const float* p, float* out, FaceInfo f) {
   const int64_t n = int64_t(f.nz) * f.ny * f.nx;

@@ -244,3 +244,34 @@ def test_repeated_forwards_replay_identically(cuda_device, ndim):
         assert np.array_equal(short.cpu().numpy(), runs[0][: w.n_steps // 2])
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_snapshots_follow_the_saving_stride(cuda_device, ndim):
+    """Frame k holds p after (k+1) * stride steps: it equals the final field of a
+    run of that length (same kernels, bit for bit) and the oracle's."""
+    import torch
+    w = small_case(ndim, 8, False, seed=31, n_steps=37)
+    dev = torch.device("cuda:0")
+    stride, frames = 5, 6
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps),
+                               window_radius=w.window_radius)
+        snaps = torch.full((frames,) + tuple(w.shape), -1.0, dtype=torch.float32, device=dev)
+        seis = torch.zeros((w.n_steps, len(w.rec_pos)), dtype=torch.float32, device=dev)
+        api.sw_set_saving(g, stride, snaps, frames)
+        api.sw_forward(g, w.n_steps, seis)
+        api.sw_set_saving(g, 0)
+        snaps = snaps.cpu().numpy()
+        for k in (0, 3, frames - 1):
+            fin = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+            api.sw_forward(g, (k + 1) * stride, seis[: (k + 1) * stride], fin)
+            assert np.array_equal(snaps[k], fin.cpu().numpy())
+        _, p_ref = run_oracle(w, n_steps=4 * stride)
+        assert rel_l2(snaps[3], p_ref) <= FP32_SEIS_TOL
+        with pytest.raises(api.SimwaveError):
+            api.sw_set_saving(g, 2, None, 3)
+    finally:
+        g.close()
