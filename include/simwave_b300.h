@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct sw_grid sw_grid;
+typedef struct sw_batch sw_batch;
 
 typedef enum {
   SW_OK = 0,
@@ -220,6 +221,43 @@ sw_status sw_set_initial_state(sw_grid* g, const float* p0, const float* pm1);
  * missing or host buffer with s > 0.
  */
 sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t max_frames);
+
+/*
+ * Batched shots.  The paper's solver runs one shot at a time; waveform
+ * inversion, the use it names (Sec. 1 and 6), runs many shots.  A batch
+ * advances several 2D constant-density grids (one space order, one device
+ * and stream, any sizes) together: per time step one stencil launch over a
+ * work list of (model, tile) for all shots, one injection and one receiver
+ * launch.  Grids of the same geometry (shape, spacing, absorbing layers,
+ * faces, damping, dt) whose kappa fields are bit-identical are one model
+ * group: each tile of the model is read once per step for all its shots.
+ * Every shot gives the same result as sw_forward on its grid alone.
+ *
+ * sw_create_batch borrows the grids (they must outlive the batch and keep
+ * their model and acquisition; a grid changed afterwards makes
+ * sw_batch_forward fail with SW_ESTATE).  Errors: SW_EINVAL for 3D or
+ * variable-density grids, mixed orders, streams or devices, a grid listed
+ * twice, grids with forcing or snapshots; SW_ESTATE for a grid without model
+ * or acquisition.
+ *
+ * sw_batch_forward runs n_steps steps of every grid from rest (or from its
+ * sw_set_initial_state levels).  seismograms[i] is grid i's [n_steps][n_rec]
+ * output in DEVICE memory (may be NULL for grids without receivers);
+ * final_fields (NULL, or an array with NULL entries to skip) receives p
+ * after the last step (host or device).  The time loop is captured as a CUDA
+ * graph on the second call with the same n_steps.  Blocks until done.
+ *
+ * sw_batch_info: number of model groups and of tiles per step.
+ * sw_batch_set_profiling / sw_batch_get_profile: as for a grid (every
+ * every-th stencil launch timed with CUDA events).
+ */
+sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids);
+sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, float* const* final_fields);
+sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_tiles);
+sw_status sw_batch_set_profiling(sw_batch* b, int every);
+sw_status sw_batch_get_profile(const sw_batch* b, double* stencil_ms, int64_t* stencil_launches,
+                               int64_t* kernel_launches);
+void sw_destroy_batch(sw_batch* b);
 
 /*
  * Failure-path test hook (no counterpart in the paper).  With starve != 0

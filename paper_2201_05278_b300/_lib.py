@@ -45,6 +45,14 @@ SIGNATURES = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sw_last_error": (ctypes.c_char_p, []),
     "sw_destroy_grid": (None, [ctypes.c_void_p]),
+    "sw_create_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.c_int]),
+    "sw_batch_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "sw_batch_info": (ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_ip]),
+    "sw_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sw_batch_get_profile": (ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_i64p, _c_i64p]),
+    "sw_destroy_batch": (None, [ctypes.c_void_p]),
 }
 
 _lib = None

@@ -175,6 +175,69 @@ def sw_set_saving(g: Grid, saving_stride: int, snapshots=None, max_frames: int =
     _check(_lib.load().sw_set_saving(g.handle, int(saving_stride), _ptr(snapshots), int(max_frames)))
 
 
+class Batch:
+    """Owner of an sw_batch handle (destroyed with sw_destroy_batch); keeps its grids alive."""
+
+    def __init__(self, handle: int, grids):
+        self.handle = handle
+        self.grids = list(grids)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            _lib.load().sw_destroy_batch(self.handle)
+            self.handle = None
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, a in enumerate(items):
+        arr[i] = _ptr(a)
+    return arr
+
+
+def sw_create_batch(grids) -> Batch:
+    """Batch of 2D constant-density grids advanced together (shots of one model share its reads)."""
+    grids = list(grids)
+    handles = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
+    h = ctypes.c_void_p()
+    _check(_lib.load().sw_create_batch(ctypes.byref(h), handles, len(grids)))
+    return Batch(h.value, grids)
+
+
+def sw_batch_forward(b: Batch, n_steps: int, seismograms=None, final_fields=None) -> None:
+    """seismograms: per grid a device tensor [n_steps, n_rec] (or None); final_fields: per grid or None."""
+    n = len(b.grids)
+    seis = _ptr_array(list(seismograms) if seismograms is not None else [None] * n)
+    fin = _ptr_array(list(final_fields)) if final_fields is not None else None
+    _check(_lib.load().sw_batch_forward(b.handle, int(n_steps), seis, fin))
+
+
+def sw_batch_info(b: Batch):
+    """(model groups, tiles per step)."""
+    ng, nt = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.load().sw_batch_info(b.handle, ctypes.byref(ng), ctypes.byref(nt)))
+    return ng.value, nt.value
+
+
+def sw_batch_set_profiling(b: Batch, every=1) -> None:
+    _check(_lib.load().sw_batch_set_profiling(b.handle, int(every)))
+
+
+def sw_batch_get_profile(b: Batch):
+    """(summed ms of the timed stencil launches, timed launches, kernel launches) of the last batch forward."""
+    ms = ctypes.c_double()
+    n1 = ctypes.c_int64()
+    n2 = ctypes.c_int64()
+    _check(_lib.load().sw_batch_get_profile(b.handle, ctypes.byref(ms), ctypes.byref(n1), ctypes.byref(n2)))
+    return ms.value, n1.value, n2.value
+
+
 def sw_get_dt(g: Grid) -> float:
     v = ctypes.c_double()
     _check(_lib.load().sw_get_dt(g.handle, ctypes.byref(v)))

@@ -1674,3 +1674,387 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
   if (bad) return fail(SW_ETIMEOUT, "a kernel raised the device error flag (0x%x)", bad);
   return SW_OK;
 }
+
+// ---- batched shots -----------------------------------------------------------
+
+#include "batch.cuh"
+
+struct sw_batch {
+  std::vector<sw_grid*> grids;
+  std::vector<uint64_t> gens;    // config_gen of every grid when the batch was made
+  std::vector<int> slot_grid;    // shot-table slot -> grid index
+  std::vector<int> grid_group;   // grid index -> group
+  std::vector<BatchShot> shots;  // host copy of the shot table
+  BatchGroup* d_groups = nullptr;
+  BatchShot* d_shots = nullptr;
+  int n_groups = 0, total_tiles = 0, blocks = 0, R = 0;
+  int max_src_taps = 0, max_rec = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = -1, last_steps = -1;
+  int profiling = 0;
+  std::vector<cudaEvent_t> events;
+  double stencil_ms = 0.0;
+  int64_t stencil_launches = 0, kernel_launches = 0;
+  int64_t nodes_per_step = 0;
+};
+
+namespace {
+
+using BatchFn = void (*)(const BatchGroup*, int, const BatchShot*, int, int);
+
+BatchFn batch_kernel(int R) {
+  switch (R) {
+    case 1: return batch_stencil_2d_kernel<1>;
+    case 2: return batch_stencil_2d_kernel<2>;
+    case 3: return batch_stencil_2d_kernel<3>;
+    case 4: return batch_stencil_2d_kernel<4>;
+    case 5: return batch_stencil_2d_kernel<5>;
+    case 6: return batch_stencil_2d_kernel<6>;
+    case 7: return batch_stencil_2d_kernel<7>;
+    case 8: return batch_stencil_2d_kernel<8>;
+    case 9: return batch_stencil_2d_kernel<9>;
+    default: return batch_stencil_2d_kernel<10>;
+  }
+}
+
+bool same_geometry(const sw_grid* a, const sw_grid* b) {
+  if (a->ndim != b->ndim || a->R != b->R || a->dt != b->dt || a->alpha != b->alpha || a->degree != b->degree)
+    return false;
+  for (int i = 0; i < 3; ++i)
+    if (a->n[i] != b->n[i] || a->h[i] != b->h[i]) return false;
+  for (int i = 0; i < 6; ++i)
+    if (a->nbl[i] != b->nbl[i] || a->bc[i] != b->bc[i]) return false;
+  return true;
+}
+
+__global__ void differ_kernel(const unsigned* a, const unsigned* b, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    if (a[i] != b[i]) {
+      *flag = 1;
+      return;
+    }
+}
+
+// Do two grids of the same geometry hold bit-identical kappa fields?
+sw_status same_model(sw_grid* a, sw_grid* b, cudaStream_t st, bool* same) {
+  SW_CUDA(cudaMemsetAsync(a->dflag, 0, sizeof(int), st));
+  differ_kernel<<<grid_blocks(a->lay.total, 256), 256, 0, st>>>(
+      reinterpret_cast<const unsigned*>(a->kappa), reinterpret_cast<const unsigned*>(b->kappa), a->lay.total, a->dflag);
+  SW_CUDA(cudaGetLastError());
+  int flag = 0;
+  SW_CUDA(cudaMemcpyAsync(&flag, a->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SW_CUDA(cudaStreamSynchronize(st));
+  SW_CUDA(cudaMemsetAsync(a->dflag, 0, sizeof(int), st));
+  *same = flag == 0;
+  return SW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
+  g_last_error.clear();
+  if (!out || !grids || n_grids < 1) return fail(SW_EINVAL, "NULL argument or empty batch");
+  *out = nullptr;
+  const sw_grid* g0 = grids[0];
+  for (int i = 0; i < n_grids; ++i) {
+    const sw_grid* g = grids[i];
+    if (!g) return fail(SW_EINVAL, "grid %d is NULL", i);
+    if (!g->has_model || !g->has_acq) return fail(SW_ESTATE, "grid %d has no model or acquisition yet", i);
+    if (g->ndim != 2) return fail(SW_EINVAL, "batches hold 2D grids only (grid %d)", i);
+    if (g->has_density) return fail(SW_EINVAL, "batches hold constant-density grids only (grid %d)", i);
+    if (g->R != g0->R) return fail(SW_EINVAL, "all grids of a batch need one space order (grid %d)", i);
+    if (g->stream != g0->stream || g->device != g0->device)
+      return fail(SW_EINVAL, "all grids of a batch need one device and stream (grid %d)", i);
+    if (g->n_force > 0 || g->snapshots) return fail(SW_EINVAL, "grid %d has forcing or snapshots set", i);
+    for (int j = 0; j < i; ++j)
+      if (grids[j] == g) return fail(SW_EINVAL, "grid %d appears twice", i);
+  }
+  sw_batch* b = new sw_batch();
+  b->grids.assign(grids, grids + n_grids);
+  b->R = g0->R;
+  b->stream = g0->stream;
+  // groups: grids of the same geometry with bit-identical kappa
+  std::vector<std::vector<int>> members;
+  b->grid_group.assign(size_t(n_grids), -1);
+  for (int i = 0; i < n_grids; ++i) {
+    b->gens.push_back(grids[i]->config_gen);
+    for (size_t k = 0; k < members.size() && b->grid_group[size_t(i)] < 0; ++k) {
+      sw_grid* rep = grids[members[k][0]];
+      if (!same_geometry(rep, grids[i])) continue;
+      bool same = false;
+      const sw_status st = same_model(rep, grids[i], b->stream, &same);
+      if (st != SW_OK) {
+        delete b;
+        return st;
+      }
+      if (same) {
+        members[k].push_back(i);
+        b->grid_group[size_t(i)] = int(k);
+      }
+    }
+    if (b->grid_group[size_t(i)] < 0) {
+      b->grid_group[size_t(i)] = int(members.size());
+      members.push_back({i});
+    }
+  }
+  std::vector<BatchGroup> groups;
+  double v[kMaxR + 1];
+  fd_second_weights(g0->order, v);
+  int tiles = 0;
+  for (const auto& m : members) {
+    const sw_grid* g = grids[m[0]];
+    BatchGroup G;
+    memset(&G, 0, sizeof(G));
+    G.kappa = g->at0(g->kappa);
+    G.damp = g->damp;
+    G.sz = g->lay.sz;
+    G.nz = int(g->n[0]);
+    G.nx = int(g->n[2]);
+    const int faces[4] = {0, 1, 4, 5};
+    for (int k = 0; k < 4; ++k) {
+      G.nbl[k] = g->nbl[faces[k]];
+      G.bc[k] = g->bc[faces[k]];
+    }
+    for (int j = 1; j <= g->R; ++j) {
+      G.cz[j] = float(v[j] / (g->h[0] * g->h[0]));
+      G.cx[j] = float(v[j] / (g->h[2] * g->h[2]));
+    }
+    G.first = int(b->slot_grid.size());
+    G.count = int(m.size());
+    G.tiles_x = (G.nx + kBatchTX - 1) / kBatchTX;
+    G.tile_base = tiles;
+    tiles += G.tiles_x * ((G.nz + kBatchZB - 1) / kBatchZB);
+    for (int i : m) {
+      sw_grid* s = grids[i];
+      b->slot_grid.push_back(i);
+      BatchShot S;
+      memset(&S, 0, sizeof(S));
+      S.u[0] = s->at0(s->u[0]);
+      S.u[1] = s->at0(s->u[1]);
+      S.src = point_set(s, true);
+      S.rec = point_set(s, false);
+      S.kappa = s->at0(s->kappa);
+      S.damp = s->damp;
+      S.f = s->faces();
+      S.wavelet = s->wavelet;
+      S.sig_stride = s->sig_stride;
+      S.seis = nullptr;
+      b->shots.push_back(S);
+      b->max_src_taps = std::max(b->max_src_taps, s->n_src * s->lz * s->ly * s->lx);
+      b->max_rec = std::max(b->max_rec, s->n_rec);
+      b->nodes_per_step += s->nodes();
+    }
+    groups.push_back(G);
+  }
+  b->n_groups = int(groups.size());
+  b->total_tiles = tiles;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchTX, 0);
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  b->blocks = std::min(tiles, per_sm * std::max(g0->sm_count, 1));
+  e = cudaMalloc((void**)&b->d_groups, groups.size() * sizeof(BatchGroup));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_shots, b->shots.size() * sizeof(BatchShot));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_groups, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_shots, b->shots.data(), b->shots.size() * sizeof(BatchShot), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sw_destroy_batch(b);
+    return fail(e == cudaErrorMemoryAllocation ? SW_ENOMEM : SW_ECUDA, "batch set-up failed: %s",
+                cudaGetErrorString(e));
+  }
+  *out = b;
+  return SW_OK;
+}
+
+sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_tiles) {
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (n_groups) *n_groups = b->n_groups;
+  if (n_tiles) *n_tiles = b->total_tiles;
+  return SW_OK;
+}
+
+sw_status sw_batch_set_profiling(sw_batch* b, int every) {
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (every < 0) return fail(SW_EINVAL, "negative profiling stride");
+  b->profiling = every;
+  b->last_steps = -1;  // the captured loop has no timing events: capture anew
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = -1;
+  }
+  return SW_OK;
+}
+
+sw_status sw_batch_get_profile(const sw_batch* b, double* stencil_ms, int64_t* stencil_launches,
+                               int64_t* kernel_launches) {
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (stencil_ms) *stencil_ms = b->stencil_ms;
+  if (stencil_launches) *stencil_launches = b->stencil_launches;
+  if (kernel_launches) *kernel_launches = b->kernel_launches;
+  return SW_OK;
+}
+
+sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, float* const* final_fields) {
+  g_last_error.clear();
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (n_steps < 0) return fail(SW_EINVAL, "n_steps < 0");
+  const int n = int(b->grids.size());
+  for (int i = 0; i < n; ++i) {
+    const sw_grid* g = b->grids[size_t(i)];
+    if (g->config_gen != b->gens[size_t(i)] || g->n_force > 0 || g->snapshots)
+      return fail(SW_ESTATE, "grid %d changed after sw_create_batch", i);
+    if (g->n_src > 0 && n_steps > g->nt)
+      return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length of grid %d (%d)", n_steps, i, g->nt);
+    if (g->n_rec > 0 && n_steps > 0) {
+      if (!seismograms || !seismograms[i]) return fail(SW_EINVAL, "seismogram of grid %d is NULL", i);
+      if (!is_device_pointer(seismograms[i])) return fail(SW_EINVAL, "seismogram of grid %d is not device memory", i);
+    }
+  }
+  cudaStream_t st = b->stream;
+  // the seismogram pointers of this call into the shot table
+  bool changed = false;
+  for (size_t k = 0; k < b->shots.size(); ++k) {
+    const int i = b->slot_grid[k];
+    float* s = (b->grids[size_t(i)]->n_rec > 0 && n_steps > 0) ? seismograms[i] : nullptr;
+    if (b->shots[k].seis != s) {
+      b->shots[k].seis = s;
+      changed = true;
+    }
+  }
+  if (changed) {
+    SW_CUDA(cudaMemcpyAsync(b->d_shots, b->shots.data(), b->shots.size() * sizeof(BatchShot),
+                            cudaMemcpyHostToDevice, st));
+    SW_CUDA(cudaStreamSynchronize(st));  // the host table may change again on the next call
+  }
+  for (sw_grid* g : b->grids) {
+    const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+    SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
+    const FaceInfo f = g->faces();
+    if (g->init_p0)
+      insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->init_p0, g->at0(g->u[0]), f, 2, g->R);
+    if (g->init_pm1)
+      insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->init_pm1, g->at0(g->u[1]), f, 2, g->R);
+  }
+  SW_CUDA(cudaGetLastError());
+  const int timed = b->profiling ? (n_steps + b->profiling - 1) / b->profiling : 0;
+  if (timed && b->events.size() < size_t(2 * timed)) {
+    const size_t old = b->events.size();
+    b->events.resize(size_t(2 * timed));
+    for (size_t i = old; i < b->events.size(); ++i) SW_CUDA(cudaEventCreate(&b->events[i]));
+  }
+  const BatchFn fn = batch_kernel(b->R);
+  const int n_shots = int(b->shots.size());
+  int64_t launches = 0;
+  auto enqueue = [&](cudaStream_t s, bool capturing) -> sw_status {
+    const unsigned evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    launches = 0;
+    for (int step = 0; step < n_steps; ++step) {
+      int parity = step & 1;
+      const bool time_it = b->profiling && step % b->profiling == 0;
+      const int ev = time_it ? 2 * (step / b->profiling) : 0;
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev)], s, evflags));
+      const BatchGroup* dg = b->d_groups;
+      const BatchShot* ds = b->d_shots;
+      int ng = b->n_groups, nt = b->total_tiles;
+      void* args[] = {&dg, &ng, &ds, &nt, &parity};
+      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchTX), args, 0, s));
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev + 1)], s, evflags));
+      ++launches;
+      if (b->max_src_taps > 0) {
+        batch_inject_kernel<<<dim3((b->max_src_taps + 127) / 128, n_shots), 128, 0, s>>>(b->d_shots, step, parity,
+                                                                                         b->R);
+        ++launches;
+      }
+      if (b->max_rec > 0 && n_steps > 0) {
+        batch_receivers_kernel<<<dim3((b->max_rec + 3) / 4, n_shots), 128, 0, s>>>(b->d_shots, step, parity);
+        ++launches;
+      }
+    }
+    SW_CUDA(cudaGetLastError());
+    return SW_OK;
+  };
+  if (n_steps > 0 && b->graph && b->graph_steps == n_steps) {
+    SW_CUDA(cudaGraphLaunch(b->graph, st));
+  } else if (n_steps > 0 && b->last_steps == n_steps) {
+    // second call with this length: capture the time loop once, replay it after
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      b->graph_steps = -1;
+    }
+    // captured on a private stream, launched on the batch's stream after the zeroing above
+    if (!b->cap_stream) SW_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    SW_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const sw_status s1 = enqueue(b->cap_stream, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (s1 != SW_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s1 != SW_OK ? s1 : fail(SW_ECUDA, "capturing the batch time loop failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      b->graph = nullptr;
+      return fail(SW_ECUDA, "instantiating the batch time loop failed: %s", cudaGetErrorString(ei));
+    }
+    b->graph_steps = n_steps;
+    SW_CUDA(cudaGraphLaunch(b->graph, st));
+  } else if (n_steps > 0) {
+    SW_TRY(enqueue(st, false));
+  }
+  if (n_steps > 0) b->last_steps = n_steps;
+  if (n_steps > 0 && launches == 0) {  // a replayed graph: count what it holds
+    launches = int64_t(n_steps) * (1 + (b->max_src_taps > 0) + (b->max_rec > 0));
+  }
+  for (int i = 0; final_fields && i < n; ++i) {
+    if (!final_fields[i]) continue;
+    sw_grid* g = b->grids[size_t(i)];
+    float* dst = final_fields[i];
+    const bool fh = !is_device_pointer(dst);
+    if (fh) {
+      if (!g->staging) SW_TRY(dev_alloc(g, (void**)&g->staging, size_t(g->nodes()) * sizeof(float)));
+      dst = g->staging;
+    }
+    extract_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(g->u[n_steps & 1]), dst, g->faces());
+    SW_CUDA(cudaGetLastError());
+    ++launches;
+    if (fh)
+      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  SW_CUDA(cudaStreamSynchronize(st));
+  b->kernel_launches = launches;
+  b->stencil_launches = timed;
+  b->stencil_ms = 0.0;
+  for (int i = 0; i < timed; ++i) {
+    float ms = 0.f;
+    SW_CUDA(cudaEventElapsedTime(&ms, b->events[size_t(2 * i)], b->events[size_t(2 * i + 1)]));
+    b->stencil_ms += ms;
+  }
+  return SW_OK;
+}
+
+void sw_destroy_batch(sw_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  cudaFree(b->d_groups);
+  cudaFree(b->d_shots);
+  delete b;
+}
+
+}  // extern "C"

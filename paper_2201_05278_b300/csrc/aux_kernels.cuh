@@ -45,11 +45,10 @@ __device__ __forceinline__ void add_with_mirrors(float* p, int64_t idx, int i, i
 // of every source (1/prod(h) is folded into the x weights).  The ghost images
 // of nodes near mirrored faces get the same increment (with the face's sign),
 // so the ghost layer stays consistent with p[n+1].  Dirichlet face nodes stay 0.
-__global__ void inject_sources_kernel(float* p, const float* kappa, const float2* damp, PointSet src,
-                                      const float* sig, int sig_stride, int step, FaceInfo f, int ndim,
-                                      int R) {
+__device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, const float2* damp,
+                                                  const PointSet& src, const float* sig, int sig_stride, int step,
+                                                  const FaceInfo& f, int ndim, int R, int t) {
   const int taps = src.lz * src.ly * src.lx;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= src.count * taps) return;
   const int s = t / taps;
   int rem = t % taps;
@@ -79,6 +78,12 @@ __global__ void inject_sources_kernel(float* p, const float* kappa, const float2
   add_with_mirrors(p, idx, z, f.nz, f.sz, f.bc[0], f.bc[1], R, d);
   add_with_mirrors(p, idx, x, f.nx, 1, f.bc[4], f.bc[5], R, d);
   if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
+}
+
+__global__ void inject_sources_kernel(float* p, const float* kappa, const float2* damp, PointSet src,
+                                      const float* sig, int sig_stride, int step, FaceInfo f, int ndim,
+                                      int R) {
+  inject_source_tap(p, kappa, damp, src, sig, sig_stride, step, f, ndim, R, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Tap table of the sources for the pipelined path, built once per forward

@@ -214,6 +214,25 @@ __global__ void __launch_bounds__(TX*(TY / PPT)) stencil_plain_kernel(const Sten
 // shared plane would leave most SMs idle on such grids).  Same arithmetic
 // and face handling as stencil_plain_kernel; one block row of 128 nodes
 // per (x tile, z) pair.
+// Eq. 9 in 2D from the 2R+1 values along z and along x around a node (centre
+// at index R), each pair as (p[+j] + p[-j]) - 2p.
+template <int R>
+__device__ __forceinline__ float laplacian_2d(const float* qz, const float* qx, const float* cz, const float* cx) {
+  const float p2 = 2.f * qz[R];
+  float lap = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    lap = fmaf(cz[j], (qz[R + j] + qz[R - j]) - p2, lap);
+    lap = fmaf(cx[j], (qx[R + j] + qx[R - j]) - p2, lap);
+  }
+  return lap;
+}
+
+// Eq. 7 divided by (1 + e): p[n+1] = a (p + (kappa L + (p - p[n-1]) + e p[n-1])).
+__device__ __forceinline__ float leapfrog_update(float pc, float po, float kp, float lap, float ca, float e) {
+  return ca * (pc + fmaf(kp, lap, fmaf(e, po, pc - po)));
+}
+
 template <int R, bool VD>
 __device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int x) {
   const int64_t sz = a.sz;
@@ -228,13 +247,7 @@ __device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int
   const float po = a.pnm1[idx];
   const float kp = __ldg(&a.kappa[idx]);
   const float pc = qz[R];
-  const float p2 = 2.f * pc;
-  float lap = 0.f;
-#pragma unroll
-  for (int j = 1; j <= R; ++j) {
-    lap = fmaf(a.cz[j], (qz[R + j] + qz[R - j]) - p2, lap);
-    lap = fmaf(a.cx[j], (qx[R + j] + qx[R - j]) - p2, lap);
-  }
+  float lap = laplacian_2d<R>(qz, qx, a.cz, a.cx);
   if constexpr (VD) {
     const float* l = a.lnrho;
     float dpz = 0.f, dlz = 0.f, dpx = 0.f, dlx = 0.f;
@@ -256,8 +269,7 @@ __device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int
     ca = c.x;
     e = c.y;
   }
-  const float dp = pc - po;
-  float pnew = ca * (pc + fmaf(kp, lap, fmaf(e, po, dp)));
+  float pnew = leapfrog_update(pc, po, kp, lap, ca, e);
   const bool dir = (z == 0 && a.bc[0] == kBcDirichlet) || (z == a.nz - 1 && a.bc[1] == kBcDirichlet) ||
                    (x == 0 && a.bc[4] == kBcDirichlet) || (x == a.nx - 1 && a.bc[5] == kBcDirichlet);
   if (dir) pnew = 0.f;
