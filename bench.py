@@ -70,17 +70,21 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-def _kernel_source_hash():
+STENCIL_SOURCES = ("stencil_plain.cuh", "stencil_tma.cuh", "tma.cuh", "layout.h")
+BATCH_SOURCES = ("batch.cuh", "stencil_plain.cuh", "layout.h")
+
+
+def _kernel_source_hash(names=STENCIL_SOURCES):
     h = hashlib.sha256()
-    for name in ("stencil_plain.cuh", "stencil_tma.cuh", "tma.cuh", "layout.h"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2201_05278_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _traffic_record(workload):
+def _traffic_record(workload, fname="stencil_traffic.txt", names=STENCIL_SOURCES):
     """DRAM bytes per stencil launch from the committed ncu summary, if still current."""
-    path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         rec = {}
         with open(path) as f:
@@ -88,7 +92,7 @@ def _traffic_record(workload):
                 if ":" in ln and not ln.startswith("#"):
                     k, v = ln.split(":", 1)
                     rec[k.strip()] = v.strip()
-        if rec.get("workload") != workload or rec.get("source_sha") != _kernel_source_hash():
+        if rec.get("workload") != workload or rec.get("source_sha") != _kernel_source_hash(names):
             return None
         return float(rec["dram_bytes_per_launch"])
     except Exception:
@@ -151,11 +155,12 @@ class ClockSampler:
 
 
 def cpu_baseline(workload_name, budget_s=12.0):
-    """Times the FP64 oracle on the host cores on a bounded sample of the workload."""
+    """Times the FP64 oracle on the host cores on a bounded sample of the workload
+    (for a shot batch: on its first shot, the oracle running one shot at a time)."""
     from paper_2201_05278_b300 import workloads
     import oracle
     threads = os.cpu_count() or 1
-    w = workloads.make(workload_name)
+    w = workloads.shot_batch()[0] if workload_name in workloads.BATCH_NAMES else workloads.make(workload_name)
     wav = oracle.ricker_samples(w.f_peak, w.dt, 400, t0=w.t0)
 
     def run(steps):
@@ -178,7 +183,112 @@ def cpu_baseline(workload_name, budget_s=12.0):
     value = w.nodes * steps / t / 1e9  # whole call, set-up included
     return {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%s full grid %s, %d of %d time steps, FP64, %d threads" % (
-                workload_name, "x".join(map(str, w.shape)), steps, w.n_steps, threads)}, t
+                w.name, "x".join(map(str, w.shape)), steps, w.n_steps, threads)}, t
+
+
+def run_batch(args, world, rank, local, dev):
+    """The shot batch: every shot of 2d_shot_batch_64 advanced by one batched
+    launch per time step (sw_batch_forward); a bench step = one forward of all
+    shots; Gpts/s counts the nodes of every shot."""
+    import torch
+    from paper_2201_05278_b300 import api, workloads
+
+    shots = workloads.shot_batch(n_steps=args.time_steps or None)
+    stream = torch.cuda.current_stream(dev)
+    grids, models = [], {}
+    for w in shots:
+        g = api.sw_create_grid(2, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
+                               stream=stream)
+        if id(w.velocity) not in models:
+            models[id(w.velocity)] = (torch.from_numpy(w.velocity).to(dev), w.nodes)
+        api.sw_set_model(g, models[id(w.velocity)][0])
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps),
+                               window_radius=w.window_radius)
+        grids.append(g)
+    b = api.sw_create_batch(grids)
+    n_groups, n_items = api.sw_batch_info(b)
+    n_steps = shots[0].n_steps
+    seis = [torch.empty((n_steps, len(w.rec_pos)), dtype=torch.float32, device=dev) for w in shots]
+    shot_nodes = sum(w.nodes for w in shots)
+    model_nodes = sum(n for _, n in models.values())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        api.sw_batch_forward(b, n_steps, seis)
+    api.sw_batch_set_profiling(b, PROFILE_EVERY)
+    for _ in range(2):  # the second call captures the loop with its timing events
+        api.sw_batch_forward(b, n_steps, seis)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stencil_ms, stencil_launches, kernels = 0.0, 0, 0
+    start.record(stream)
+    for _ in range(args.steps):
+        api.sw_batch_forward(b, n_steps, seis)
+        ms, nl, nk = api.sw_batch_get_profile(b)
+        stencil_ms += ms
+        stencil_launches += nl
+        kernels += nk
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = job_seconds(start.elapsed_time(stop) * 1e-3, world, dev) * 1e3
+    value = job_throughput(shot_nodes * n_steps, args.steps, world, elapsed_ms * 1e-3)
+
+    # e2e: the same forwards with every shot's seismogram read back into pinned
+    # host memory (the inputs stay resident: models and wavelets are set up once)
+    seis_h = [torch.empty(s.shape, dtype=torch.float32).pin_memory() for s in seis]
+    e2e = None
+    if args.e2e_steps > 0:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            api.sw_batch_forward(b, n_steps, seis)
+            for d, h in zip(seis, seis_h):
+                h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            _ = float(seis_h[-1][-1, 0])
+        barrier()
+        e2e_s = job_seconds(time.perf_counter() - t0, world, dev)
+        e2e = {"value": round(job_throughput(shot_nodes * n_steps, args.e2e_steps, world, e2e_s), 3), "unit": UNIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(sum(h.numel() for h in seis_h) * 4)}
+
+    peak, peak_kind = _peaks()
+    avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
+    alg_bytes = 12 * shot_nodes + 4 * model_nodes
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = _traffic_record(args.workload, "batch_traffic.txt", BATCH_SOURCES)
+    b.close()
+    for g in grids:
+        g.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "shots": len(shots), "models": n_groups, "work_items_per_step": n_items,
+                       "nodes_per_step": shot_nodes, "space_order": shots[0].order,
+                       "time_steps_per_forward": n_steps, "receivers_per_shot": len(shots[0].rec_pos),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "batched stencil (CUDA events around every %dth launch, %d launches timed)" % (
+                             PROFILE_EVERY, stencil_launches),
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+            "e2e": e2e,
+            "gpu_launches": int(kernels),
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cb, _ = cpu_baseline(args.workload)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
 
 
 def main():
@@ -223,6 +333,11 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    if args.workload in workloads.BATCH_NAMES:
+        run_batch(args, world, rank, local, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     w = workloads.make(args.workload, n_steps=args.time_steps or None)
     vd = w.density is not None

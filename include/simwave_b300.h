@@ -247,13 +247,14 @@ sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t
  * after the last step (host or device).  The time loop is captured as a CUDA
  * graph on the second call with the same n_steps.  Blocks until done.
  *
- * sw_batch_info: number of model groups and of tiles per step.
+ * sw_batch_info: number of model groups and of work items (tile of one
+ * shot) per step.
  * sw_batch_set_profiling / sw_batch_get_profile: as for a grid (every
  * every-th stencil launch timed with CUDA events).
  */
 sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids);
 sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, float* const* final_fields);
-sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_tiles);
+sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_items);
 sw_status sw_batch_set_profiling(sw_batch* b, int every);
 sw_status sw_batch_get_profile(const sw_batch* b, double* stencil_ms, int64_t* stencil_launches,
                                int64_t* kernel_launches);

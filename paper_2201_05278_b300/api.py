@@ -219,7 +219,7 @@ def sw_batch_forward(b: Batch, n_steps: int, seismograms=None, final_fields=None
 
 
 def sw_batch_info(b: Batch):
-    """(model groups, tiles per step)."""
+    """(model groups, work items per step: tiles x shots)."""
     ng, nt = ctypes.c_int(), ctypes.c_int()
     _check(_lib.load().sw_batch_info(b.handle, ctypes.byref(ng), ctypes.byref(nt)))
     return ng.value, nt.value

@@ -1687,8 +1687,9 @@ struct sw_batch {
   std::vector<BatchShot> shots;  // host copy of the shot table
   BatchGroup* d_groups = nullptr;
   BatchShot* d_shots = nullptr;
-  int n_groups = 0, total_tiles = 0, blocks = 0, R = 0;
+  int n_groups = 0, total_items = 0, blocks = 0, R = 0;
   int max_src_taps = 0, max_rec = 0;
+  int smem = 0;  // dynamic shared memory of the batched stencil
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -1703,6 +1704,21 @@ struct sw_batch {
 namespace {
 
 using BatchFn = void (*)(const BatchGroup*, int, const BatchShot*, int, int);
+
+int batch_smem_bytes(int R) {
+  switch (R) {
+    case 1: return BatchSmem<1>::BYTES;
+    case 2: return BatchSmem<2>::BYTES;
+    case 3: return BatchSmem<3>::BYTES;
+    case 4: return BatchSmem<4>::BYTES;
+    case 5: return BatchSmem<5>::BYTES;
+    case 6: return BatchSmem<6>::BYTES;
+    case 7: return BatchSmem<7>::BYTES;
+    case 8: return BatchSmem<8>::BYTES;
+    case 9: return BatchSmem<9>::BYTES;
+    default: return BatchSmem<10>::BYTES;
+  }
+}
 
 BatchFn batch_kernel(int R) {
   switch (R) {
@@ -1770,6 +1786,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
     if (g->stream != g0->stream || g->device != g0->device)
       return fail(SW_EINVAL, "all grids of a batch need one device and stream (grid %d)", i);
     if (g->n_force > 0 || g->snapshots) return fail(SW_EINVAL, "grid %d has forcing or snapshots set", i);
+    if (g->lay.total >= (int64_t(1) << 31)) return fail(SW_EINVAL, "grid %d is too large for a batch", i);
     for (int j = 0; j < i; ++j)
       if (grids[j] == g) return fail(SW_EINVAL, "grid %d appears twice", i);
   }
@@ -1826,8 +1843,8 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
     G.first = int(b->slot_grid.size());
     G.count = int(m.size());
     G.tiles_x = (G.nx + kBatchTX - 1) / kBatchTX;
-    G.tile_base = tiles;
-    tiles += G.tiles_x * ((G.nz + kBatchZB - 1) / kBatchZB);
+    G.item_base = tiles;
+    tiles += G.tiles_x * ((G.nz + kBatchZB - 1) / kBatchZB) * G.count;
     for (int i : m) {
       sw_grid* s = grids[i];
       b->slot_grid.push_back(i);
@@ -1851,9 +1868,13 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
     groups.push_back(G);
   }
   b->n_groups = int(groups.size());
-  b->total_tiles = tiles;
+  b->total_items = tiles;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchTX, 0);
+  b->smem = batch_smem_bytes(b->R);
+  cudaError_t e = cudaFuncSetAttribute((const void*)batch_kernel(b->R), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       b->smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchTX, size_t(b->smem));
   if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   b->blocks = std::min(tiles, per_sm * std::max(g0->sm_count, 1));
   e = cudaMalloc((void**)&b->d_groups, groups.size() * sizeof(BatchGroup));
@@ -1875,10 +1896,10 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
   return SW_OK;
 }
 
-sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_tiles) {
+sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_items) {
   if (!b) return fail(SW_EINVAL, "NULL batch");
   if (n_groups) *n_groups = b->n_groups;
-  if (n_tiles) *n_tiles = b->total_tiles;
+  if (n_items) *n_items = b->total_items;
   return SW_OK;
 }
 
@@ -1966,9 +1987,9 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev)], s, evflags));
       const BatchGroup* dg = b->d_groups;
       const BatchShot* ds = b->d_shots;
-      int ng = b->n_groups, nt = b->total_tiles;
+      int ng = b->n_groups, nt = b->total_items;
       void* args[] = {&dg, &ng, &ds, &nt, &parity};
-      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchTX), args, 0, s));
+      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchTX), args, size_t(b->smem), s));
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev + 1)], s, evflags));
       ++launches;
       if (b->max_src_taps > 0) {

@@ -23,6 +23,14 @@ available, so synthetic layered models of the same kind stand in for them:
                        Gardner density rho = 310 v^0.25, 3000 steps, 10 Hz,
                        50-cell layer, 128 x 128 receivers at the surface
 
+  2d_shot_batch_64     64 shots for batched runs: 8 models (seeds 0..7) of
+                       (nz, nx) drawn from U{300..800} x U{400..1200}, h = 10 m,
+                       3-8 flat layers at random depths with random speeds in
+                       1500-4500 m/s; 8 shots per model with sources 2 cells
+                       deep spread evenly along the surface; 256 receivers per
+                       shot 2 cells deep across the surface; order 8, 10 Hz,
+                       40-cell layer, 2000 steps (shot_batch())
+
 Every model has no absorbing layer on the top face, which is null Neumann
 (as in the paper's listings); the other faces are null Dirichlet behind the
 layer.  dt = 0.4 h / c_max (Courant number 0.4).  The damping alpha follows a
@@ -173,4 +181,34 @@ def make(name: str, n_steps: Optional[int] = None, shape: Optional[Tuple[int, ..
     raise KeyError(name)
 
 
+def shot_batch(n_models: int = 8, shots_per_model: int = 8, n_steps: Optional[int] = None,
+               size_scale: float = 1.0) -> List[Workload]:
+    """The shots of 2d_shot_batch_64 (model after model); size_scale shrinks the
+    grids for quick tests.  Shots of one model share its velocity array and dt."""
+    out = []
+    h = (10.0, 10.0)
+    nb = 40
+    f = 10.0
+    for m in range(n_models):
+        rng = np.random.default_rng(m)
+        nz = max(2 * nb + 20, int(round(int(rng.integers(300, 801)) * size_scale)))
+        nx = max(2 * nb + 40, int(round(int(rng.integers(400, 1201)) * size_scale)))
+        n_layers = int(rng.integers(3, 9))
+        depths = np.sort(rng.choice(np.arange(1, nz), size=n_layers - 1, replace=False))
+        speeds = 1500.0 + 3000.0 * rng.random(n_layers)
+        v1 = speeds[np.searchsorted(depths, np.arange(nz), side="right")].astype(np.float32)
+        vel = np.ascontiguousarray(np.broadcast_to(v1[:, None], (nz, nx)), dtype=np.float32)
+        c_max = float(vel.max())
+        dt = 0.4 * h[0] / c_max
+        phys_x = (nx - 2 * nb - 1) * h[1]
+        rec = np.stack([np.full(256, 2 * h[0]), _grid_positions(0.02 * phys_x, 0.98 * phys_x, 256)], 1)
+        for k in range(shots_per_model):
+            src = np.array([[2 * h[0], (k + 0.5) / shots_per_model * phys_x]])
+            out.append(Workload("2d_shot_batch_64/model%d/shot%d" % (m, k), 2, (nz, nx), h, 8, [0, nb, nb, nb],
+                                ["null_neumann", "null_dirichlet", "null_dirichlet", "null_dirichlet"],
+                                _alpha(c_max, nb, h[0]), 3, dt, n_steps or 2000, f, 1.0 / f, src, rec, 4, vel))
+    return out
+
+
 NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384"]
+BATCH_NAMES = ["2d_shot_batch_64"]
