@@ -1703,7 +1703,7 @@ struct sw_batch {
 
 namespace {
 
-using BatchFn = void (*)(const BatchGroup*, int, const BatchShot*, int, int);
+using BatchFn = void (*)(const BatchGroup*, int, const BatchShot*, int, int, int*, unsigned long long);
 
 int batch_smem_bytes(int R) {
   switch (R) {
@@ -1874,7 +1874,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
   cudaError_t e = cudaFuncSetAttribute((const void*)batch_kernel(b->R), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        b->smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchTX, size_t(b->smem));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchThreads, size_t(b->smem));
   if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   b->blocks = std::min(tiles, per_sm * std::max(g0->sm_count, 1));
   e = cudaMalloc((void**)&b->d_groups, groups.size() * sizeof(BatchGroup));
@@ -1988,8 +1988,11 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
       const BatchGroup* dg = b->d_groups;
       const BatchShot* ds = b->d_shots;
       int ng = b->n_groups, nt = b->total_items;
-      void* args[] = {&dg, &ng, &ds, &nt, &parity};
-      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchTX), args, size_t(b->smem), s));
+      int* flag = b->grids[0]->dflag;
+      unsigned long long limit = b->grids[0]->wait_limit_ns;
+      void* args[] = {&dg, &ng, &ds, &nt, &parity, &flag, &limit};
+      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchThreads), args, size_t(b->smem),
+                               s));
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev + 1)], s, evflags));
       ++launches;
       if (b->max_src_taps > 0) {
@@ -2055,7 +2058,7 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
     if (fh)
       SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
   }
-  SW_CUDA(cudaStreamSynchronize(st));
+  SW_TRY(check_device_flag(b->grids[0]));  // synchronises
   b->kernel_launches = launches;
   b->stencil_launches = timed;
   b->stencil_ms = 0.0;

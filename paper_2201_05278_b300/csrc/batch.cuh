@@ -12,24 +12,26 @@
 // rows; a work item is one tile of one shot.  Items are numbered group after
 // group, tile-major with the shot fastest (so the shots of a tile run side by
 // side and read its kappa once from memory, then from L2), and a persistent
-// grid walks them.  A CTA copies the whole item (p[n] with its halo, p[n-1],
-// kappa) into shared memory with asynchronous 16-byte copies, one copy group
-// per chunk of kBatchU rows, and computes each chunk as soon as its group has
-// landed, so that an item's reads are all in flight at once.  One thread
-// owns one column and keeps its z-neighbours in a register queue; the
-// x-neighbours come from the shared image.  The arithmetic is the same
-// sequence of operations as the single-grid 2D kernel (laplacian_2d,
-// leapfrog_update), so a batched shot reproduces its single-grid run bit for
-// bit.
+// grid walks them.  One warp copies the item's p[n] rows (with both halos)
+// into shared memory with 1D bulk copies, one mbarrier per chunk of kBatchU
+// rows, and every thread computes a chunk as soon as its barrier completes,
+// so that an item's reads are all in flight at once; p[n-1] and kappa are
+// loaded into registers a chunk ahead (across items too).  A thread owns one
+// column and keeps its z-neighbours in a register queue; the x-neighbours
+// come from the shared image.  The arithmetic is the single-grid 2D kernel's
+// (laplacian_2d, leapfrog_update), so a batched shot reproduces its
+// single-grid run bit for bit.
 #pragma once
 
 #include "aux_kernels.cuh"
 #include "layout.h"
 #include "stencil_plain.cuh"
+#include "tma.cuh"
 
 namespace sw {
 
-constexpr int kBatchTX = 128;  // columns per tile, one per thread
+constexpr int kBatchTX = 128;       // columns per tile
+constexpr int kBatchThreads = 128;  // one column per thread
 constexpr int kBatchZB = 32;   // rows per tile
 constexpr int kBatchU = 4;     // rows per register-queue chunk
 
@@ -61,88 +63,115 @@ struct BatchShot {
 
 // Shared-memory image of one work item: p[n] rows z0 - R .. z0 + ZB + R - 1
 // over columns x0 - RH .. x0 + TX + RH - 1 (RH = R rounded up to 4 floats, so
-// that every row starts on a 16-byte boundary), p[n-1] and kappa of rows
-// z0 .. z0 + ZB - 1 over the tile's columns.
+// that every row starts on a 16-byte boundary).  p[n-1] and kappa, read once
+// and without neighbours, go straight to registers, a chunk ahead.
 template <int R>
 struct BatchSmem {
   static constexpr int RH = (R + 3) / 4 * 4;
   static constexpr int TXP = kBatchTX + 2 * RH;
   static constexpr int PROWS = kBatchZB + 2 * R;
-  static constexpr int BYTES = (PROWS * TXP + 2 * kBatchZB * kBatchTX) * 4;
+  static constexpr int BYTES = PROWS * TXP * 4;
+};
+static_assert(kBatchZB / kBatchU <= 8, "one mbarrier per chunk, at most 8");
+
+// 1D bulk copy global -> shared, completing `bytes` on the mbarrier `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Where a work item lies: its group, shot, first column and row range.
+struct BatchItem {
+  int g, s, x0, z0, z1, nch;
 };
 
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// wait until at most n of this thread's copy groups are still in flight
-__device__ __forceinline__ void cp_async_wait(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+__device__ __forceinline__ BatchItem batch_item(const BatchGroup* __restrict__ groups, int n_groups, int t) {
+  int lo = 0, hi = n_groups - 1;  // last group whose first item is <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].item_base <= t) lo = mid;
+    else hi = mid - 1;
   }
+  const BatchGroup& G = groups[lo];
+  // items of a group: tile-major, shot fastest, so that the shots of one
+  // tile run at about the same time and share its kappa reads through L2
+  const int local = t - G.item_base;
+  const int tile = local / G.count;
+  const int strip = tile / G.tiles_x;
+  BatchItem it;
+  it.g = lo;
+  it.s = G.first + (local - tile * G.count);
+  it.x0 = (tile - strip * G.tiles_x) * kBatchTX;
+  it.z0 = strip * kBatchZB;
+  it.z1 = min(it.z0 + kBatchZB, G.nz);
+  it.nch = (it.z1 - it.z0 + kBatchU - 1) / kBatchU;
+  return it;
 }
-static_assert(kBatchZB / kBatchU <= 8, "at most 8 copy groups per work item");
 
 template <int R>
-__global__ void __launch_bounds__(kBatchTX) batch_stencil_2d_kernel(const BatchGroup* __restrict__ groups,
-                                                                   int n_groups, const BatchShot* __restrict__ shots,
-                                                                   int total_items, int parity) {
+__global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
+    const BatchGroup* __restrict__ groups, int n_groups, const BatchShot* __restrict__ shots, int total_items,
+    int parity, int* err_flag, unsigned long long limit_ns) {
   using S = BatchSmem<R>;
-  extern __shared__ __align__(16) float batch_smem[];
-  float* P = batch_smem;                         // [PROWS][TXP]
-  float* O = batch_smem + S::PROWS * S::TXP;     // [ZB][TX]
-  float* K = O + kBatchZB * kBatchTX;            // [ZB][TX]
+  constexpr int TXP = S::TXP, RH = S::RH;
+  extern __shared__ __align__(128) float batch_smem[];  // the image [PROWS][TXP]
+  __shared__ __align__(8) uint64_t bars[8];            // one per chunk
+  __shared__ int abort_s;
   const int tid = threadIdx.x;
-  for (int t = blockIdx.x; t < total_items; t += gridDim.x) {
-    int lo = 0, hi = n_groups - 1;  // last group whose first item is <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (groups[mid].item_base <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchGroup& G = groups[lo];
-    // items of a group: tile-major, shot fastest, so that the shots of one
-    // tile run at about the same time and share its kappa reads through L2
-    const int local = t - G.item_base;
-    const int tile = local / G.count;
-    const int s = G.first + (local - tile * G.count);
-    const int strip = tile / G.tiles_x;
-    const int x0 = (tile - strip * G.tiles_x) * kBatchTX;
-    const int nz = G.nz, nx = G.nx;
-    const int z0 = strip * kBatchZB;
-    const int z1 = min(z0 + kBatchZB, nz);
-    const int sz = int(G.sz);  // a padded field holds fewer than 2^31 elements (checked on the host)
-    const float* pn = shots[s].u[parity] + x0;
-    float* pout = shots[s].u[parity ^ 1] + x0;  // holds p[n-1] until overwritten
-    const float* kap = G.kappa + x0;
+  if (tid == 0) {
+    for (int k = 0; k < 8; ++k) mbar_init(smem_addr(&bars[k]), 1);
+    abort_s = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  unsigned phases = 0;   // parity of the next phase of every barrier
+  unsigned pending = 0;  // barriers armed and not yet seen complete
 
-    // copies: group 0 = p rows of the first chunk with both halos, then one
-    // group per chunk (its R-ahead p rows, its p[n-1] and kappa rows)
-    const int nch = (z1 - z0 + kBatchU - 1) / kBatchU;
-    for (int k = 0; k < nch; ++k) {
-      const int ra = k == 0 ? 0 : 2 * R + k * kBatchU;   // smem rows of p (row r is z0 - R + r)
-      const int rb = min(2 * R + (k + 1) * kBatchU, z1 - z0 + 2 * R);
-      constexpr int CPR = S::TXP / 4;
-      for (int i = tid; i < (rb - ra) * CPR; i += kBatchTX) {
-        const int r = ra + i / CPR, c = (i - (i / CPR) * CPR) * 4;
-        cp_async16(P + r * S::TXP + c, pn + (z0 - R + r) * sz + (c - S::RH));
+  // p[n-1] and kappa of a thread's column for one chunk (rows past z1 are not read)
+  auto load_ok = [&](const BatchItem& it, int k, float* dpo, float* dkp) {
+    const BatchGroup& G = groups[it.g];
+    const int sz = int(G.sz);
+    const float* ob = shots[it.s].u[parity ^ 1] + it.x0 + tid;
+    const float* kb = G.kappa + it.x0 + tid;
+    const int z = it.z0 + k * kBatchU;
+#pragma unroll
+    for (int u = 0; u < kBatchU; ++u) {
+      const bool in = z + u < it.z1;
+      dpo[u] = in ? ob[(z + u) * sz] : 0.f;
+      dkp[u] = in ? __ldg(kb + (z + u) * sz) : 0.f;
+    }
+  };
+
+  float po[kBatchU], kp[kBatchU], npo[kBatchU] = {}, nkp[kBatchU] = {};
+  int t = blockIdx.x;
+  BatchItem cur;
+  if (t < total_items) {
+    cur = batch_item(groups, n_groups, t);
+    load_ok(cur, 0, po, kp);
+  }
+  for (; t < total_items; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    const BatchItem nxt = tn < total_items ? batch_item(groups, n_groups, tn) : cur;
+    const BatchGroup& G = groups[cur.g];
+    const int nz = G.nz, nx = G.nx, x0 = cur.x0, z0 = cur.z0, z1 = cur.z1, nch = cur.nch;
+    const int sz = int(G.sz);  // a padded field holds fewer than 2^31 elements (checked on the host)
+    float* pout = shots[cur.s].u[parity ^ 1] + x0;  // holds p[n-1] until overwritten
+
+    // warp 0 issues the item's bulk copies of p[n]: chunk 0 = the rows of the
+    // first chunk with both halos, then per chunk its R-ahead rows
+    if (tid < 32 && !abort_s) {
+      const float* pn = shots[cur.s].u[parity] + x0;
+      for (int k = 0; k < nch; ++k) {
+        const int ra = k == 0 ? 0 : 2 * R + k * kBatchU;  // image rows (row r is z0 - R + r)
+        const int rb = min(2 * R + (k + 1) * kBatchU, z1 - z0 + 2 * R);
+        const uint32_t bar = smem_addr(&bars[k]);
+        if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t((rb - ra) * TXP * 4));
+        __syncwarp();
+        for (int r = ra + tid; r < rb; r += 32)
+          bulk_load(smem_addr(batch_smem + r * TXP), pn + (z0 - R + r) * sz - RH, TXP * 4, bar);
+        pending |= 1u << k;
       }
-      const int oa = k * kBatchU, ob = min(oa + kBatchU, z1 - z0);
-      constexpr int CPO = kBatchTX / 4;
-      for (int i = tid; i < (ob - oa) * CPO; i += kBatchTX) {
-        const int r = oa + i / CPO, c = (i - (i / CPO) * CPO) * 4;
-        cp_async16(O + r * kBatchTX + c, pout + (z0 + r) * sz + c);
-        cp_async16(K + r * kBatchTX + c, kap + (z0 + r) * sz + c);
-      }
-      cp_async_commit();
     }
 
     const int x = x0 + tid;
@@ -153,8 +182,9 @@ __global__ void __launch_bounds__(kBatchTX) batch_stencil_2d_kernel(const BatchG
       cz[j] = G.cz[j];
       cx[j] = G.cx[j];
     }
-    // per-column constants: damping distance, Dirichlet column, x-mirror images
-    const int dx = layer_distance(x, nx, G.nbl[2], G.nbl[3]);
+    // per-column constants: damping distance (0 past the grid, where the
+    // damping table ends), Dirichlet column, x-face images
+    const int dx = act ? layer_distance(x, nx, G.nbl[2], G.nbl[3]) : 0;
     const int dx2 = dx * dx;
     const int bz0 = G.bc[0], bz1 = G.bc[1], bx0 = G.bc[2], bx1 = G.bc[3];
     const bool xdir = (x == 0 && bx0 == kBcDirichlet) || (x == nx - 1 && bx1 == kBcDirichlet);
@@ -164,56 +194,111 @@ __global__ void __launch_bounds__(kBatchTX) batch_stencil_2d_kernel(const BatchG
     const float xs_lo = bx0 == kBcDirichlet ? -1.f : 1.f, xs_hi = bx1 == kBcDirichlet ? -1.f : 1.f;
     const int nbz0 = G.nbl[0], nbz1 = G.nbl[1];
     const float2* damp = G.damp;
-    const float* col = P + S::RH + tid;  // this thread's column of the p image
+    // damping of this column on rows outside the z layers
+    float ca_x = 1.f, e_x = 0.f;
+    if (dx2 != 0) {
+      const float2 c = __ldg(&damp[dx2]);
+      ca_x = c.x;
+      e_x = c.y;
+    }
+    // rows with nothing special along z: no z-face image, not a Dirichlet
+    // face, outside the z absorbing layers
+    const int plain_lo = max(R + 1, nbz0), plain_hi = min(nz - 2 - R, nz - 1 - nbz1);
+    const float* col = batch_smem + RH + tid;  // this thread's column of the image
     float* out = pout + tid;
     float q[2 * R + kBatchU];  // p[n] of rows z - R .. z + R + U - 1 of this column
     for (int k = 0; k < nch; ++k) {
-      cp_async_wait(nch - 1 - k);
-      __syncthreads();
-      const int z = z0 + k * kBatchU;
-      const int rz = k * kBatchU;  // smem row of p for z - R
-      if (k == 0) {
-#pragma unroll
-        for (int j = 0; j < 2 * R; ++j) q[j] = col[j * S::TXP];
+      // the next chunk's p[n-1] and kappa (the next item's first chunk after the last)
+      if (k + 1 < nch) load_ok(cur, k + 1, npo, nkp);
+      else if (tn < total_items) load_ok(nxt, 0, npo, nkp);
+      bool ok = false;
+      if (!abort_s) ok = mbar_wait_bounded(smem_addr(&bars[k]), (phases >> k) & 1u, limit_ns);
+      if (ok) {
+        phases ^= 1u << k;
+        pending &= ~(1u << k);
+      } else {
+        if (!abort_s) atomicOr(err_flag, 1);
+        abort_s = 1;
       }
+      if (ok) {
+        const int z = z0 + k * kBatchU;
+        const int rz = k * kBatchU;  // image row of p for z - R
+        if (k == 0) {
 #pragma unroll
-      for (int u = 0; u < kBatchU; ++u) q[2 * R + u] = col[(rz + 2 * R + u) * S::TXP];  // rows past z1 + R unused
+          for (int j = 0; j < 2 * R; ++j) q[j] = col[j * TXP];
+        }
+#pragma unroll
+        for (int u = 0; u < kBatchU; ++u) q[2 * R + u] = col[(rz + 2 * R + u) * TXP];  // rows past z1 + R unused
+        if (act) {
+          if (z >= plain_lo && z + kBatchU - 1 <= plain_hi && z + kBatchU <= z1) {
+            // the common case: a whole chunk of plain rows
+            float* o = out + z * sz;
+#pragma unroll
+            for (int u = 0; u < kBatchU; ++u) {
+              const float* row = col + (rz + u + R) * TXP;
+              float qx[2 * R + 1];
+              qx[R] = q[u + R];
+#pragma unroll
+              for (int j = 1; j <= R; ++j) {
+                qx[R + j] = row[j];
+                qx[R - j] = row[-j];
+              }
+              float pnew = leapfrog_update(q[u + R], po[u], kp[u], laplacian_2d<R>(q + u, qx, cz, cx), ca_x, e_x);
+              if (xdir) pnew = 0.f;
+              o[0] = pnew;
+              if (xm_lo) o[-2 * x] = xs_lo * pnew;
+              if (xm_hi) o[2 * xr] = xs_hi * pnew;
+              o += sz;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < kBatchU; ++u) {
+              const int zu = z + u;
+              if (zu >= z1) break;
+              const float* row = col + (rz + u + R) * TXP;
+              float qx[2 * R + 1];
+              qx[R] = q[u + R];
+#pragma unroll
+              for (int j = 1; j <= R; ++j) {
+                qx[R + j] = row[j];
+                qx[R - j] = row[-j];
+              }
+              const float lap = laplacian_2d<R>(q + u, qx, cz, cx);
+              const int dz = layer_distance(zu, nz, nbz0, nbz1);
+              const int d2 = dz * dz + dx2;
+              float ca = 1.f, e = 0.f;
+              if (d2 != 0) {
+                const float2 c = __ldg(&damp[d2]);
+                ca = c.x;
+                e = c.y;
+              }
+              float pnew = leapfrog_update(q[u + R], po[u], kp[u], lap, ca, e);
+              if (xdir || (zu == 0 && bz0 == kBcDirichlet) || (zu == nz - 1 && bz1 == kBcDirichlet)) pnew = 0.f;
+              float* o = out + zu * sz;
+              o[0] = pnew;
+              if (xm_lo) o[-2 * x] = xs_lo * pnew;
+              if (xm_hi) o[2 * xr] = xs_hi * pnew;
+              if (zu <= R || zu >= nz - 1 - R) mirror_ghosts<R>(o, 0, zu, nz, sz, bz0, bz1, pnew);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * R; ++j) q[j] = q[j + kBatchU];
+      }
 #pragma unroll
       for (int u = 0; u < kBatchU; ++u) {
-        const int zu = z + u;
-        if (act && zu < z1) {
-          const float* row = col + (rz + u + R) * S::TXP;
-          float qx[2 * R + 1];
-          qx[R] = q[u + R];
-#pragma unroll
-          for (int j = 1; j <= R; ++j) {
-            qx[R + j] = row[j];
-            qx[R - j] = row[-j];
-          }
-          const float lap = laplacian_2d<R>(q + u, qx, cz, cx);
-          const int dz = layer_distance(zu, nz, nbz0, nbz1);
-          const int d2 = dz * dz + dx2;
-          float ca = 1.f, e = 0.f;
-          if (d2 != 0) {
-            const float2 c = __ldg(&damp[d2]);
-            ca = c.x;
-            e = c.y;
-          }
-          const int ro = (rz + u) * kBatchTX + tid;
-          float pnew = leapfrog_update(q[u + R], O[ro], K[ro], lap, ca, e);
-          if (xdir || (zu == 0 && bz0 == kBcDirichlet) || (zu == nz - 1 && bz1 == kBcDirichlet)) pnew = 0.f;
-          float* o = out + zu * sz;
-          o[0] = pnew;
-          if (xm_lo) o[-2 * x] = xs_lo * pnew;
-          if (xm_hi) o[2 * xr] = xs_hi * pnew;
-          if (zu <= R || zu >= nz - 1 - R) mirror_ghosts<R>(o, 0, zu, nz, sz, bz0, bz1, pnew);
-        }
+        po[u] = npo[u];
+        kp[u] = nkp[u];
       }
-#pragma unroll
-      for (int j = 0; j < 2 * R; ++j) q[j] = q[j + kBatchU];
     }
-    __syncthreads();  // the next item's copies overwrite the image
+    __syncthreads();  // the next item's copies overwrite the image; abort_s is settled
+    if (abort_s) break;
+    cur = nxt;
   }
+  // after a failed wait: let this CTA's own copies land (bounded) before it exits
+  if (abort_s && tid == 0)
+    for (int k = 0; k < 8; ++k)
+      if (pending & (1u << k)) mbar_wait_bounded(smem_addr(&bars[k]), (phases >> k) & 1u, limit_ns);
 }
 
 // Eq. 11 for every shot of the batch (blockIdx.y = shot), into p[n+1].
