@@ -139,20 +139,29 @@ __global__ void inject_taps_kernel(float* p, const int64_t* tap_off, const float
 __device__ __forceinline__ void sample_receiver(const float* p, const PointSet& rec, const FaceInfo& f, float* out,
                                                 int step, int r, int lane, bool dirichlet_zero) {
   const float* w = rec.w + int64_t(r) * 3 * rec.L;
-  const int z0 = rec.first[3 * r], y0 = rec.first[3 * r + 1], x0 = rec.first[3 * r + 2];
-  const int rows = rec.lz * rec.ly, rpp = 32 / rec.lx;
+  // only the window rows with a non-zero weight along z and y contribute (a
+  // receiver on a grid plane has a single one along that axis)
+  int za = 0, zb = rec.lz, ya = 0, yb = rec.ly;
+  while (za < zb - 1 && w[za] == 0.f) ++za;
+  while (zb - 1 > za && w[zb - 1] == 0.f) --zb;
+  while (ya < yb - 1 && w[rec.L + ya] == 0.f) ++ya;
+  while (yb - 1 > ya && w[rec.L + yb - 1] == 0.f) --yb;
+  const int z0 = rec.first[3 * r] + za, y0 = rec.first[3 * r + 1] + ya, x0 = rec.first[3 * r + 2];
+  const float* wz = w + za;
+  const float* wy = w + rec.L + ya;
+  const int ly = yb - ya, rows = (zb - za) * ly, rpp = 32 / rec.lx;
   const int ix = lane % rec.lx, rs = lane / rec.lx;
   float acc = 0.f;
   if (rs < rows && rs < rpp) {
     const int x = x0 + ix;
     const bool xd = dirichlet_zero && ((x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet));
     // window rows rs, rs + rpp, ... as (iz, iy), stepped without divisions
-    const int ly = rec.ly, dz = rpp / ly, dy = rpp - dz * ly;
+    const int lz = zb - za, dz = rpp / ly, dy = rpp - dz * ly;
     int iz = rs / ly, iy = rs - (rs / ly) * ly;
     const float* q = p + int64_t(z0) * f.sz + int64_t(y0) * f.sy + x;
     float s = 0.f;
 #pragma unroll 4
-    while (iz < rec.lz) {
+    while (iz < lz) {
       float v = q[int64_t(iz) * f.sz + int64_t(iy) * f.sy];
       if (dirichlet_zero) {
         const int z = z0 + iz, y = y0 + iy;
@@ -160,7 +169,7 @@ __device__ __forceinline__ void sample_receiver(const float* p, const PointSet& 
             (y == 0 && f.bc[2] == kBcDirichlet) || (y == f.ny - 1 && f.bc[3] == kBcDirichlet))
           v = 0.f;
       }
-      s = fmaf(w[iz] * w[rec.L + iy], v, s);
+      s = fmaf(wz[iz] * wy[iy], v, s);
       iz += dz;
       iy += dy;
       if (iy >= ly) {
