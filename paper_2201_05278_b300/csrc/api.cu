@@ -107,6 +107,7 @@ struct sw_grid {
   float* tap_coef = nullptr;
   int* rec_first = nullptr;
   float* rec_w = nullptr;
+  int4* rec_span = nullptr;  // per receiver: rows with non-zero weight along z and y
 
   // TMA tensor maps of the 3D pipelined stencil: p[n] with halo box and
   // interior box for each of the two wavefield buffers, kappa interior box
@@ -476,6 +477,7 @@ PointSet point_set(const sw_grid* g, bool src) {
   p.lz = g->lz;
   p.ly = g->ly;
   p.lx = g->lx;
+  p.span = src ? nullptr : g->rec_span;
   return p;
 }
 
@@ -489,6 +491,8 @@ void free_acquisition(sw_grid* g) {
   dev_free(g, g->src_w, size_t(g->n_src) * 3 * g->L * sizeof(float));
   dev_free(g, g->rec_first, size_t(g->n_rec) * 3 * sizeof(int));
   dev_free(g, g->rec_w, size_t(g->n_rec) * 3 * g->L * sizeof(float));
+  dev_free(g, g->rec_span, size_t(g->n_rec) * sizeof(int4));
+  g->rec_span = nullptr;
   dev_free(g, g->wavelet, size_t(g->n_src > 0 ? g->n_src : 1) * g->nt * sizeof(float));
   g->src_first = g->rec_first = nullptr;
   g->src_w = g->rec_w = g->wavelet = nullptr;
@@ -801,6 +805,23 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
     SW_TRY(dev_alloc(g, (void**)&g->rec_w, rwt.size() * sizeof(float)));
     SW_CUDA(cudaMemcpyAsync(g->rec_first, rf.data(), rf.size() * sizeof(int), cudaMemcpyHostToDevice, g->stream));
     SW_CUDA(cudaMemcpyAsync(g->rec_w, rwt.data(), rwt.size() * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    // rows of each window with a non-zero weight along z and y (the sampler reads only those)
+    std::vector<int4> span(static_cast<size_t>(n_rec));
+    for (int i = 0; i < n_rec; ++i) {
+      int lo[2], cnt[2];
+      const int len[2] = {g->lz, g->ly};
+      for (int k = 0; k < 2; ++k) {
+        const float* wk = rwt.data() + (size_t(i) * 3 + k) * g->L;
+        int a = 0, b = len[k];
+        while (a < b - 1 && wk[a] == 0.f) ++a;
+        while (b - 1 > a && wk[b - 1] == 0.f) --b;
+        lo[k] = a;
+        cnt[k] = b - a;
+      }
+      span[size_t(i)] = make_int4(lo[0], cnt[0], lo[1], cnt[1]);
+    }
+    SW_TRY(dev_alloc(g, (void**)&g->rec_span, span.size() * sizeof(int4)));
+    SW_CUDA(cudaMemcpyAsync(g->rec_span, span.data(), span.size() * sizeof(int4), cudaMemcpyHostToDevice, g->stream));
   }
   SW_CUDA(cudaStreamSynchronize(g->stream));
   g->has_acq = true;

@@ -19,6 +19,7 @@ struct PointSet {
   int count;
   int L;             // row length of w
   int lz, ly, lx;    // window lengths per axis
+  const int4* span;  // optional [count]: (first row, rows) along z and y with non-zero weight
 };
 
 struct FaceInfo {
@@ -141,22 +142,25 @@ __device__ __forceinline__ void sample_receiver(const float* p, const PointSet& 
   const float* w = rec.w + int64_t(r) * 3 * rec.L;
   // only the window rows with a non-zero weight along z and y contribute (a
   // receiver on a grid plane has a single one along that axis)
-  int za = 0, zb = rec.lz, ya = 0, yb = rec.ly;
-  while (za < zb - 1 && w[za] == 0.f) ++za;
-  while (zb - 1 > za && w[zb - 1] == 0.f) --zb;
-  while (ya < yb - 1 && w[rec.L + ya] == 0.f) ++ya;
-  while (yb - 1 > ya && w[rec.L + yb - 1] == 0.f) --yb;
+  int za = 0, lz = rec.lz, ya = 0, ly = rec.ly;
+  if (rec.span) {
+    const int4 sp = rec.span[r];
+    za = sp.x;
+    lz = sp.y;
+    ya = sp.z;
+    ly = sp.w;
+  }
   const int z0 = rec.first[3 * r] + za, y0 = rec.first[3 * r + 1] + ya, x0 = rec.first[3 * r + 2];
   const float* wz = w + za;
   const float* wy = w + rec.L + ya;
-  const int ly = yb - ya, rows = (zb - za) * ly, rpp = 32 / rec.lx;
+  const int rows = lz * ly, rpp = 32 / rec.lx;
   const int ix = lane % rec.lx, rs = lane / rec.lx;
   float acc = 0.f;
   if (rs < rows && rs < rpp) {
     const int x = x0 + ix;
     const bool xd = dirichlet_zero && ((x == 0 && f.bc[4] == kBcDirichlet) || (x == f.nx - 1 && f.bc[5] == kBcDirichlet));
     // window rows rs, rs + rpp, ... as (iz, iy), stepped without divisions
-    const int lz = zb - za, dz = rpp / ly, dy = rpp - dz * ly;
+    const int dz = rpp / ly, dy = rpp - dz * ly;
     int iz = rs / ly, iy = rs - (rs / ly) * ly;
     const float* q = p + int64_t(z0) * f.sz + int64_t(y0) * f.sy + x;
     float s = 0.f;
