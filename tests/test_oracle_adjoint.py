@@ -104,3 +104,107 @@ def test_gradient_matches_finite_differences(ndim):
     eps = 1e-3
     fd = (misfit(vel + eps * dv) - misfit(vel - eps * dv)) / (2 * eps)
     assert fd == pytest.approx(float(np.sum(g * dv)), rel=1e-6)
+
+
+# ---- variable density (Eq. 5 with the Eq. 10 term) --------------------------
+
+def _rho(shape, seed):
+    rng = np.random.default_rng(seed)
+    return 1500.0 + 1200.0 * rng.random(shape)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_numpy_forward_equals_oracle_c_variable_density(ndim):
+    shape, spacing, vel, dt, kw, wav, n = _case(ndim)
+    rho = _rho(shape, 1)
+    pb = A.make_problem(ndim, shape, spacing, 6, vel, dt, rho=rho, **kw)
+    states, seis = A.forward_states(pb, wav, n)
+    seis_c, p_c = oracle.forward(ndim, shape, spacing, 6, vel, dt, n, wavelet=np.asarray(wav), rho=rho, **kw)
+    assert np.abs(seis - seis_c).max() <= 1e-12 * np.abs(seis_c).max()
+    assert np.abs(states[-1] - p_c).max() <= 1e-12 * np.abs(p_c).max()
+
+
+@pytest.mark.parametrize("even", [False, True])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_first_derivative_transpose_is_the_matrix_transpose(ndim, even):
+    if ndim == 3:
+        shape, spacing, bc = (9, 10, 11), (7.0, 8.0, 9.0), BC3
+    else:
+        shape, spacing, bc = (11, 13), (7.0, 9.0), BC2
+    pb = A.make_problem(ndim, shape, spacing, 6, np.full(shape, 2000.0), 1e-3, bc=bc)
+    n = int(np.prod(shape))
+    for ax in range(ndim):
+        D = np.zeros((n, n))
+        DT = np.zeros((n, n))
+        for i in range(n):
+            e = np.zeros(n)
+            e[i] = 1.0
+            D[:, i] = A.first_deriv(e.reshape(shape), pb, ax, even).ravel()
+            DT[:, i] = A.first_deriv_t(e.reshape(shape), pb, ax, even).ravel()
+        assert np.abs(D.T - DT).max() <= 1e-15 * np.abs(D).max()
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_variable_density_operator_transpose(ndim):
+    if ndim == 3:
+        shape, spacing, bc = (9, 10, 11), (7.0, 8.0, 9.0), BC3
+    else:
+        shape, spacing, bc = (11, 13), (7.0, 9.0), BC2
+    pb = A.make_problem(ndim, shape, spacing, 6, np.full(shape, 2000.0), 1e-3, bc=bc, rho=_rho(shape, 2))
+    n = int(np.prod(shape))
+    M = np.zeros((n, n))
+    MT = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        M[:, i] = A.operator(e.reshape(shape), pb).ravel()
+        MT[:, i] = A.operator_t(e.reshape(shape), pb).ravel()
+    keep = np.ones(shape, bool)  # Dirichlet face nodes are held at zero on both sides
+    for ax in range(ndim):
+        for side, kind in enumerate(pb.bc[ax]):
+            if kind == oracle.BC_DIRICHLET:
+                idx = [slice(None)] * ndim
+                idx[ax] = 0 if side == 0 else shape[ax] - 1
+                keep[tuple(idx)] = False
+    k = keep.ravel()
+    assert np.abs(M.T[np.ix_(k, k)] - MT[np.ix_(k, k)]).max() <= 1e-14 * np.abs(M).max()
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_dot_product_variable_density(ndim):
+    shape, spacing, vel, dt, kw, _, n = _case(ndim, seed=5)
+    rho = _rho(shape, 3)
+    rng = np.random.default_rng(11)
+    s = rng.standard_normal(n)
+    r = rng.standard_normal((n, len(kw["rec_pos"])))
+    seis_c, _ = oracle.forward(ndim, shape, spacing, 6, vel, dt, n, wavelet=s, rho=rho, **kw)
+    pb = A.make_problem(ndim, shape, spacing, 6, vel, dt, rho=rho, **kw)
+    _, adj = A.backward(pb, r, n)
+    lhs = float(np.sum(seis_c * r))
+    rhs = float(np.sum(s * adj[0]))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1e-300)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_density_and_velocity_gradients_match_finite_differences(ndim):
+    shape, spacing, vel, dt, kw, wav, n = _case(ndim, seed=7)
+    rng = np.random.default_rng(3)
+    rho = _rho(shape, 4)
+    vel_true = vel * (1.0 + 0.02 * rng.standard_normal(shape))
+    rho_true = rho * (1.0 + 0.05 * rng.standard_normal(shape))
+    obs, _ = oracle.forward(ndim, shape, spacing, 6, vel_true, dt, n, wavelet=np.asarray(wav), rho=rho_true, **kw)
+    pb = A.make_problem(ndim, shape, spacing, 6, vel, dt, rho=rho, **kw)
+    J, g_c, g_rho, _ = A.adjoint_gradient_full(pb, wav, obs, n)
+    assert J > 0
+
+    def misfit(v, r):
+        d, _ = oracle.forward(ndim, shape, spacing, 6, v, dt, n, wavelet=np.asarray(wav), rho=r, **kw)
+        return 0.5 * float(np.sum((d - obs) ** 2))
+
+    dv = rng.standard_normal(shape)
+    eps = 1e-3
+    fd = (misfit(vel + eps * dv, rho) - misfit(vel - eps * dv, rho)) / (2 * eps)
+    assert fd == pytest.approx(float(np.sum(g_c * dv)), rel=1e-6)
+    dr = rng.standard_normal(shape)
+    fd = (misfit(vel, rho + eps * dr) - misfit(vel, rho - eps * dr)) / (2 * eps)
+    assert fd == pytest.approx(float(np.sum(g_rho * dr)), rel=1e-6)
