@@ -130,16 +130,17 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
 /*
  * Misfit gradient by the adjoint-state method.  The paper names full-waveform
  * inversion as the solver's use but prints no adjoint; this is the exact
- * discrete adjoint of the forward recurrence sw_forward runs (constant
- * density only).  sw_gradient runs the forward simulation of the current
- * model and acquisition for n_steps, the misfit
+ * discrete adjoint of the forward recurrence sw_forward runs, with or
+ * without density (Eq. 5, Eq. 10).  sw_gradient runs the forward simulation
+ * of the current model and acquisition for n_steps, the misfit
  *   J = 1/2 sum_n sum_r (d[n][r] - observed[n][r])^2
  * of its seismogram d against `observed`, and the adjoint sweep backwards in
- * time, and returns J and dJ/dc, the derivative with respect to the velocity
- * at every node.
+ * time, and returns J, dJ/dc (the derivative with respect to the velocity
+ * at every node) and, with a density model, dJ/drho.
  *   observed         [n_steps][n_rec] FP32, device or host (copied)
  *   misfit           host, one double
  *   grad_vel         [nz][ny][nx] FP32 (2D: [nz][nx]), device or host
+ *   grad_rho         same layout, or NULL; needs a density model
  *   checkpoint_every forward states kept every K time steps (0: K about
  *                    sqrt(2 n_steps)); each segment is recomputed during the
  *                    adjoint sweep.
@@ -151,17 +152,18 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  *                    carries that rounding.  Device memory for the call,
  *                    freed before it returns: (2 n_steps / K + K + 4) padded
  *                    FP32 wavefields (K + 4 with 16-bit checkpoints, plus
- *                    2 n_steps / K node arrays of 2 bytes per node) and three
- *                    [n_steps][n_rec] arrays.
- * Errors: SW_ESTATE before sw_set_model / sw_set_acquisition; SW_EINVAL with
- * a density model, without receivers, for n_steps < 1 or beyond the
- * wavelet, or with 2R+1 nodes or fewer along an axis; SW_ENOMEM when the
+ *                    2 n_steps / K node arrays of 2 bytes per node; 3 or 6
+ *                    more with density) and three [n_steps][n_rec] arrays.
+ * Errors: SW_ESTATE before sw_set_model / sw_set_acquisition; SW_EINVAL for
+ * grad_rho without a density model, without receivers, for n_steps < 1 or
+ * beyond the wavelet, or with 2R+1 nodes or fewer along an axis; SW_ENOMEM
+ * when the
  * buffers do not fit.  The grid's wavefields
  * hold the forward run's last two levels afterwards.
  */
 enum { SW_CKPT_FP32 = 0, SW_CKPT_BF16 = 1, SW_CKPT_FP16 = 2 };
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
-                      int checkpoint_every, int checkpoint_format);
+                      float* grad_rho, int checkpoint_every, int checkpoint_format);
 
 sw_status sw_get_dt(const sw_grid* g, double* dt);
 

@@ -131,12 +131,13 @@ SW_CKPT_FP32, SW_CKPT_BF16, SW_CKPT_FP16 = 0, 1, 2
 
 
 def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int = 0,
-                checkpoint_format: int = SW_CKPT_FP32) -> float:
-    """Misfit J = 1/2 |d - observed|^2 of a forward run and dJ/dvelocity into
-    grad_vel (adjoint-state method, constant density); returns J."""
+                checkpoint_format: int = SW_CKPT_FP32, grad_rho=None) -> float:
+    """Misfit J = 1/2 |d - observed|^2 of a forward run, dJ/dvelocity into
+    grad_vel and (density models) dJ/ddensity into grad_rho (adjoint-state
+    method); returns J."""
     j = ctypes.c_double()
     _check(_lib.load().sw_gradient(g.handle, int(n_steps), _ptr(observed), ctypes.byref(j), _ptr(grad_vel),
-                                   int(checkpoint_every), int(checkpoint_format)))
+                                   _ptr(grad_rho), int(checkpoint_every), int(checkpoint_format)))
     return j.value
 
 

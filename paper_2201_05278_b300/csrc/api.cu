@@ -399,8 +399,9 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cud
 // Variable density: four rows per thread in 4-warp CTAs with three bundles
 // (730 against 863 us per launch at order 16 on 512 x 512 x 384) up to
 // radius 8, two rows in 8-warp CTAs above.
-void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
-  if (g->has_density) {
+void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st,
+                             bool vd) {
+  if (vd) {
     switch (g->R) {
       case 1: launch_tma_t<1, 16, 4, 3, 1, true>(g, a, m, st); break;
       case 2: launch_tma_t<2, 16, 4, 3, 1, true>(g, a, m, st); break;
@@ -434,7 +435,7 @@ void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepM
 // The time loop's step: p[n] in u[buf], p[n-1] and p[n+1] in u[buf ^ 1].
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
   const StepMaps m{&g->map_halo[buf], &g->map_inner[buf], &g->map_inner[buf ^ 1]};
-  launch_stencil_tma_maps(g, a, m, st);
+  launch_stencil_tma_maps(g, a, m, st, g->has_density);
 }
 
 void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, const float* kappa, float* gk,
@@ -452,6 +453,26 @@ void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, 
     default: break;
   }
 #undef SW_IMAGE
+}
+
+void launch_image_vd(int R, int ndim, dim3 grid, const float* p, const float* psi, const float* kappa,
+                     float* const* gg, float* gk, float* const* ag, const FaceInfo& f, const LapCoef& lc,
+                     const VdWeights& w, cudaStream_t st) {
+#define SW_IMAGE_VD(RR)                                                                                            \
+  case RR:                                                                                                          \
+    if (ndim == 3)                                                                                                  \
+      image_vd_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, kappa, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f, \
+                                                   lc, w);                                                          \
+    else                                                                                                            \
+      image_vd_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, kappa, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f, \
+                                                   lc, w);                                                          \
+    break;
+  switch (R) {
+    SW_IMAGE_VD(1) SW_IMAGE_VD(2) SW_IMAGE_VD(3) SW_IMAGE_VD(4) SW_IMAGE_VD(5)
+    SW_IMAGE_VD(6) SW_IMAGE_VD(7) SW_IMAGE_VD(8) SW_IMAGE_VD(9) SW_IMAGE_VD(10)
+    default: break;
+  }
+#undef SW_IMAGE_VD
 }
 
 bool use_tma(const sw_grid* g) {
@@ -1013,12 +1034,12 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
 }
 
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
-                      int checkpoint_every, int checkpoint_format) {
+                      float* grad_rho, int checkpoint_every, int checkpoint_format) {
   g_last_error.clear();
   if (!g || !observed || !misfit || !grad_vel) return fail(SW_EINVAL, "NULL argument");
   if (!g->has_model) return fail(SW_ESTATE, "sw_gradient before sw_set_model");
   if (!g->has_acq) return fail(SW_ESTATE, "sw_gradient before sw_set_acquisition");
-  if (g->has_density) return fail(SW_EINVAL, "the gradient is built for constant density only");
+  if (grad_rho && !g->has_density) return fail(SW_EINVAL, "a density gradient needs a density model");
   if (g->n_force > 0 || g->init_p0 || g->init_pm1)
     return fail(SW_ESTATE, "the gradient assumes zero initial levels and no distributed forcing");
   if (g->n_rec <= 0) return fail(SW_EINVAL, "the gradient needs receivers");
@@ -1043,8 +1064,13 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // device memory of this call: checkpoint pairs (padded FP32 fields, or
   // 16-bit node arrays with their scales), segment states, psi, dJ/dkappa
   const bool packed = checkpoint_format != SW_CKPT_FP32;
+  const bool vd = g->has_density;
   const int nck = packed ? 0 : 2 * nseg;
-  const int nfields = nck + (K + 1) + 2 + 1;
+  // with density: dJ/dG_a accumulators, and G_a = D_a ln rho unless the
+  // pipelined kernel's copies exist
+  const bool own_g = vd && !g->glr[0];
+  const int nvd = vd ? 3 + (own_g ? 3 : 0) : 0;
+  const int nfields = nck + (K + 1) + 2 + 1 + nvd;
   const size_t pbytes = size_t(g->nodes()) * 2;  // one packed checkpoint
   void* packs = nullptr;
   unsigned* scales = nullptr;
@@ -1087,13 +1113,40 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   auto ck = [&](int sgm, int i) { return F[size_t(2 * sgm + i)]; };  // FP32: i = 0: p[k0-1], 1: p[k0]
   auto B = [&](int j) { return F[size_t(nck + j)]; };                 // p[k0 + j - 1]
   auto PSI = [&](int i) { return F[size_t(nck + K + 1 + i)]; };
-  float* GK = F[size_t(nfields - 1)];
+  float* GK = F[size_t(nck + K + 3)];
+  float* AG[3] = {nullptr, nullptr, nullptr};  // dJ/dG_a
+  float* GG[3] = {nullptr, nullptr, nullptr};  // G_a
+  VdWeights vw;
+  memset(&vw, 0, sizeof(vw));
+  if (vd) {
+    for (int i = 0; i < 3; ++i) {
+      AG[i] = g->at0(F[size_t(nck + K + 4 + i)]);
+      GG[i] = own_g ? g->at0(F[size_t(nck + K + 7 + i)]) : g->at0(g->glr[i]);
+    }
+    double wj[kMaxR + 1];
+    fd_first_weights(g->order, wj);
+    GradWeights gw;
+    for (int j = 0; j <= kMaxR; ++j) {
+      const bool in = j >= 1 && j <= g->R;
+      gw.z[j] = in ? wj[j] / (2.0 * g->h[0]) : 0.0;
+      gw.y[j] = in ? wj[j] / (2.0 * g->h[1]) : 0.0;
+      gw.x[j] = in ? wj[j] / (2.0 * g->h[2]) : 0.0;
+      vw.w[0][j] = float(gw.z[j]);
+      vw.w[1][j] = float(gw.y[j]);
+      vw.w[2][j] = float(gw.x[j]);
+    }
+    if (own_g) {
+      lnrho_gradient_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(g->lnrho), GG[0], GG[1], GG[2], f,
+                                                                          gw, g->R);
+      SW_CUDA(cudaGetLastError());
+    }
+  }
   std::vector<CUtensorMap> halo(static_cast<size_t>(nfields)), inner(static_cast<size_t>(nfields));
   if (tma) {
     int tx, ty;
     tma_tile(g->R, &tx, &ty);
     const uint32_t xh = uint32_t((g->R + 3) / 4 * 4);
-    for (int i = nck; i < nfields - 1; ++i) {  // segment states and psi
+    for (int i = nck; i < nck + K + 3; ++i) {  // segment states and psi
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &halo[size_t(i)]));
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &inner[size_t(i)]));
     }
@@ -1118,9 +1171,9 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     a.pnm1 = g->at0(pm);
     a.pout = g->at0(po);
     if (m)
-      launch_stencil_tma_maps(g, a, *m, st);
+      launch_stencil_tma_maps(g, a, *m, st, vd);
     else
-      launch_stencil(g->R, g->ndim, false, a, st);
+      launch_stencil(g->R, g->ndim, vd, a, st);
     const int taps = pts.count * pts.lz * pts.ly * pts.lx;
     if (taps > 0)
       inject_sources_kernel<<<(taps + 127) / 128, 128, 0, st>>>(a.pout, a.kappa, g->damp, pts, sig, sig_stride, n,
@@ -1195,22 +1248,26 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
       a.pn = g->at0(p1);
       a.pnm1 = g->at0(p2);
       a.pout = g->at0(p2);
+      // L^T psi: the constant-density stencil, then its Neumann-face correction
       if (tma)
-        launch_stencil_tma_maps(g, a, m, st);
+        launch_stencil_tma_maps(g, a, m, st, false);
       else
         launch_stencil(g->R, g->ndim, false, a, st);
       neumann_adjoint_kernel<<<dim3(unsigned((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]),
                                                        g->n[0] * g->n[1]) + 255) / 256), 3), 256, 0, st>>>(
           g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R);
+      if (vd)  // - sum_a D_a^T (G_a psi)
+        vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
+                                                                        g->damp, g->at0(p2), f, vw, g->R, g->ndim);
       const int rtaps = rec.count * rec.lz * rec.ly * rec.lx;
       inject_sources_kernel<<<(rtaps + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, res, N, k - 1,
                                                                  f, g->ndim, g->R);
       launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
       const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
-      if (g->ndim == 3)
-        launch_image(g->R, 3, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+      if (vd)
+        launch_image_vd(g->R, g->ndim, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, GG, g->at0(GK), AG, f, lc, vw, st);
       else
-        launch_image(g->R, 2, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+        launch_image(g->R, g->ndim, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
       if (src_threads > 0)
         image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->at0(GK), src,
                                                                         g->wavelet, g->sig_stride, k - 1, f);
@@ -1229,6 +1286,19 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   SW_CUDA(cudaGetLastError());
   if (host_out)
     SW_CUDA(cudaMemcpyAsync(grad_vel, out, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (grad_rho) {  // dJ/drho
+    float* ro = grad_rho;
+    const bool host_r = !is_device_pointer(grad_rho);
+    if (host_r) {
+      if (!g->staging2) SW_TRY(dev_alloc(g, (void**)&g->staging2, size_t(g->nodes()) * sizeof(float)));
+      ro = g->staging2;
+    }
+    gradient_density_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(AG[0], AG[1], AG[2], g->at0(g->lnrho), ro,
+                                                                           f, vw, g->R, g->ndim);
+    SW_CUDA(cudaGetLastError());
+    if (host_r)
+      SW_CUDA(cudaMemcpyAsync(grad_rho, ro, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
   SW_CUDA(cudaMemcpyAsync(misfit, macc, sizeof(double), cudaMemcpyDeviceToHost, st));
   SW_TRY(check_device_flag(g));
   return SW_OK;

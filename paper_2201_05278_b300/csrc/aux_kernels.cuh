@@ -580,6 +580,129 @@ __global__ void gradient_velocity_kernel(const float* gk, const float* kappa, fl
   }
 }
 
+// ---- variable-density gradient -------------------------------------------------
+//
+// With density the forward operator is L_rho p = L p - sum_a G_a D_a p
+// (G_a = D_a ln rho, Eq. 10), whose transpose is
+// L_rho^T q = L^T q - sum_a D_a^T (G_a q).  D_a^T is the transpose of "fill
+// the ghosts from the face conditions, then take the centred difference":
+// (D^T q)[m] = sum_j w_j/(2h) (q[m-j] - q[m+j]) with q zero off the nodes,
+// plus, for each ghost of a mirrored face, its share folded back onto the
+// node it mirrors (sign -1 on a Dirichlet face, +1 on a Neumann face or for
+// the even extension of ln rho).
+
+struct VdWeights {
+  float w[3][kMaxR + 1];  // w_j / (2h) per axis (z, y, x)
+};
+
+// (D^T q) at node m of an axis of n nodes; q(i) reads q at node i of the axis.
+template <typename Q>
+__device__ __forceinline__ float dt_axis(const Q& q, int m, int n, const float* wh, int R, float s_lo, float s_hi) {
+  float acc = 0.f;
+  for (int j = 1; j <= R; ++j) {
+    if (m - j >= 0) acc = fmaf(wh[j], q(m - j), acc);
+    if (m + j < n) acc = fmaf(-wh[j], q(m + j), acc);
+  }
+  if (s_lo != 0.f && m >= 1 && m <= R)  // ghost -m: gets -sum_{j>=m} w_j q[j-m]
+    for (int j = m; j <= R; ++j) acc = fmaf(-s_lo * wh[j], q(j - m), acc);
+  const int g = n - 1 - m;
+  if (s_hi != 0.f && g >= 1 && g <= R)  // ghost n-1+g: gets sum_{j>=g} w_j q[n-1+g-j]
+    for (int j = g; j <= R; ++j) acc = fmaf(s_hi * wh[j], q(n - 1 + g - j), acc);
+  return acc;
+}
+
+__device__ __forceinline__ float mirror_sign(int bc) {
+  return bc == kBcDirichlet ? -1.f : (bc == kBcNeumann ? 1.f : 0.f);
+}
+
+// The density part of one adjoint step: out += -a kappa sum_a D_a^T (G_a psi)
+// at every node (psi = psi[k+1], G_a = D_a ln rho in the padded layout).
+__global__ void vd_adjoint_kernel(const float* psi, const float* gz, const float* gy, const float* gx,
+                                  const float* kappa, const float2* damp, float* out, FaceInfo f, VdWeights W, int R,
+                                  int ndim) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    const int64_t bz = k - int64_t(z) * f.sz, bx = k - x;
+    float t = dt_axis([&](int j) { return gz[bz + j * f.sz] * psi[bz + j * f.sz]; }, z, f.nz, W.w[0], R,
+                      mirror_sign(f.bc[0]), mirror_sign(f.bc[1]));
+    t += dt_axis([&](int j) { return gx[bx + j] * psi[bx + j]; }, x, f.nx, W.w[2], R, mirror_sign(f.bc[4]),
+                 mirror_sign(f.bc[5]));
+    if (ndim == 3) {
+      const int64_t by = k - int64_t(y) * f.sy;
+      t += dt_axis([&](int j) { return gy[by + j * f.sy] * psi[by + j * f.sy]; }, y, f.ny, W.w[1], R,
+                   mirror_sign(f.bc[2]), mirror_sign(f.bc[3]));
+    }
+    const int dz = face_distance(z, f.nz, f.nbl[0], f.nbl[1]);
+    const int dy = ndim == 3 ? face_distance(y, f.ny, f.nbl[2], f.nbl[3]) : 0;
+    const int dx = face_distance(x, f.nx, f.nbl[4], f.nbl[5]);
+    const int d2 = dz * dz + dy * dy + dx * dx;
+    const float a = d2 ? damp[d2].x : 1.f;
+    out[k] -= a * kappa[k] * t;
+  }
+}
+
+// One term of dJ/dkappa and of dJ/dG_a with density: gk += psi L_rho p / kappa
+// and A_a -= psi D_a p (p's ghosts hold the face conditions).
+template <int R, int NDIM>
+__global__ void image_vd_kernel(const float* p, const float* psi, const float* kappa, const float* gz,
+                                const float* gy, const float* gx, float* gk, float* az, float* ay, float* ax,
+                                FaceInfo f, LapCoef lc, VdWeights W) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= f.nx) return;
+  const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+  const float ps = psi[k];
+  if (ps == 0.f) return;
+  const float pc = p[k], p2 = 2.f * pc;
+  float lap = 0.f, dz = 0.f, dy = 0.f, dx = 0.f;
+#pragma unroll
+  for (int j = 1; j <= R; ++j) {
+    const float zp = p[k + j * f.sz], zm = p[k - j * f.sz], xp = p[k + j], xm = p[k - j];
+    lap = fmaf(lc.c[0][j], (zp + zm) - p2, lap);
+    lap = fmaf(lc.c[2][j], (xp + xm) - p2, lap);
+    dz = fmaf(W.w[0][j], zp - zm, dz);
+    dx = fmaf(W.w[2][j], xp - xm, dx);
+    if constexpr (NDIM == 3) {
+      const float yp = p[k + j * f.sy], ym = p[k - j * f.sy];
+      lap = fmaf(lc.c[1][j], (yp + ym) - p2, lap);
+      dy = fmaf(W.w[1][j], yp - ym, dy);
+    }
+  }
+  float adv = fmaf(gz[k], dz, gx[k] * dx);
+  if constexpr (NDIM == 3) adv = fmaf(gy[k], dy, adv);
+  gk[k] += ps * (lap - adv) / kappa[k];
+  az[k] -= ps * dz;
+  ax[k] -= ps * dx;
+  if constexpr (NDIM == 3) ay[k] -= ps * dy;
+}
+
+// dJ/drho = (sum_a D_a^T A_a) / rho with the even extension of ln rho (A_a =
+// dJ/dG_a), densely per node.
+__global__ void gradient_density_kernel(const float* az, const float* ay, const float* ax, const float* lnrho,
+                                        float* out, FaceInfo f, VdWeights W, int R, int ndim) {
+  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(i % f.nx);
+    const int64_t zy = i / f.nx;
+    const int y = int(zy % f.ny);
+    const int z = int(zy / f.ny);
+    const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
+    const int64_t bz = k - int64_t(z) * f.sz, bx = k - x;
+    float t = dt_axis([&](int j) { return az[bz + j * f.sz]; }, z, f.nz, W.w[0], R, 1.f, 1.f);
+    t += dt_axis([&](int j) { return ax[bx + j]; }, x, f.nx, W.w[2], R, 1.f, 1.f);
+    if (ndim == 3) {
+      const int64_t by = k - int64_t(y) * f.sy;
+      t += dt_axis([&](int j) { return ay[by + j * f.sy]; }, y, f.ny, W.w[1], R, 1.f, 1.f);
+    }
+    out[i] = t / expf(lnrho[k]);
+  }
+}
+
 // ---- compressed checkpoints ---------------------------------------------------
 // A checkpointed wavefield is stored as its nodes only, in 16 bits, divided by
 // the field's largest magnitude (its per-snapshot scale); restoring

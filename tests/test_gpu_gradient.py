@@ -64,20 +64,55 @@ def test_gradient_does_not_depend_on_checkpoint_interval(cuda_device):
         assert rel_l2(gk, g0) <= 1e-6
 
 
-def test_gradient_rejects_what_it_does_not_cover(cuda_device):
-    import torch
-    w = small_case(3, 8, True, seed=2, n_steps=10)
+def test_density_gradient_needs_a_density_model(cuda_device):
+    w, wav, obs, _ = _setup(2, 8, 10, seed=2)
     g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
     try:
-        api.sw_set_model(g, torch.from_numpy(w.velocity), torch.from_numpy(w.density))
-        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, api.sw_ricker(w.f_peak, w.t0, w.dt, 10), window_radius=4)
-        obs = np.zeros((10, len(w.rec_pos)), np.float32)
-        grad = np.zeros(w.shape, np.float32)
+        api.sw_set_model(g, np.ascontiguousarray(w.velocity, np.float32))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
         with pytest.raises(api.SimwaveError) as e:
-            api.sw_gradient(g, 10, obs, grad)
+            api.sw_gradient(g, 10, obs, np.zeros(w.shape, np.float32), grad_rho=np.zeros(w.shape, np.float32))
         assert e.value.status == api.SW_EINVAL
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("ndim,order,variant", [(2, 8, None), (3, 8, api.SW_STENCIL_TMA),
+                                                (3, 8, api.SW_STENCIL_PLAIN), (3, 4, None)])
+def test_variable_density_gradients_match_oracle(cuda_device, ndim, order, variant):
+    """dJ/dc and dJ/drho of the density model against the FP64 oracle."""
+    import torch
+    n = 50
+    w = small_case(ndim, order, True, seed=60 + ndim + order, n_steps=n)
+    wav = np.asarray(oracle.ricker_samples(w.f_peak, w.dt, n, t0=w.t0), dtype=np.float32)
+    rng = np.random.default_rng(9)
+    v_true = w.velocity.astype(np.float64) * (1.0 + 0.03 * rng.standard_normal(w.shape))
+    r_true = w.density.astype(np.float64) * (1.0 + 0.05 * rng.standard_normal(w.shape))
+    kw = dict(src_pos=[tuple(p) for p in w.src_pos], rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc,
+              damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
+    obs, _ = oracle.forward(w.ndim, w.shape, w.spacing, w.order, v_true, w.dt, n, wavelet=wav.astype(np.float64),
+                            rho=r_true, **kw)
+    obs = obs.astype(np.float32)
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev), torch.from_numpy(w.density).to(dev))
+        if variant is not None:
+            api.sw_set_stencil_variant(g, variant)
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+        gr = np.zeros(w.shape, np.float32)  # host output
+        J = api.sw_gradient(g, n, torch.from_numpy(obs).to(dev), gv, 9, grad_rho=gr)
+        gv = gv.cpu().numpy()
+    finally:
+        g.close()
+    pb = A.make_problem(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
+                        rho=w.density.astype(np.float64), **kw)
+    J_ref, gv_ref, gr_ref, _ = A.adjoint_gradient_full(pb, wav.astype(np.float64), obs.astype(np.float64), n)
+    assert J == pytest.approx(J_ref, rel=1e-4)
+    assert np.abs(gr_ref).max() > 0
+    assert rel_l2(gv, gv_ref) <= GRAD_TOL
+    assert rel_l2(gr, gr_ref) <= GRAD_TOL
 
 
 def test_autograd_misfit_backward_gives_the_adjoint_gradient(cuda_device):
@@ -97,6 +132,36 @@ def test_autograd_misfit_backward_gives_the_adjoint_gradient(cuda_device):
         J_ref, g_ref, _ = A.adjoint_gradient(pb, wav.astype(np.float64), obs.astype(np.float64), n)
         assert float(J.detach()) == pytest.approx(J_ref, rel=1e-4)
         assert rel_l2(vel.grad.cpu().numpy(), 2.0 * g_ref) <= GRAD_TOL
+    finally:
+        g.close()
+
+
+def test_autograd_density_gradient(cuda_device):
+    import torch
+    from paper_2201_05278_b300 import autograd
+    n = 40
+    w = small_case(2, 8, True, seed=13, n_steps=n)
+    wav = np.asarray(oracle.ricker_samples(w.f_peak, w.dt, n, t0=w.t0), dtype=np.float32)
+    kw = dict(src_pos=[tuple(p) for p in w.src_pos], rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc,
+              damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
+    obs, _ = oracle.forward(w.ndim, w.shape, w.spacing, w.order, 1.02 * w.velocity.astype(np.float64), w.dt, n,
+                            wavelet=wav.astype(np.float64), rho=0.97 * w.density.astype(np.float64), **kw)
+    obs = obs.astype(np.float32)
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        vel = torch.from_numpy(w.velocity).to(dev).requires_grad_(True)
+        rho = torch.from_numpy(w.density).to(dev).requires_grad_(True)
+        api.sw_set_model(g, vel.detach(), rho.detach())
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        J = autograd.misfit(vel, g, torch.from_numpy(obs).to(dev), n, density=rho)
+        J.backward()
+        pb = A.make_problem(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
+                            rho=w.density.astype(np.float64), **kw)
+        J_ref, gv_ref, gr_ref, _ = A.adjoint_gradient_full(pb, wav.astype(np.float64), obs.astype(np.float64), n)
+        assert float(J.detach()) == pytest.approx(J_ref, rel=1e-4)
+        assert rel_l2(vel.grad.cpu().numpy(), gv_ref) <= GRAD_TOL
+        assert rel_l2(rho.grad.cpu().numpy(), gr_ref) <= GRAD_TOL
     finally:
         g.close()
 
