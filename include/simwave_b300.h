@@ -165,6 +165,23 @@ enum { SW_CKPT_FP32 = 0, SW_CKPT_BF16 = 1, SW_CKPT_FP16 = 2 };
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
                       float* grad_rho, int checkpoint_every, int checkpoint_format);
 
+/*
+ * Memory-capped schedule for sw_gradient: with max_states = s > 0 the adjoint
+ * sweep keeps at most s forward states (pairs of padded FP32 levels) besides
+ * two working levels and follows the binomial checkpointing schedule (the
+ * recursive form of Griewank's revolve): after a plain forward run for the
+ * residuals, steps (l, r] are reversed by storing the state at
+ * m = r - min(C(s - 1 + t, s - 1), r - l - 1), t the least count with
+ * C(s + t, s) >= r - l, reversing (m, r] with one slot fewer and then (l, m].
+ * Device memory: 2 s + 5 padded fields (+3 or 6 with density) instead of the
+ * uniform scheme's 2 n_steps / K + K + 4; the forward steps recomputed grow
+ * like n_steps times the least t.  The gradient is the same as with uniform
+ * checkpoints.  0 (the default) selects the uniform segments of
+ * checkpoint_every steps.  Needs checkpoint_format SW_CKPT_FP32 (SW_EINVAL
+ * from sw_gradient otherwise).  Errors: SW_EINVAL for a negative budget.
+ */
+sw_status sw_set_checkpoint_budget(sw_grid* g, int max_states);
+
 sw_status sw_get_dt(const sw_grid* g, double* dt);
 
 /*

@@ -30,6 +30,7 @@ SIGNATURES = {
     "sw_set_stencil_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_set_pipeline_test": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong]),
     "sw_set_saving": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    "sw_set_checkpoint_budget": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_set_forcing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "sw_set_initial_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sw_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),

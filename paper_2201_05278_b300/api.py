@@ -239,6 +239,11 @@ def sw_batch_get_profile(b: Batch):
     return ms.value, n1.value, n2.value
 
 
+def sw_set_checkpoint_budget(g: Grid, max_states: int) -> None:
+    """sw_gradient keeps at most max_states forward states (binomial schedule); 0: uniform segments."""
+    _check(_lib.load().sw_set_checkpoint_budget(g.handle, int(max_states)))
+
+
 def sw_get_dt(g: Grid) -> float:
     v = ctypes.c_double()
     _check(_lib.load().sw_get_dt(g.handle, ctypes.byref(v)))

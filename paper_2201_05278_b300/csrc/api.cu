@@ -112,6 +112,7 @@ struct sw_grid {
   // TMA tensor maps of the 3D pipelined stencil: p[n] with halo box and
   // interior box for each of the two wavefield buffers, kappa interior box
   int variant = SW_STENCIL_AUTO;
+  int ckpt_budget = 0;  // sw_gradient: 0 uniform checkpoints, else at most this many stored states (binomial)
   bool tma_ready = false;
   bool starve = false;                               // failure-path test: no tensor copies
   unsigned long long wait_limit_ns = 2000000000ull;  // bound of every mbarrier wait
@@ -1053,9 +1054,15 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     if ((g->ndim == 3 || ax != 1) && g->n[ax] <= 2 * int64_t(g->R) + 1)
       return fail(SW_EINVAL, "the gradient needs more than 2R+1 nodes along every axis");
   const int N = n_steps;
+  // binomial (revolve) schedule: at most `budget` stored states and two
+  // working levels; else uniform segments of K steps
+  const int budget = g->ckpt_budget;
+  const bool revolve = budget > 0;
+  if (revolve && checkpoint_format != SW_CKPT_FP32)
+    return fail(SW_EINVAL, "the binomial schedule keeps FP32 states");
   int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, int(std::lround(std::sqrt(2.0 * N))));
-  K = std::min(K, N);
-  const int nseg = (N + K - 1) / K;
+  K = revolve ? 1 : std::min(K, N);
+  const int nseg = revolve ? budget : (N + K - 1) / K;
   const FaceInfo f = g->faces();
   const size_t fbytes = size_t(g->lay.total) * sizeof(float);
   const bool tma = use_tma(g);
@@ -1189,7 +1196,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   for (int n = 0; n < N; ++n) {
     float* pn = g->u[n & 1];
     float* pm = g->u[(n + 1) & 1];
-    if (n % K == 0) {
+    if (!revolve && n % K == 0) {
       if (packed) {
         for (int i = 0; i < 2; ++i) {
           const int slot = 2 * (n / K) + i;
@@ -1217,61 +1224,132 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   SW_CUDA(cudaGetLastError());
 
   // backward: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
-  for (int sgm = nseg - 1; sgm >= 0; --sgm) {
-    const int k0 = sgm * K, k1 = std::min(N, k0 + K);
-    if (packed) {
-      for (int i = 0; i < 2; ++i) {
-        const int slot = 2 * sgm + i;
-        const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
-        if (checkpoint_format == SW_CKPT_BF16)
-          unpack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
-              reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, g->at0(B(i)));
-        else
-          unpack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
-              reinterpret_cast<const __half*>(src_p), scales + slot, f, g->at0(B(i)));
-        launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored level
+  // one adjoint step: psi[k] from psi[k+1], psi[k+2], then its imaging
+  // terms with the forward state p[k-1] (pk1, ghosts set)
+  auto adjoint_step = [&](int k, float* pk1) -> sw_status {
+    float* p1 = PSI((k + 1) & 1);  // psi[k+1]
+    float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
+    const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)]};
+    a.pn = g->at0(p1);
+    a.pnm1 = g->at0(p2);
+    a.pout = g->at0(p2);
+    // L^T psi: the constant-density stencil, then its Neumann-face correction
+    if (tma)
+      launch_stencil_tma_maps(g, a, m, st, false);
+    else
+      launch_stencil(g->R, g->ndim, false, a, st);
+    neumann_adjoint_kernel<<<dim3(unsigned((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]),
+                                                     g->n[0] * g->n[1]) + 255) / 256), 3), 256, 0, st>>>(
+        g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R);
+    if (vd)  // - sum_a D_a^T (G_a psi)
+      vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
+                                                                      g->damp, g->at0(p2), f, vw, g->R, g->ndim);
+    const int rtaps = rec.count * rec.lz * rec.ly * rec.lx;
+    inject_sources_kernel<<<(rtaps + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, res, N, k - 1, f,
+                                                               g->ndim, g->R);
+    launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
+    const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
+    if (vd)
+      launch_image_vd(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), a.kappa, GG, g->at0(GK), AG, f, lc, vw, st);
+    else
+      launch_image(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+    if (src_threads > 0)
+      image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->at0(GK), src,
+                                                                      g->wavelet, g->sig_stride, k - 1, f);
+    SW_CUDA(cudaGetLastError());
+    return SW_OK;
+  };
+
+  if (revolve) {
+    // Binomial checkpointing (the recursive form of Griewank's revolve):
+    // reverse steps (l, r] from the stored state (p[l-1], p[l]) in slot sl
+    // (-1: the zero state at level 0) with `fr` free slots.  With n = r - l
+    // steps and t the least repetition count with C(fr + t, fr) >= n, the
+    // state at m = r - min(C(fr - 1 + t, fr - 1), n - 1) is stored; (m, r]
+    // is reversed with one slot fewer, then (l, m] with the same slots.
+    // Without a free slot every step recomputes from l.  The two working
+    // levels are B(0) and B(1); each forward step overwrites the older.
+    auto binom = [](int s_, int t_) {
+      double b = 1.0;
+      for (int i = 1; i <= s_; ++i) b = b * double(t_ + i) / double(i);
+      return b;
+    };
+    int cur = 1;  // B(cur) holds the newest working level
+    auto load = [&](int sl) -> sw_status {
+      if (sl < 0) {
+        SW_CUDA(cudaMemsetAsync(B(0), 0, fbytes, st));
+        SW_CUDA(cudaMemsetAsync(B(1), 0, fbytes, st));
+      } else {
+        SW_CUDA(cudaMemcpyAsync(B(0), ck(sl, 0), fbytes, cudaMemcpyDeviceToDevice, st));
+        SW_CUDA(cudaMemcpyAsync(B(1), ck(sl, 1), fbytes, cudaMemcpyDeviceToDevice, st));
       }
-      SW_CUDA(cudaGetLastError());
-    } else {
-      SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
-      SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
-    }
-    for (int n = k0; n <= k1 - 2; ++n) {
-      const int j = n - k0 + 1;
-      const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))]};
-      SW_TRY(step(B(j), B(j - 1), B(j + 1), tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
-    }
-    for (int k = k1; k >= k0 + 1; --k) {
-      float* p1 = PSI((k + 1) & 1);  // psi[k+1]
-      float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
-      const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)]};
-      a.pn = g->at0(p1);
-      a.pnm1 = g->at0(p2);
-      a.pout = g->at0(p2);
-      // L^T psi: the constant-density stencil, then its Neumann-face correction
-      if (tma)
-        launch_stencil_tma_maps(g, a, m, st, false);
-      else
-        launch_stencil(g->R, g->ndim, false, a, st);
-      neumann_adjoint_kernel<<<dim3(unsigned((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]),
-                                                       g->n[0] * g->n[1]) + 255) / 256), 3), 256, 0, st>>>(
-          g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R);
-      if (vd)  // - sum_a D_a^T (G_a psi)
-        vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
-                                                                        g->damp, g->at0(p2), f, vw, g->R, g->ndim);
-      const int rtaps = rec.count * rec.lz * rec.ly * rec.lx;
-      inject_sources_kernel<<<(rtaps + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, res, N, k - 1,
-                                                                 f, g->ndim, g->R);
-      launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
-      const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
-      if (vd)
-        launch_image_vd(g->R, g->ndim, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, GG, g->at0(GK), AG, f, lc, vw, st);
-      else
-        launch_image(g->R, g->ndim, ig, g->at0(B(k - k0)), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
-      if (src_threads > 0)
-        image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->at0(GK), src,
-                                                                        g->wavelet, g->sig_stride, k - 1, f);
-      SW_CUDA(cudaGetLastError());
+      cur = 1;
+      return SW_OK;
+    };
+    auto advance = [&](int from, int to) -> sw_status {  // working levels from `from` to `to`
+      for (int n = from; n < to; ++n) {
+        float* pn = B(cur);
+        float* pm = B(cur ^ 1);
+        const StepMaps m{&halo[idx(pn)], &inner[idx(pn)], &inner[idx(pm)]};
+        SW_TRY(step(pn, pm, pm, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
+        cur ^= 1;
+      }
+      return SW_OK;
+    };
+    std::function<sw_status(int, int, int, int)> reverse = [&](int l, int r, int sl, int fr) -> sw_status {
+      const int n = r - l;
+      if (n <= 0) return SW_OK;
+      if (n == 1) {
+        SW_TRY(load(sl));
+        return adjoint_step(r, B(cur));
+      }
+      if (fr == 0) {
+        for (int k = r; k > l; --k) {
+          SW_TRY(load(sl));
+          SW_TRY(advance(l, k - 1));
+          SW_TRY(adjoint_step(k, B(cur)));
+        }
+        return SW_OK;
+      }
+      int t = 0;
+      while (binom(fr, t) < double(n)) ++t;
+      const int right = int(std::min(binom(fr - 1, t), double(n - 1)));
+      const int m = r - std::max(right, 1);
+      const int slot = budget - fr;  // slots are taken in stack order
+      SW_TRY(load(sl));
+      SW_TRY(advance(l, m));
+      SW_CUDA(cudaMemcpyAsync(ck(slot, 0), B(cur ^ 1), fbytes, cudaMemcpyDeviceToDevice, st));
+      SW_CUDA(cudaMemcpyAsync(ck(slot, 1), B(cur), fbytes, cudaMemcpyDeviceToDevice, st));
+      SW_TRY(reverse(m, r, slot, fr - 1));
+      return reverse(l, m, sl, fr);
+    };
+    SW_TRY(reverse(0, N, -1, budget));
+  } else {  // uniform: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
+    for (int sgm = nseg - 1; sgm >= 0; --sgm) {
+      const int k0 = sgm * K, k1 = std::min(N, k0 + K);
+      if (packed) {
+        for (int i = 0; i < 2; ++i) {
+          const int slot = 2 * sgm + i;
+          const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
+          if (checkpoint_format == SW_CKPT_BF16)
+            unpack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+                reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, g->at0(B(i)));
+          else
+            unpack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+                reinterpret_cast<const __half*>(src_p), scales + slot, f, g->at0(B(i)));
+          launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored level
+        }
+        SW_CUDA(cudaGetLastError());
+      } else {
+        SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
+        SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
+      }
+      for (int n = k0; n <= k1 - 2; ++n) {
+        const int j = n - k0 + 1;
+        const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))]};
+        SW_TRY(step(B(j), B(j - 1), B(j + 1), tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
+      }
+      for (int k = k1; k >= k0 + 1; --k) SW_TRY(adjoint_step(k, B(k - k0)));
     }
   }
 
@@ -1393,6 +1471,14 @@ sw_status sw_set_initial_state(sw_grid* g, const float* p0, const float* pm1) {
     SW_CUDA(cudaMemcpyAsync(*dst[i], src[i], bytes, cudaMemcpyDefault, g->stream));
   }
   SW_CUDA(cudaStreamSynchronize(g->stream));
+  return SW_OK;
+}
+
+sw_status sw_set_checkpoint_budget(sw_grid* g, int max_states) {
+  g_last_error.clear();
+  if (!g) return fail(SW_EINVAL, "NULL grid");
+  if (max_states < 0) return fail(SW_EINVAL, "negative checkpoint budget");
+  g->ckpt_budget = max_states;
   return SW_OK;
 }
 

@@ -183,3 +183,30 @@ def test_gradient_with_16_bit_checkpoints(cuda_device, fmt):
     print("checkpoint format %d: gradient rel-L2 error %.3e against the FP64 oracle" % (fmt, err))
     assert J == pytest.approx(J_ref, rel=1e-4)  # the forward pass itself is not rounded
     assert err <= CKPT_TOL[fmt]
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_binomial_checkpointing_gives_the_same_gradient(cuda_device, ndim):
+    """A memory budget of 1, 2 or 5 stored states (binomial schedule) gives the
+    uniform scheme's misfit and gradient; BF16 checkpoints are refused there."""
+    import torch
+    n = 37
+    w, wav, obs, _ = _setup(ndim, 8, n, seed=21)
+    J0, g0 = _gpu_gradient(w, wav, obs, n, 6)
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, torch.from_numpy(np.ascontiguousarray(w.velocity, np.float32)).to(dev))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        for budget in (1, 2, 5):
+            api.sw_set_checkpoint_budget(g, budget)
+            grad = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+            J = api.sw_gradient(g, n, torch.from_numpy(obs).to(dev), grad)
+            assert J == J0
+            assert rel_l2(grad.cpu().numpy(), g0) <= 1e-6
+        with pytest.raises(api.SimwaveError):
+            api.sw_gradient(g, n, torch.from_numpy(obs).to(dev), grad, 0, api.SW_CKPT_BF16)
+        with pytest.raises(api.SimwaveError):
+            api.sw_set_checkpoint_budget(g, -1)
+    finally:
+        g.close()
