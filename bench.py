@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--time-steps", type=int, default=0,
                     help="override the workload's time steps per forward (profiling runs only)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="forwards timed end to end (0 skips)")
+    ap.add_argument("--shape", default="",
+                    help="override the workload's grid as nz,ny,nx (profiling runs on a smaller case only)")
     args = ap.parse_args()
     world, rank, local = _dist()
 
@@ -339,7 +341,8 @@ def main():
             dist.destroy_process_group()
         return
 
-    w = workloads.make(args.workload, n_steps=args.time_steps or None)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    w = workloads.make(args.workload, n_steps=args.time_steps or None, shape=shape)
     vd = w.density is not None
     stream = torch.cuda.current_stream(dev)
     g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
