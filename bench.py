@@ -291,6 +291,150 @@ def run_batch(args, world, rank, local, dev):
         print(json.dumps(line))
 
 
+def gradient_cpu_baseline(budget_s=15.0):
+    """The FP64 adjoint oracle (numpy) on the 3d_fwi_gradient_256 recipe at
+    96^3 (64 receivers; the oracle forms one dense field per receiver, so the
+    full grid's 4096 would not fit) for a bounded number of time steps:
+    forward states, residual, adjoint sweep, imaging."""
+    from paper_2201_05278_b300 import workloads
+    import oracle
+    from oracle import adjoint as A
+    c = workloads.fwi_gradient_256(shape=(96, 96, 96))
+    w = c.base
+    kw = dict(src_pos=[tuple(c.shots[0])], rec_pos=[tuple(q) for q in w.rec_pos], nbl=w.nbl, bc=w.bc,
+              damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
+
+    def run(steps):
+        wav = oracle.ricker_samples(w.f_peak, w.dt, steps, t0=w.t0)
+        t = time.perf_counter()
+        pb = A.make_problem(3, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, **kw)
+        obs = np.zeros((steps, len(w.rec_pos)))
+        A.adjoint_gradient(pb, wav, obs, steps)
+        return time.perf_counter() - t
+
+    t1 = run(2) / 2.0
+    steps = int(max(2, min(60, budget_s / max(t1, 1e-3))))
+    t = run(steps)
+    return {"value": round(w.nodes * steps / t / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "3d_fwi_gradient_256 recipe on a 96^3 grid with 64 receivers, %d time steps (forward "
+                      "states, adjoint sweep, imaging), FP64 numpy" % steps}, t
+
+
+def run_gradient(args, world, rank, local, dev):
+    """Misfit gradients of 3d_fwi_gradient_256: a bench step is one shot's
+    sw_gradient (forward with BF16 checkpoints every 10 steps, residual,
+    adjoint sweep with recomputation and imaging), the shots taken in turn;
+    Gpts/s counts the forward's grid-point updates per second of gradient."""
+    import torch
+    from paper_2201_05278_b300 import api, workloads
+
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    c = workloads.fwi_gradient_256(n_steps=args.time_steps or None, shape=shape)
+    w = c.base
+    N = w.n_steps
+    stream = torch.cuda.current_stream(dev)
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
+                           stream=stream)
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, N)
+    n_rec = len(w.rec_pos)
+    n_shots = len(c.shots)
+    used = [i % n_shots for i in range(args.warmup + args.steps + max(args.e2e_steps, 0))]
+
+    def shot(i):
+        api.sw_set_acquisition(g, c.shots[i:i + 1], w.rec_pos, wav, window_radius=w.window_radius)
+
+    # observed data from the true model (FP32 forward on the GPU), before timing
+    api.sw_set_model(g, torch.from_numpy(c.v_true).to(dev))
+    obs = {}
+    for i in sorted(set(used)):
+        shot(i)
+        obs[i] = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
+        api.sw_forward(g, N, obs[i], None)
+    api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+    # the forward stencil's launch time on this grid, for the roofline line
+    shot(used[0])
+    api.sw_set_profiling(g, PROFILE_EVERY)
+    tmp = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
+    api.sw_forward(g, N, tmp, None)
+    st_ms, st_n, _ = api.sw_get_profile(g)
+    api.sw_set_profiling(g, 0)
+    grad = torch.empty(w.shape, dtype=torch.float32, device=dev)
+
+    def one(k):
+        shot(used[k])
+        return api.sw_gradient(g, N, obs[used[k]], grad, c.checkpoint_every, api.SW_CKPT_BF16)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for k in range(args.warmup):
+        one(k)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kernels = 0
+    start.record(stream)
+    for k in range(args.warmup, args.warmup + args.steps):
+        one(k)
+        kernels += api.sw_get_profile(g)[2]
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = job_seconds(start.elapsed_time(stop) * 1e-3, world, dev) * 1e3
+    value = job_throughput(w.nodes * N, args.steps, world, elapsed_ms * 1e-3)
+
+    # e2e: observed data from pinned host memory, the gradient back to it
+    e2e = None
+    if args.e2e_steps > 0:
+        grad_h = torch.empty(w.shape, dtype=torch.float32).pin_memory()
+        obs_h = {i: obs[i].cpu().pin_memory() for i in set(used)}
+        barrier()
+        t0 = time.perf_counter()
+        base = args.warmup + args.steps
+        for k in range(base, base + args.e2e_steps):
+            shot(used[k])
+            api.sw_gradient(g, N, obs_h[used[k]], grad_h, c.checkpoint_every, api.SW_CKPT_BF16)
+            _ = float(grad_h[0, 0, 0])
+        barrier()
+        e2e_s = job_seconds(time.perf_counter() - t0, world, dev)
+        e2e = {"value": round(job_throughput(w.nodes * N, args.e2e_steps, world, e2e_s), 3), "unit": UNIT,
+               "h2d_bytes_per_step": N * n_rec * 4, "d2h_bytes_per_step": w.nodes * 4}
+    g.close()
+
+    peak, peak_kind = _peaks()
+    alg_bytes = BYTES_PER_UPDATE[False] * w.nodes
+    achieved = alg_bytes / (st_ms * 1e-3 / max(st_n, 1)) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": list(w.shape), "space_order": w.order,
+                       "time_steps": N, "shots": n_shots, "receivers": n_rec,
+                       "checkpoints": "BF16 pairs with per-snapshot scale every %d steps" % c.checkpoint_every,
+                       "quantity": "forward grid-point updates per second of gradient computation (forward, "
+                                   "residual, adjoint sweep with recomputation, imaging)",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "forward stencil of the same grid (CUDA events around every %dth launch of a "
+                                   "profiled sw_forward just before the timed region, %d launches)" % (
+                                       PROFILE_EVERY, st_n),
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+            "e2e": e2e,
+            "gpu_launches": int(kernels),
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cb, _ = gradient_cpu_baseline()
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,6 +481,11 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     if args.workload in workloads.BATCH_NAMES:
         run_batch(args, world, rank, local, dev)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload in workloads.GRADIENT_NAMES:
+        run_gradient(args, world, rank, local, dev)
         if world > 1:
             dist.destroy_process_group()
         return

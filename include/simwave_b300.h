@@ -296,7 +296,8 @@ sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_l
  * (N = 1: all of them; a sample keeps the events' own cost out of the run);
  * every = 0 turns timing off.  sw_get_profile returns, for the last
  * sw_forward, the summed time of the timed stencil launches, how many were
- * timed, and the number of kernels it launched in total.
+ * timed, and the number of kernels it launched in total (after sw_gradient:
+ * no timed launches, and the kernels that call launched).
  */
 sw_status sw_set_profiling(sw_grid* g, int every);
 sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_launches,

@@ -1171,9 +1171,11 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     lc.c[1][j] = a.cy[j];
     lc.c[2][j] = a.cx[j];
   }
+  int64_t nk = 0;  // kernels launched by this call
   // one step p[n] (pn), p[n-1] (pm) -> p[n+1] (po), with sources at step n
   auto step = [&](float* pn, float* pm, float* po, const StepMaps* m, int n, const float* sig, int sig_stride,
                   const PointSet& pts, const PointSet& recs, float* seis) -> sw_status {
+    nk += 2 + (pts.count > 0);
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pm);
     a.pout = g->at0(po);
@@ -1227,6 +1229,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // one adjoint step: psi[k] from psi[k+1], psi[k+2], then its imaging
   // terms with the forward state p[k-1] (pk1, ghosts set)
   auto adjoint_step = [&](int k, float* pk1) -> sw_status {
+    nk += 5 + (vd ? 1 : 0) + (src_threads > 0);
     float* p1 = PSI((k + 1) & 1);  // psi[k+1]
     float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
     const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)]};
@@ -1379,6 +1382,11 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   }
   SW_CUDA(cudaMemcpyAsync(misfit, macc, sizeof(double), cudaMemcpyDeviceToHost, st));
   SW_TRY(check_device_flag(g));
+  // + residual and velocity gradient, density gradient, ln rho gradients,
+  // and per 16-bit checkpoint segment absmax + pack and unpack + faces of two levels
+  g->kernel_launches = nk + 2 + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) + (packed ? 8 * int64_t(nseg) : 0);
+  g->stencil_launches = 0;
+  g->stencil_ms = 0.0;
   return SW_OK;
 }
 

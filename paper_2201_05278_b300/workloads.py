@@ -31,6 +31,12 @@ available, so synthetic layered models of the same kind stand in for them:
                        shot 2 cells deep across the surface; order 8, 10 Hz,
                        40-cell layer, 2000 steps (shot_batch())
 
+  3d_fwi_gradient_256  misfit-gradient workload: 256^3, background 2500 m/s,
+                       true model with a +10% Gaussian anomaly (sigma 25
+                       cells), 16 shots on a 4 x 4 surface grid, 1500 steps,
+                       10 Hz, BF16 checkpoints every 10 steps
+                       (fwi_gradient_256())
+
 Every model has no absorbing layer on the top face, which is null Neumann
 (as in the paper's listings); the other faces are null Dirichlet behind the
 layer.  dt = 0.4 h / c_max (Courant number 0.4).  The damping alpha follows a
@@ -210,5 +216,46 @@ def shot_batch(n_models: int = 8, shots_per_model: int = 8, n_steps: Optional[in
     return out
 
 
+@dataclass
+class GradientCase:
+    """A misfit-gradient workload: true and initial models, one source per shot."""
+    base: Workload          # grid, initial (background) model, receivers, wavelet parameters
+    v_true: np.ndarray
+    shots: np.ndarray       # [n_shots][3] source positions
+    checkpoint_every: int
+
+
+def fwi_gradient_256(n_steps: Optional[int] = None, shape: Optional[Tuple[int, ...]] = None) -> GradientCase:
+    """3d_fwi_gradient_256: 256^3, h = 10 m, background 2500 m/s, true model
+    with a centred Gaussian anomaly of +10% (sigma 25 cells), constant
+    density; 16 shots on a 4 x 4 grid 2 cells deep, 64 x 64 receivers 2 cells
+    deep; order 8, 10 Hz Ricker, 1500 steps, checkpoints every 10 steps;
+    40-cell absorbing layer, top face null Neumann."""
+    shp = tuple(shape) if shape else (256, 256, 256)
+    h = (10.0, 10.0, 10.0)
+    nb = min(40, max(4, shp[1] // 6))
+    nbl = [0, nb, nb, nb, nb, nb]
+    v0 = 2500.0
+    zz, yy, xx = np.meshgrid(*[np.arange(n, dtype=np.float64) - (n - 1) / 2.0 for n in shp], indexing="ij")
+    bump = np.exp(-(zz ** 2 + yy ** 2 + xx ** 2) / (2.0 * 25.0 ** 2))
+    v_true = (v0 * (1.0 + 0.1 * bump)).astype(np.float32)
+    v_init = np.full(shp, v0, dtype=np.float32)
+    c_max = float(v_true.max())
+    dt = 0.4 * h[0] / c_max
+    f = 10.0
+    py = (shp[1] - 2 * nb - 1) * h[1]
+    px = (shp[2] - 2 * nb - 1) * h[2]
+    sy, sx = np.meshgrid(_grid_positions(0.125 * py, 0.875 * py, 4), _grid_positions(0.125 * px, 0.875 * px, 4),
+                         indexing="ij")
+    shots = np.stack([np.full(16, 2 * h[0]), sy.ravel(), sx.ravel()], 1)
+    ny_r = nx_r = 64 if shp[1] >= 128 else 8
+    ry, rx = np.meshgrid(_grid_positions(0.0, py, ny_r), _grid_positions(0.0, px, nx_r), indexing="ij")
+    rec = np.stack([np.full(ry.size, 2 * h[0]), ry.ravel(), rx.ravel()], 1)
+    base = Workload("3d_fwi_gradient_256", 3, shp, h, 8, nbl, ["null_neumann"] + ["null_dirichlet"] * 5,
+                    _alpha(c_max, nb, h[0]), 3, dt, n_steps or 1500, f, 1.0 / f, shots[:1], rec, 4, v_init)
+    return GradientCase(base, v_true, shots, 10)
+
+
 NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384"]
+GRADIENT_NAMES = ["3d_fwi_gradient_256"]
 BATCH_NAMES = ["2d_shot_batch_64"]
