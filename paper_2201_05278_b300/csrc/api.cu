@@ -952,6 +952,10 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       // follow, with the receiver samples in the same launch
       launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st);
       ++launches;
+    } else if (g->n_rec > 0 && g->ndim == 2) {
+      sample_receivers_grouped_kernel<<<(grouped_receiver_warps(rec) + 3) / 4, 128, 0, st>>>(a.pout, rec, f,
+                                                                                            seis_dev, step);
+      ++launches;
     } else if (g->n_rec > 0) {
       sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pout, rec, f, seis_dev, step);
       ++launches;
@@ -1873,7 +1877,7 @@ struct sw_batch {
   BatchGroup* d_groups = nullptr;
   BatchShot* d_shots = nullptr;
   int n_groups = 0, total_items = 0, blocks = 0, R = 0;
-  int max_src_taps = 0, max_rec = 0;
+  int max_src_taps = 0, max_rec = 0, max_rec_warps = 0;
   int smem = 0;  // dynamic shared memory of the batched stencil
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -2048,6 +2052,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
       b->shots.push_back(S);
       b->max_src_taps = std::max(b->max_src_taps, s->n_src * s->lz * s->ly * s->lx);
       b->max_rec = std::max(b->max_rec, s->n_rec);
+      b->max_rec_warps = std::max(b->max_rec_warps, grouped_receiver_warps(S.rec));
       b->nodes_per_step += s->nodes();
     }
     groups.push_back(G);
@@ -2186,7 +2191,8 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
         ++launches;
       }
       if (b->max_rec > 0 && n_steps > 0) {
-        batch_receivers_kernel<<<dim3((b->max_rec + 3) / 4, n_shots), 128, 0, s>>>(b->d_shots, step, parity);
+        batch_receivers_kernel<<<dim3(unsigned((b->max_rec_warps + 3) / 4), n_shots), 128, 0, s>>>(b->d_shots, step,
+                                                                                                   parity);
         ++launches;
       }
     }

@@ -188,6 +188,48 @@ __device__ __forceinline__ void sample_receiver(const float* p, const PointSet& 
   if (lane == 0) out[int64_t(step) * rec.count + r] = acc;
 }
 
+// Eq. 12 with several receivers per warp, for windows of at most 32 columns
+// (lx): a group of G lanes (lx rounded up to a power of two) per receiver,
+// lane i of the group on window column i, the window rows (those with a
+// non-zero weight along z and y) summed in turn, then the group's lanes
+// reduced.  2D grids use it on both the single-grid and the batched path.
+__device__ __forceinline__ void sample_receivers_grouped(const float* p, const PointSet& rec, const FaceInfo& f,
+                                                         float* out, int step, int warp, int lane) {
+  const int G = rec.lx <= 8 ? 8 : (rec.lx <= 16 ? 16 : 32);
+  const int r = warp * (32 / G) + lane / G;
+  const int ix = lane % G;
+  float acc = 0.f;
+  if (r < rec.count && ix < rec.lx) {
+    const float* w = rec.w + int64_t(r) * 3 * rec.L;
+    int za = 0, lz = rec.lz, ya = 0, ly = rec.ly;
+    if (rec.span) {
+      const int4 sp = rec.span[r];
+      za = sp.x;
+      lz = sp.y;
+      ya = sp.z;
+      ly = sp.w;
+    }
+    const float* q = p + int64_t(rec.first[3 * r] + za) * f.sz + int64_t(rec.first[3 * r + 1] + ya) * f.sy +
+                     (rec.first[3 * r + 2] + ix);
+    float s = 0.f;
+    for (int iz = 0; iz < lz; ++iz)
+      for (int iy = 0; iy < ly; ++iy)
+        s = fmaf(w[za + iz] * w[rec.L + ya + iy], q[int64_t(iz) * f.sz + int64_t(iy) * f.sy], s);
+    acc = w[2 * rec.L + ix] * s;
+  }
+  for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (r < rec.count && ix == 0) out[int64_t(step) * rec.count + r] = acc;
+}
+
+__global__ void sample_receivers_grouped_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
+  sample_receivers_grouped(p, rec, f, out, step, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+}
+
+__host__ __device__ inline int grouped_receiver_warps(const PointSet& rec) {
+  const int per = rec.lx <= 8 ? 4 : (rec.lx <= 16 ? 2 : 1);
+  return (rec.count + per - 1) / per;
+}
+
 __global__ void sample_receivers_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= rec.count) return;

@@ -308,12 +308,13 @@ __global__ void batch_inject_kernel(const BatchShot* __restrict__ shots, int ste
                     blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// Eq. 12 for every shot of the batch (blockIdx.y = shot): one warp per receiver.
+// Eq. 12 for every shot of the batch (blockIdx.y = shot), several receivers
+// per warp (sample_receivers_grouped, as the single-grid 2D path).
 __global__ void batch_receivers_kernel(const BatchShot* __restrict__ shots, int step, int parity) {
   const BatchShot& S = shots[blockIdx.y];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= S.rec.count || !S.seis) return;
-  sample_receiver(S.u[parity ^ 1], S.rec, S.f, S.seis, step, warp, threadIdx.x & 31, false);
+  if (warp >= grouped_receiver_warps(S.rec) || !S.seis) return;  // whole warps leave together
+  sample_receivers_grouped(S.u[parity ^ 1], S.rec, S.f, S.seis, step, warp, threadIdx.x & 31);
 }
 
 }  // namespace sw
