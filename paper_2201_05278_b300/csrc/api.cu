@@ -257,7 +257,7 @@ void launch_stencil_t(StencilArgs a, cudaStream_t st) {
     stencil_plain_kernel<R, 3, VD, TX, TY, PPT><<<grid, TX * (TY / PPT), 0, st>>>(a);
   } else {
     const dim3 grid((a.nx + 127) / 128, std::min(a.nz, 65535));  // one thread per node
-    stencil_2d_kernel<R, VD><<<grid, 128, 0, st>>>(a);
+    launch_dependent(stencil_2d_kernel<R, VD>, grid, dim3(128), 0, st, a);  // waits for the previous step
   }
 }
 
@@ -936,6 +936,11 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
                        (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
                        (const float*)g->wavelet, g->sig_stride, step);
       ++launches;
+    } else if (src_threads > 0 && g->ndim == 2) {
+      launch_dependent(inject_sources_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pout,
+                       (const float*)a.kappa, (const float2*)g->damp, src, (const float*)g->wavelet, g->sig_stride,
+                       step, f, g->ndim, g->R);
+      ++launches;
     } else if (src_threads > 0) {
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
           a.pout, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
@@ -953,8 +958,8 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st);
       ++launches;
     } else if (g->n_rec > 0 && g->ndim == 2) {
-      sample_receivers_grouped_kernel<<<(grouped_receiver_warps(rec) + 3) / 4, 128, 0, st>>>(a.pout, rec, f,
-                                                                                            seis_dev, step);
+      launch_dependent(sample_receivers_grouped_kernel, dim3((grouped_receiver_warps(rec) + 3) / 4), dim3(128), 0,
+                       st, (const float*)a.pout, rec, f, seis_dev, step);
       ++launches;
     } else if (g->n_rec > 0) {
       sample_receivers_kernel<<<(g->n_rec + 3) / 4, 128, 0, st>>>(a.pout, rec, f, seis_dev, step);

@@ -84,6 +84,8 @@ __device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, 
 __global__ void inject_sources_kernel(float* p, const float* kappa, const float2* damp, PointSet src,
                                       const float* sig, int sig_stride, int step, FaceInfo f, int ndim,
                                       int R) {
+  griddep_launch_dependents();
+  griddep_wait();  // p[n+1] of the stencil launched before (when launched as its dependent)
   inject_source_tap(p, kappa, damp, src, sig, sig_stride, step, f, ndim, R, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -222,6 +224,8 @@ __device__ __forceinline__ void sample_receivers_grouped(const float* p, const P
 }
 
 __global__ void sample_receivers_grouped_kernel(const float* p, PointSet rec, FaceInfo f, float* out, int step) {
+  griddep_launch_dependents();
+  griddep_wait();  // the level it samples (when launched as a dependent)
   sample_receivers_grouped(p, rec, f, out, step, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 

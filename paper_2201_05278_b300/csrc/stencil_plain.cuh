@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "layout.h"
+#include "tma.cuh"
 
 namespace sw {
 
@@ -280,6 +281,10 @@ __device__ __forceinline__ void stencil_2d_node(const StencilArgs& a, int z, int
 
 template <int R, bool VD>
 __global__ void __launch_bounds__(128) stencil_2d_kernel(const StencilArgs a) {
+  // may be launched as a programmatic dependent of the previous step's last
+  // kernel: wait for it before touching the fields
+  griddep_launch_dependents();
+  griddep_wait();
   const int x = blockIdx.x * 128 + threadIdx.x;
   if (x >= a.nx) return;
   for (int z = blockIdx.y; z < a.nz; z += gridDim.y) stencil_2d_node<R, VD>(a, z, x);
