@@ -108,6 +108,7 @@ struct sw_grid {
   int* rec_first = nullptr;
   float* rec_w = nullptr;
   int4* rec_span = nullptr;  // per receiver: rows with non-zero weight along z and y
+  int rec_rows_max = 0;       // the largest such row count
 
   // TMA tensor maps of the 3D pipelined stencil: p[n] with halo box and
   // interior box for each of the two wavefield buffers, kappa interior box
@@ -515,6 +516,7 @@ void free_acquisition(sw_grid* g) {
   dev_free(g, g->rec_w, size_t(g->n_rec) * 3 * g->L * sizeof(float));
   dev_free(g, g->rec_span, size_t(g->n_rec) * sizeof(int4));
   g->rec_span = nullptr;
+  g->rec_rows_max = 0;
   dev_free(g, g->wavelet, size_t(g->n_src > 0 ? g->n_src : 1) * g->nt * sizeof(float));
   g->src_first = g->rec_first = nullptr;
   g->src_w = g->rec_w = g->wavelet = nullptr;
@@ -841,6 +843,7 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
         cnt[k] = b - a;
       }
       span[size_t(i)] = make_int4(lo[0], cnt[0], lo[1], cnt[1]);
+      g->rec_rows_max = std::max(g->rec_rows_max, cnt[0] * cnt[1]);
     }
     SW_TRY(dev_alloc(g, (void**)&g->rec_span, span.size() * sizeof(int4)));
     SW_CUDA(cudaMemcpyAsync(g->rec_span, span.data(), span.size() * sizeof(int4), cudaMemcpyHostToDevice, g->stream));
@@ -1256,9 +1259,10 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     if (vd)  // - sum_a D_a^T (G_a psi)
       vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
                                                                       g->damp, g->at0(p2), f, vw, g->R, g->ndim);
-    const int rtaps = rec.count * rec.lz * rec.ly * rec.lx;
-    inject_sources_kernel<<<(rtaps + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, res, N, k - 1, f,
-                                                               g->ndim, g->R);
+    // the residuals into psi through the receiver windows (rows with non-zero weight only)
+    const int rthreads = rec.count * g->rec_rows_max * rec.lx;
+    inject_rows_kernel<<<(rthreads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, g->rec_rows_max,
+                                                               res, N, k - 1, f, g->ndim, g->R);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
     const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
     if (vd)

@@ -46,17 +46,9 @@ __device__ __forceinline__ void add_with_mirrors(float* p, int64_t idx, int i, i
 // of every source (1/prod(h) is folded into the x weights).  The ghost images
 // of nodes near mirrored faces get the same increment (with the face's sign),
 // so the ghost layer stays consistent with p[n+1].  Dirichlet face nodes stay 0.
-__device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, const float2* damp,
-                                                  const PointSet& src, const float* sig, int sig_stride, int step,
-                                                  const FaceInfo& f, int ndim, int R, int t) {
-  const int taps = src.lz * src.ly * src.lx;
-  if (t >= src.count * taps) return;
-  const int s = t / taps;
-  int rem = t % taps;
-  const int ix = rem % src.lx;
-  rem /= src.lx;
-  const int iy = rem % src.ly;
-  const int iz = rem / src.ly;
+__device__ __forceinline__ void inject_source_node(float* p, const float* kappa, const float2* damp,
+                                                   const PointSet& src, const float* sig, int sig_stride, int step,
+                                                   const FaceInfo& f, int ndim, int R, int s, int iz, int iy, int ix) {
   const float* w = src.w + int64_t(s) * 3 * src.L;
   const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
   if (wgt == 0.f) return;
@@ -79,6 +71,37 @@ __device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, 
   add_with_mirrors(p, idx, z, f.nz, f.sz, f.bc[0], f.bc[1], R, d);
   add_with_mirrors(p, idx, x, f.nx, 1, f.bc[4], f.bc[5], R, d);
   if (ndim == 3) add_with_mirrors(p, idx, y, f.ny, f.sy, f.bc[2], f.bc[3], R, d);
+}
+
+__device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, const float2* damp,
+                                                  const PointSet& src, const float* sig, int sig_stride, int step,
+                                                  const FaceInfo& f, int ndim, int R, int t) {
+  const int taps = src.lz * src.ly * src.lx;
+  if (t >= src.count * taps) return;
+  const int s = t / taps;
+  int rem = t % taps;
+  const int ix = rem % src.lx;
+  rem /= src.lx;
+  const int iy = rem % src.ly;
+  const int iz = rem / src.ly;
+  inject_source_node(p, kappa, damp, src, sig, sig_stride, step, f, ndim, R, s, iz, iy, ix);
+}
+
+// The same increments over only the window rows with a non-zero weight along
+// z and y (src.span set; max_rows = the largest such row count): one thread
+// per (point, row, column).
+__global__ void inject_rows_kernel(float* p, const float* kappa, const float2* damp, PointSet src, int max_rows,
+                                   const float* sig, int sig_stride, int step, FaceInfo f, int ndim, int R) {
+  const int per = max_rows * src.lx;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= src.count * per) return;
+  const int s = t / per;
+  const int rem = t - s * per;
+  const int row = rem / src.lx, ix = rem - (rem / src.lx) * src.lx;
+  const int4 sp = src.span[s];
+  if (row >= sp.y * sp.w) return;
+  inject_source_node(p, kappa, damp, src, sig, sig_stride, step, f, ndim, R, s, sp.x + row / sp.w, sp.z + row % sp.w,
+                     ix);
 }
 
 __global__ void inject_sources_kernel(float* p, const float* kappa, const float2* damp, PointSet src,
@@ -505,44 +528,59 @@ struct LapCoef {
   float c[3][kMaxR + 1];  // v_j / h^2 per axis (z, y, x)
 };
 
-__global__ void neumann_adjoint_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
-                                       FaceInfo f, LapCoef lc, int R) {
-  const int axis = blockIdx.y;
-  const int n[3] = {f.nz, f.ny, f.nx};
-  const int64_t st[3] = {f.sz, f.sy, 1};
-  const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
-  const int64_t face = int64_t(n[o1]) * n[o2];
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+template <int AX>
+__device__ __forceinline__ void neumann_adjoint_axis(const float* psi1, float* out, const float* kappa,
+                                                     const float2* damp, const FaceInfo& f, const LapCoef& lc, int R,
+                                                     int64_t t) {
+  // the two other axes (o1 slower, o2 faster) and their extents and strides
+  constexpr int O1 = AX == 0 ? 1 : 0, O2 = AX == 2 ? 1 : 2;
+  const int n_ax = AX == 0 ? f.nz : (AX == 1 ? f.ny : f.nx);
+  const int n1 = O1 == 0 ? f.nz : f.ny;
+  const int n2 = O2 == 1 ? f.ny : f.nx;
+  const int64_t s_ax = AX == 0 ? f.sz : (AX == 1 ? f.sy : 1);
+  const int64_t s1 = O1 == 0 ? f.sz : f.sy;
+  const int64_t s2 = O2 == 1 ? f.sy : 1;
+  const int64_t face = int64_t(n1) * n2;
   if (t >= 2 * face) return;
   const int side = int(t / face);
-  if (f.bc[2 * axis + side] != kBcNeumann) return;
-  const int64_t e = t % face;
-  int c[3];
-  c[o1] = int(e / n[o2]);
-  c[o2] = int(e % n[o2]);
-  const int64_t base = int64_t(c[o1]) * st[o1] + int64_t(c[o2]) * st[o2];
-  auto node = [&](int k) {  // the node k in from this face; also sets c[axis]
-    c[axis] = side == 0 ? k : n[axis] - 1 - k;
-    return base + int64_t(c[axis]) * st[axis];
+  if ((side ? f.bc[2 * AX + 1] : f.bc[2 * AX]) != kBcNeumann) return;  // constant indices: f stays in registers
+  const int64_t e = t - side * face;
+  const int c1 = int(e / n2), c2 = int(e - (e / n2) * n2);
+  const int64_t base = int64_t(c1) * s1 + int64_t(c2) * s2;
+  // squared distance to the physical box along the two other axes
+  const int d1 = O1 == 0 ? face_distance(c1, f.nz, f.nbl[0], f.nbl[1]) : face_distance(c1, f.ny, f.nbl[2], f.nbl[3]);
+  const int d2o = O2 == 1 ? face_distance(c2, f.ny, f.nbl[2], f.nbl[3]) : face_distance(c2, f.nx, f.nbl[4], f.nbl[5]);
+  const int d12 = d1 * d1 + d2o * d2o;
+  auto at = [&](int k, float* a) {  // node k in from this face, and its 1/(1+e)
+    const int c = side == 0 ? k : n_ax - 1 - k;
+    const int da = face_distance(c, n_ax, f.nbl[2 * AX], f.nbl[2 * AX + 1]);
+    const int d2 = d12 + da * da;
+    *a = d2 ? damp[d2].x : 1.f;
+    return base + int64_t(c) * s_ax;
   };
-  auto damped_a = [&]() {  // 1/(1+e) of the node at c
-    const int dz = face_distance(c[0], f.nz, f.nbl[0], f.nbl[1]);
-    const int dy = face_distance(c[1], f.ny, f.nbl[2], f.nbl[3]);
-    const int dx = face_distance(c[2], f.nx, f.nbl[4], f.nbl[5]);
-    const int d2 = dz * dz + dy * dy + dx * dx;
-    return d2 ? damp[d2].x : 1.f;
-  };
-  const int64_t k0 = node(0);
-  const float a0 = damped_a();
+  float a0;
+  const int64_t k0 = at(0, &a0);
   const float pf = psi1[k0];
   float back = 0.f;
-  for (int k = 1; k <= R; ++k) {
-    const int64_t kk = node(k);
-    const float ak = damped_a();
-    atomicAdd(&out[kk], ak * kappa[kk] * lc.c[axis][k] * pf);
-    back = fmaf(lc.c[axis][k], psi1[kk], back);
+#pragma unroll
+  for (int k = 1; k <= kMaxR; ++k) {  // unrolled to kMaxR so that the weights stay in registers
+    if (k > R) break;
+    float ak;
+    const int64_t kk = at(k, &ak);
+    atomicAdd(&out[kk], ak * kappa[kk] * lc.c[AX][k] * pf);
+    back = fmaf(lc.c[AX][k], psi1[kk], back);
   }
   atomicAdd(&out[k0], -a0 * kappa[k0] * back);
+}
+
+__global__ void neumann_adjoint_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
+                                       FaceInfo f, LapCoef lc, int R) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  switch (blockIdx.y) {  // axis
+    case 0: neumann_adjoint_axis<0>(psi1, out, kappa, damp, f, lc, R, t); break;
+    case 1: neumann_adjoint_axis<1>(psi1, out, kappa, damp, f, lc, R, t); break;
+    default: neumann_adjoint_axis<2>(psi1, out, kappa, damp, f, lc, R, t); break;
+  }
 }
 
 // One term of dJ/dkappa per node: gk += psi (L p) / kappa, L the Eq. 9
