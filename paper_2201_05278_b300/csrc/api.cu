@@ -1216,13 +1216,13 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
           const int slot = 2 * (n / K) + i;
           const float* src_f = g->at0(i == 0 ? pm : pn);
           unsigned* sc = scales + slot;
-          absmax_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(src_f, f, sc);
+          absmax_kernel<<<row_grid(f), 256, 0, st>>>(src_f, f, sc);
           char* dst = static_cast<char*>(packs) + pbytes * slot;
           if (checkpoint_format == SW_CKPT_BF16)
-            pack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+            pack_snapshot_kernel<__nv_bfloat16><<<row_grid(f), 256, 0, st>>>(
                 src_f, f, sc, reinterpret_cast<__nv_bfloat16*>(dst));
           else
-            pack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(src_f, f, sc,
+            pack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(src_f, f, sc,
                                                                                      reinterpret_cast<__half*>(dst));
         }
         SW_CUDA(cudaGetLastError());
@@ -1348,10 +1348,10 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
           const int slot = 2 * sgm + i;
           const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
           if (checkpoint_format == SW_CKPT_BF16)
-            unpack_snapshot_kernel<__nv_bfloat16><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+            unpack_snapshot_kernel<__nv_bfloat16><<<row_grid(f), 256, 0, st>>>(
                 reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, g->at0(B(i)));
           else
-            unpack_snapshot_kernel<__half><<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(
+            unpack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(
                 reinterpret_cast<const __half*>(src_p), scales + slot, f, g->at0(B(i)));
           launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored level
         }

@@ -794,15 +794,21 @@ __global__ void gradient_density_kernel(const float* az, const float* ay, const 
 
 // max |p| over the nodes, as the bit pattern of a non-negative float
 // (order-preserving as an unsigned integer).
+// Node passes over (z, y) rows: blockIdx.x along x (256 threads), blockIdx.y
+// striding over the nz * ny rows, so that no thread divides per node.
+inline dim3 row_grid(const FaceInfo& f) {
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  const int64_t cap = 4096 / ((f.nx + 255) / 256) + 1;  // a few thousand CTAs, each walking many rows
+  return dim3(unsigned((f.nx + 255) / 256), unsigned(rows < cap ? rows : cap));
+}
+
 __global__ void absmax_kernel(const float* p, FaceInfo f, unsigned* out) {
-  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
   unsigned m = 0u;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int x = int(i % f.nx);
-    const int64_t zy = i / f.nx;
-    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
-    m = max(m, __float_as_uint(fabsf(p[k])));
-  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  if (x < f.nx)
+    for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
+      m = max(m, __float_as_uint(fabsf(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x])));
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
@@ -821,24 +827,22 @@ __device__ __forceinline__ __half to_half_kind<__half>(float v) { return __float
 
 template <typename T>
 __global__ void pack_snapshot_kernel(const float* p, FaceInfo f, const unsigned* scale_bits, T* out) {
-  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
   const float inv = 1.f / snapshot_scale(scale_bits);
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int x = int(i % f.nx);
-    const int64_t zy = i / f.nx;
-    out[i] = to_half_kind<T>(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] * inv);
-  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  if (x >= f.nx) return;
+  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
+    out[zy * f.nx + x] = to_half_kind<T>(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] * inv);
 }
 
 template <typename T>
 __global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, FaceInfo f, float* p) {
-  const int64_t n = int64_t(f.nz) * f.ny * f.nx;
   const float sc = snapshot_scale(scale_bits);
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int x = int(i % f.nx);
-    const int64_t zy = i / f.nx;
-    p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] = float(in[i]) * sc;
-  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  if (x >= f.nx) return;
+  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
+    p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] = float(in[zy * f.nx + x]) * sc;
 }
 
 // Distributed forcing f(x, t_n) = sum_m F_m(x) T_m(t_n), added like a source
