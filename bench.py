@@ -258,12 +258,29 @@ def run_batch(args, world, rank, local, dev):
         e2e = {"value": round(job_throughput(shot_nodes * n_steps, args.e2e_steps, world, e2e_s), 3), "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(sum(h.numel() for h in seis_h) * 4)}
 
+    tile_rows, tuned_us = api.sw_batch_get_tile(b)
+    b.close()
+    # the same shots run one after another with the plain single-grid forward
+    # (its second call, the captured graph, is the one timed)
+    unbatched = None
+    if args.e2e_steps > 0 or not args.no_cpu_baseline:
+        for g, s in zip(grids, seis):
+            api.sw_forward(g, n_steps, s, None)
+        barrier()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for g, s in zip(grids, seis):
+            api.sw_forward(g, n_steps, s, None)
+        u1.record(stream)
+        barrier()
+        ums = u0.elapsed_time(u1)
+        unbatched = {"value": round(shot_nodes * n_steps / (ums * 1e-3) / 1e9, 3), "unit": UNIT,
+                     "ms": round(ums, 3), "how": "sw_forward per shot, one after another, same GPU"}
     peak, peak_kind = _peaks()
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
     alg_bytes = 12 * shot_nodes + 4 * model_nodes
     achieved = alg_bytes / avg_launch_s / 1e9
     traffic = _traffic_record(args.workload, "batch_traffic.txt", BATCH_SOURCES)
-    b.close()
     for g in grids:
         g.close()
     if rank == 0:
@@ -275,7 +292,10 @@ def run_batch(args, world, rank, local, dev):
                        "nodes_per_step": shot_nodes, "space_order": shots[0].order,
                        "time_steps_per_forward": n_steps, "receivers_per_shot": len(shots[0].rec_pos),
                        "parallelism": "replicas" if world > 1 else "single",
+                       "tile": "128 x %d (tuner, us per launch for 16/32/64 rows: %s)" % (
+                           tile_rows, ", ".join("%.1f" % t for t in tuned_us)),
                        "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+            "unbatched": unbatched,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "batched stencil (CUDA events around every %dth launch, %d launches timed)" % (
@@ -355,7 +375,12 @@ def run_gradient(args, world, rank, local, dev):
     shot(used[0])
     api.sw_set_profiling(g, PROFILE_EVERY)
     tmp = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
     api.sw_forward(g, N, tmp, None)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    forward_ms = f0.elapsed_time(f1)
     st_ms, st_n, _ = api.sw_get_profile(g)
     api.sw_set_profiling(g, 0)
     grad = torch.empty(w.shape, dtype=torch.float32, device=dev)
@@ -371,6 +396,19 @@ def run_gradient(args, world, rank, local, dev):
 
     for k in range(args.warmup):
         one(k)
+    # error of the BF16 checkpoints at this scale: the same shot's gradient
+    # with FP32 checkpoints (untimed; the FP32 path matches the FP64 oracle
+    # within 2e-3 on the test grids)
+    shot(used[0])
+    g_ref = torch.empty_like(grad)
+    api.sw_gradient(g, N, obs[used[0]], g_ref, c.checkpoint_every, api.SW_CKPT_FP32)
+    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_FP16)
+    fp16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
+    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_I16)
+    i16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
+    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_BF16)
+    bf16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
+    del g_ref
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -415,6 +453,14 @@ def run_gradient(args, world, rank, local, dev):
             "config": {"workload": args.workload, "grid": list(w.shape), "space_order": w.order,
                        "time_steps": N, "shots": n_shots, "receivers": n_rec,
                        "checkpoints": "BF16 pairs with per-snapshot scale every %d steps" % c.checkpoint_every,
+                       "shots_per_s": round(world * args.steps / (elapsed_ms * 1e-3), 4),
+                       "forward_ms_per_shot": round(forward_ms, 3),
+                       "gradient_error": {"bf16_vs_fp32_checkpoints_rel_l2": round(bf16_err, 6),
+                                          "fp16_vs_fp32_checkpoints_rel_l2": round(fp16_err, 6),
+                                          "i16_vs_fp32_checkpoints_rel_l2": round(i16_err, 6),
+                                          "vs_fp64_oracle": "test grids (tests/test_gpu_gradient.py): "
+                                                            "FP32 checkpoints <= 2e-3, BF16 <= 1e-2, FP16 <= "
+                                                            "2e-3, I16 <= 5e-4"},
                        "quantity": "forward grid-point updates per second of gradient computation (forward, "
                                    "residual, adjoint sweep with recomputation, imaging)",
                        "parallelism": "replicas" if world > 1 else "single",

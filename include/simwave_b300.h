@@ -145,11 +145,18 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  *                    sqrt(2 n_steps)); each segment is recomputed during the
  *                    adjoint sweep.
  *   checkpoint_format SW_CKPT_FP32: each checkpoint is a copy of the two
- *                    padded FP32 levels; SW_CKPT_BF16 / SW_CKPT_FP16: the
- *                    levels' nodes in 16 bits, divided by the level's largest
- *                    magnitude (kept per snapshot), so the recomputed
- *                    segments start from rounded states and the gradient
- *                    carries that rounding.  Device memory for the call,
+ *                    padded FP32 levels.  16-bit formats keep the nodes of
+ *                    p[k0] and of the difference p[k0] - p[k0-1] (small
+ *                    next to p; stored on its own, so that the time
+ *                    difference a recomputed segment starts from is as
+ *                    accurate as the level), so the recomputed segments
+ *                    start from rounded states and the gradient carries
+ *                    that rounding: SW_CKPT_BF16 / SW_CKPT_FP16 as 16-bit
+ *                    floats divided by the field's largest magnitude (one
+ *                    scale per snapshot); SW_CKPT_I16 as 16-bit fixed point
+ *                    with one scale per (z, y) row of nodes (the rounding
+ *                    step is 1/32767 of the row's largest magnitude instead
+ *                    of 8 or 11 bits of every value).  Device memory for the call,
  *                    freed before it returns: (2 n_steps / K + K + 4) padded
  *                    FP32 wavefields (K + 4 with 16-bit checkpoints, plus
  *                    2 n_steps / K node arrays of 2 bytes per node; 3 or 6
@@ -161,7 +168,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  * buffers do not fit.  The grid's wavefields
  * hold the forward run's last two levels afterwards.
  */
-enum { SW_CKPT_FP32 = 0, SW_CKPT_BF16 = 1, SW_CKPT_FP16 = 2 };
+enum { SW_CKPT_FP32 = 0, SW_CKPT_BF16 = 1, SW_CKPT_FP16 = 2, SW_CKPT_I16 = 3 };
 sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
                       float* grad_rho, int checkpoint_every, int checkpoint_format);
 
@@ -268,12 +275,22 @@ sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t
  *
  * sw_batch_info: number of model groups and of work items (tile of one
  * shot) per step.
+ *
+ * Tile shape: tiles are 128 columns wide and 16, 32 or 64 rows high.
+ * sw_create_batch tunes the height on the batch itself: it times a few
+ * stencil launches with each height (on zeroed fields) and keeps the
+ * fastest.  sw_batch_get_tile returns the height in use and, if tuned_us is
+ * not NULL, the three timings (microseconds per launch, heights 16, 32, 64);
+ * sw_batch_set_tile forces a height (SW_EINVAL for another value).  The
+ * results do not depend on the height.
  * sw_batch_set_profiling / sw_batch_get_profile: as for a grid (every
  * every-th stencil launch timed with CUDA events).
  */
 sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids);
 sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, float* const* final_fields);
 sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_items);
+sw_status sw_batch_get_tile(const sw_batch* b, int* tile_rows, float* tuned_us);
+sw_status sw_batch_set_tile(sw_batch* b, int tile_rows);
 sw_status sw_batch_set_profiling(sw_batch* b, int every);
 sw_status sw_batch_get_profile(const sw_batch* b, double* stencil_ms, int64_t* stencil_launches,
                                int64_t* kernel_launches);

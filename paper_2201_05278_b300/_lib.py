@@ -51,6 +51,8 @@ SIGNATURES = {
     "sw_batch_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "sw_batch_info": (ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_ip]),
+    "sw_batch_get_tile": (ctypes.c_int, [ctypes.c_void_p, _c_ip, ctypes.POINTER(ctypes.c_float)]),
+    "sw_batch_set_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_batch_get_profile": (ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_i64p, _c_i64p]),
     "sw_destroy_batch": (None, [ctypes.c_void_p]),

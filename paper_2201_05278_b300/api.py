@@ -127,7 +127,7 @@ def sw_forward(g: Grid, n_steps: int, seismogram=None, final_field=None) -> None
     _check(_lib.load().sw_forward(g.handle, int(n_steps), _ptr(seismogram), _ptr(final_field)))
 
 
-SW_CKPT_FP32, SW_CKPT_BF16, SW_CKPT_FP16 = 0, 1, 2
+SW_CKPT_FP32, SW_CKPT_BF16, SW_CKPT_FP16, SW_CKPT_I16 = 0, 1, 2, 3
 
 
 def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int = 0,
@@ -224,6 +224,19 @@ def sw_batch_info(b: Batch):
     ng, nt = ctypes.c_int(), ctypes.c_int()
     _check(_lib.load().sw_batch_info(b.handle, ctypes.byref(ng), ctypes.byref(nt)))
     return ng.value, nt.value
+
+
+def sw_batch_get_tile(b: Batch):
+    """(tile height in use, [us per stencil launch with heights 16, 32, 64] as timed by the tuner)."""
+    rows = ctypes.c_int()
+    us = (ctypes.c_float * 3)()
+    _check(_lib.load().sw_batch_get_tile(b.handle, ctypes.byref(rows), us))
+    return rows.value, list(us)
+
+
+def sw_batch_set_tile(b: Batch, tile_rows: int) -> None:
+    """Force the tile height (16, 32 or 64 rows) instead of the tuner's choice."""
+    _check(_lib.load().sw_batch_set_tile(b.handle, int(tile_rows)))
 
 
 def sw_batch_set_profiling(b: Batch, every=1) -> None:

@@ -1059,7 +1059,8 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   if (n_steps < 1) return fail(SW_EINVAL, "n_steps < 1");
   if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
   if (checkpoint_every < 0) return fail(SW_EINVAL, "checkpoint_every < 0");
-  if (checkpoint_format != SW_CKPT_FP32 && checkpoint_format != SW_CKPT_BF16 && checkpoint_format != SW_CKPT_FP16)
+  if (checkpoint_format != SW_CKPT_FP32 && checkpoint_format != SW_CKPT_BF16 && checkpoint_format != SW_CKPT_FP16 &&
+      checkpoint_format != SW_CKPT_I16)
     return fail(SW_EINVAL, "unknown checkpoint format %d", checkpoint_format);
   if (g->n[0] > 65535 || g->n[1] > 65535) return fail(SW_EINVAL, "axis longer than 65535 nodes");
   for (int ax = 0; ax < 3; ++ax)  // the face passes need every node within R of one face only
@@ -1093,6 +1094,9 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   const size_t pbytes = size_t(g->nodes()) * 2;  // one packed checkpoint
   void* packs = nullptr;
   unsigned* scales = nullptr;
+  const bool i16 = checkpoint_format == SW_CKPT_I16;
+  const int64_t nrows = g->n[0] * g->n[1];
+  float* row_scales = nullptr;  // SW_CKPT_I16: one scale per (z, y) row of every stored level
   std::vector<float*> F(size_t(nfields), nullptr);
   float *syn = nullptr, *obs = nullptr, *res = nullptr;
   double* macc = nullptr;
@@ -1109,6 +1113,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     dev_free(g, macc, sizeof(double));
     dev_free(g, packs, packed ? pbytes * 2 * nseg : 0);
     dev_free(g, scales, packed ? sizeof(unsigned) * 2 * nseg : 0);
+    dev_free(g, row_scales, i16 ? sizeof(float) * size_t(nrows) * 2 * nseg : 0);
   };
   struct Guard {
     std::function<void()> fn;
@@ -1126,6 +1131,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     SW_TRY(dev_alloc(g, &packs, pbytes * 2 * nseg));
     SW_TRY(dev_alloc(g, (void**)&scales, sizeof(unsigned) * 2 * nseg));
     SW_CUDA(cudaMemsetAsync(scales, 0, sizeof(unsigned) * 2 * nseg, st));
+    if (i16) SW_TRY(dev_alloc(g, (void**)&row_scales, sizeof(float) * size_t(nrows) * 2 * nseg));
   }
   SW_CUDA(cudaMemcpyAsync(obs, observed, sbytes, cudaMemcpyDefault, st));
   SW_CUDA(cudaMemsetAsync(macc, 0, sizeof(double), st));
@@ -1212,18 +1218,27 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     float* pm = g->u[(n + 1) & 1];
     if (!revolve && n % K == 0) {
       if (packed) {
+        // slot 1: p[n]; slot 0: p[n] - p[n-1], small next to p, kept with its
+        // own scale so that the time difference a recomputed segment starts
+        // from is as accurate as the level itself
         for (int i = 0; i < 2; ++i) {
           const int slot = 2 * (n / K) + i;
-          const float* src_f = g->at0(i == 0 ? pm : pn);
+          const float* a_f = g->at0(pn);
+          const float* b_f = i == 0 ? g->at0(pm) : nullptr;
           unsigned* sc = scales + slot;
-          absmax_kernel<<<row_grid(f), 256, 0, st>>>(src_f, f, sc);
           char* dst = static_cast<char*>(packs) + pbytes * slot;
+          if (i16) {
+            pack_rows_i16_kernel<<<unsigned(std::min<int64_t>(nrows, 4096)), 256, 0, st>>>(
+                a_f, b_f, f, row_scales + size_t(nrows) * slot, reinterpret_cast<int16_t*>(dst));
+            continue;
+          }
+          absmax_kernel<<<row_grid(f), 256, 0, st>>>(a_f, b_f, f, sc);
           if (checkpoint_format == SW_CKPT_BF16)
             pack_snapshot_kernel<__nv_bfloat16><<<row_grid(f), 256, 0, st>>>(
-                src_f, f, sc, reinterpret_cast<__nv_bfloat16*>(dst));
+                a_f, b_f, f, sc, reinterpret_cast<__nv_bfloat16*>(dst));
           else
-            pack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(src_f, f, sc,
-                                                                                     reinterpret_cast<__half*>(dst));
+            pack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(a_f, b_f, f, sc,
+                                                                     reinterpret_cast<__half*>(dst));
         }
         SW_CUDA(cudaGetLastError());
       } else {
@@ -1344,17 +1359,23 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     for (int sgm = nseg - 1; sgm >= 0; --sgm) {
       const int k0 = sgm * K, k1 = std::min(N, k0 + K);
       if (packed) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 1; i >= 0; --i) {  // p[k0] first, then p[k0-1] = p[k0] - (p[k0] - p[k0-1])
           const int slot = 2 * sgm + i;
           const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
-          if (checkpoint_format == SW_CKPT_BF16)
+          const float* base = i == 0 ? g->at0(B(1)) : nullptr;
+          if (i16)
+            unpack_rows_i16_kernel<<<row_grid(f), 256, 0, st>>>(reinterpret_cast<const int16_t*>(src_p),
+                                                                row_scales + size_t(nrows) * slot, f, base,
+                                                                g->at0(B(i)));
+          else if (checkpoint_format == SW_CKPT_BF16)
             unpack_snapshot_kernel<__nv_bfloat16><<<row_grid(f), 256, 0, st>>>(
-                reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, g->at0(B(i)));
+                reinterpret_cast<const __nv_bfloat16*>(src_p), scales + slot, f, base, g->at0(B(i)));
           else
             unpack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(
-                reinterpret_cast<const __half*>(src_p), scales + slot, f, g->at0(B(i)));
-          launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored level
+                reinterpret_cast<const __half*>(src_p), scales + slot, f, base, g->at0(B(i)));
         }
+        for (int i = 0; i < 2; ++i)
+          launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored levels
         SW_CUDA(cudaGetLastError());
       } else {
         SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
@@ -1397,7 +1418,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   SW_TRY(check_device_flag(g));
   // + residual and velocity gradient, density gradient, ln rho gradients,
   // and per 16-bit checkpoint segment absmax + pack and unpack + faces of two levels
-  g->kernel_launches = nk + 2 + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) + (packed ? 8 * int64_t(nseg) : 0);
+  g->kernel_launches = nk + 2 + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) + (packed ? (i16 ? 6 : 8) * int64_t(nseg) : 0);
   g->stencil_launches = 0;
   g->stencil_ms = 0.0;
   return SW_OK;
@@ -1883,11 +1904,14 @@ struct sw_batch {
   std::vector<int> slot_grid;    // shot-table slot -> grid index
   std::vector<int> grid_group;   // grid index -> group
   std::vector<BatchShot> shots;  // host copy of the shot table
-  BatchGroup* d_groups = nullptr;
+  // one work list per tile height the tuner tries (kBatchZBs); `cfg` is the one in use
+  BatchGroup* d_groups[3] = {nullptr, nullptr, nullptr};
+  int total_items[3] = {0, 0, 0}, blocks[3] = {0, 0, 0}, smem[3] = {0, 0, 0};
+  float tuned_us[3] = {0.f, 0.f, 0.f};  // one stencil launch per tile height, timed at creation
+  int cfg = 1;
   BatchShot* d_shots = nullptr;
-  int n_groups = 0, total_items = 0, blocks = 0, R = 0;
+  int n_groups = 0, R = 0;
   int max_src_taps = 0, max_rec = 0, max_rec_warps = 0;
-  int smem = 0;  // dynamic shared memory of the batched stencil
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -1903,34 +1927,26 @@ namespace {
 
 using BatchFn = void (*)(const BatchGroup*, int, const BatchShot*, int, int, int*, unsigned long long);
 
-int batch_smem_bytes(int R) {
+template <int ZB>
+void batch_variant(int R, BatchFn* fn, int* smem) {
+#define SW_BATCH_R(RR)                                 \
+  case RR:                                             \
+    *fn = batch_stencil_2d_kernel<RR, ZB>;             \
+    *smem = BatchSmem<RR, ZB>::BYTES;                  \
+    break;
   switch (R) {
-    case 1: return BatchSmem<1>::BYTES;
-    case 2: return BatchSmem<2>::BYTES;
-    case 3: return BatchSmem<3>::BYTES;
-    case 4: return BatchSmem<4>::BYTES;
-    case 5: return BatchSmem<5>::BYTES;
-    case 6: return BatchSmem<6>::BYTES;
-    case 7: return BatchSmem<7>::BYTES;
-    case 8: return BatchSmem<8>::BYTES;
-    case 9: return BatchSmem<9>::BYTES;
-    default: return BatchSmem<10>::BYTES;
+    SW_BATCH_R(1) SW_BATCH_R(2) SW_BATCH_R(3) SW_BATCH_R(4) SW_BATCH_R(5)
+    SW_BATCH_R(6) SW_BATCH_R(7) SW_BATCH_R(8) SW_BATCH_R(9) SW_BATCH_R(10)
+    default: *fn = nullptr; *smem = 0; break;
   }
+#undef SW_BATCH_R
 }
 
-BatchFn batch_kernel(int R) {
-  switch (R) {
-    case 1: return batch_stencil_2d_kernel<1>;
-    case 2: return batch_stencil_2d_kernel<2>;
-    case 3: return batch_stencil_2d_kernel<3>;
-    case 4: return batch_stencil_2d_kernel<4>;
-    case 5: return batch_stencil_2d_kernel<5>;
-    case 6: return batch_stencil_2d_kernel<6>;
-    case 7: return batch_stencil_2d_kernel<7>;
-    case 8: return batch_stencil_2d_kernel<8>;
-    case 9: return batch_stencil_2d_kernel<9>;
-    default: return batch_stencil_2d_kernel<10>;
-  }
+// The batched stencil for radius R and tile height kBatchZBs[cfg].
+void batch_kernel(int R, int cfg, BatchFn* fn, int* smem) {
+  if (cfg == 0) batch_variant<kBatchZBs[0]>(R, fn, smem);
+  else if (cfg == 1) batch_variant<kBatchZBs[1]>(R, fn, smem);
+  else batch_variant<kBatchZBs[2]>(R, fn, smem);
 }
 
 bool same_geometry(const sw_grid* a, const sw_grid* b) {
@@ -1963,6 +1979,52 @@ sw_status same_model(sw_grid* a, sw_grid* b, cudaStream_t st, bool* same) {
   SW_CUDA(cudaMemsetAsync(a->dflag, 0, sizeof(int), st));
   *same = flag == 0;
   return SW_OK;
+}
+
+sw_status tune_batch(sw_batch* b) {
+  cudaStream_t st = b->stream;
+  for (sw_grid* g : b->grids) {
+    const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+    SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
+  }
+  cudaEvent_t ev[2];
+  SW_CUDA(cudaEventCreate(&ev[0]));
+  SW_CUDA(cudaEventCreate(&ev[1]));
+  float best = 0.f;
+  sw_status status = SW_OK;
+  for (int c = 0; c < 3 && status == SW_OK; ++c) {
+    BatchFn fn = nullptr;
+    int smem = 0;
+    batch_kernel(b->R, c, &fn, &smem);
+    const BatchGroup* dg = b->d_groups[c];
+    const BatchShot* ds = b->d_shots;
+    int ng = b->n_groups, nt = b->total_items[c];
+    int* flag = b->grids[0]->dflag;
+    unsigned long long limit = b->grids[0]->wait_limit_ns;
+    constexpr int kWarm = 1, kTimed = 4;
+    for (int i = 0; i < kWarm + kTimed && status == SW_OK; ++i) {
+      int parity = i & 1;
+      void* args[] = {&dg, &ng, &ds, &nt, &parity, &flag, &limit};
+      if (i == kWarm && cudaEventRecord(ev[0], st) != cudaSuccess) status = fail(SW_ECUDA, "tuner event");
+      const cudaError_t e = cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks[c])), dim3(kBatchThreads), args,
+                                             size_t(smem), st);
+      if (e != cudaSuccess) status = fail(SW_ECUDA, "tuner launch: %s", cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    if (status == SW_OK && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess))
+      status = fail(SW_ECUDA, "tuner timing");
+    b->tuned_us[c] = 1000.f * ms / float(kTimed);
+    if (status == SW_OK && (c == 0 || b->tuned_us[c] < best)) {
+      best = b->tuned_us[c];
+      b->cfg = c;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (status != SW_OK) return status;
+  return check_device_flag(b->grids[0]);
 }
 
 }  // namespace
@@ -2041,8 +2103,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
     G.first = int(b->slot_grid.size());
     G.count = int(m.size());
     G.tiles_x = (G.nx + kBatchTX - 1) / kBatchTX;
-    G.item_base = tiles;
-    tiles += G.tiles_x * ((G.nz + kBatchZB - 1) / kBatchZB) * G.count;
+    G.item_base = 0;  // per tile height, below
     for (int i : m) {
       sw_grid* s = grids[i];
       b->slot_grid.push_back(i);
@@ -2067,29 +2128,47 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
     groups.push_back(G);
   }
   b->n_groups = int(groups.size());
-  b->total_items = tiles;
-  int per_sm = 0;
-  b->smem = batch_smem_bytes(b->R);
-  cudaError_t e = cudaFuncSetAttribute((const void*)batch_kernel(b->R), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       b->smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(b->R), kBatchThreads, size_t(b->smem));
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  b->blocks = std::min(tiles, per_sm * std::max(g0->sm_count, 1));
-  e = cudaMalloc((void**)&b->d_groups, groups.size() * sizeof(BatchGroup));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_shots, b->shots.size() * sizeof(BatchShot));
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_groups, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice,
-                        b->stream);
+  // one work list, occupancy and launch size per tile height
+  cudaError_t e = cudaMalloc((void**)&b->d_shots, b->shots.size() * sizeof(BatchShot));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_shots, b->shots.data(), b->shots.size() * sizeof(BatchShot), cudaMemcpyHostToDevice,
                         b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    int items = 0;
+    for (BatchGroup& G : groups) {
+      G.item_base = items;
+      items += G.tiles_x * ((G.nz + kBatchZBs[c] - 1) / kBatchZBs[c]) * G.count;
+    }
+    b->total_items[c] = items;
+    BatchFn fn = nullptr;
+    batch_kernel(b->R, c, &fn, &b->smem[c]);
+    int per_sm = 0;
+    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem[c]);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, size_t(b->smem[c]));
+    if (e == cudaSuccess) {
+      b->blocks[c] = std::max(1, std::min(items, std::max(per_sm, 1) * std::max(g0->sm_count, 1)));
+      e = cudaMalloc((void**)&b->d_groups[c], groups.size() * sizeof(BatchGroup));
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_groups[c], groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice,
+                          b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the host table changes for the next height
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     sw_destroy_batch(b);
     return fail(e == cudaErrorMemoryAllocation ? SW_ENOMEM : SW_ECUDA, "batch set-up failed: %s",
                 cudaGetErrorString(e));
+  }
+  // tuner: time a few stencil launches with every tile height on this batch
+  // (zeroed fields; every forward zeroes them again) and keep the fastest
+  const sw_status ts = tune_batch(b);
+  if (ts != SW_OK) {
+    std::string msg = g_last_error;
+    sw_destroy_batch(b);
+    g_last_error = msg;
+    return ts;
   }
   *out = b;
   return SW_OK;
@@ -2098,8 +2177,34 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
 sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_items) {
   if (!b) return fail(SW_EINVAL, "NULL batch");
   if (n_groups) *n_groups = b->n_groups;
-  if (n_items) *n_items = b->total_items;
+  if (n_items) *n_items = b->total_items[b->cfg];
   return SW_OK;
+}
+
+sw_status sw_batch_get_tile(const sw_batch* b, int* tile_rows, float* tuned_us) {
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (tile_rows) *tile_rows = kBatchZBs[b->cfg];
+  if (tuned_us)
+    for (int c = 0; c < 3; ++c) tuned_us[c] = b->tuned_us[c];
+  return SW_OK;
+}
+
+sw_status sw_batch_set_tile(sw_batch* b, int tile_rows) {
+  if (!b) return fail(SW_EINVAL, "NULL batch");
+  for (int c = 0; c < 3; ++c)
+    if (kBatchZBs[c] == tile_rows) {
+      if (c != b->cfg) {
+        b->cfg = c;
+        b->last_steps = -1;  // the captured loop holds the old kernel: capture anew
+        if (b->graph) {
+          cudaGraphExecDestroy(b->graph);
+          b->graph = nullptr;
+          b->graph_steps = -1;
+        }
+      }
+      return SW_OK;
+    }
+  return fail(SW_EINVAL, "tile height %d is not one of 16, 32, 64", tile_rows);
 }
 
 sw_status sw_batch_set_profiling(sw_batch* b, int every) {
@@ -2173,7 +2278,9 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
     b->events.resize(size_t(2 * timed));
     for (size_t i = old; i < b->events.size(); ++i) SW_CUDA(cudaEventCreate(&b->events[i]));
   }
-  const BatchFn fn = batch_kernel(b->R);
+  BatchFn fn = nullptr;
+  int smem_c = 0;
+  batch_kernel(b->R, b->cfg, &fn, &smem_c);
   const int n_shots = int(b->shots.size());
   int64_t launches = 0;
   auto enqueue = [&](cudaStream_t s, bool capturing) -> sw_status {
@@ -2184,14 +2291,14 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
       const bool time_it = b->profiling && step % b->profiling == 0;
       const int ev = time_it ? 2 * (step / b->profiling) : 0;
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev)], s, evflags));
-      const BatchGroup* dg = b->d_groups;
+      const BatchGroup* dg = b->d_groups[b->cfg];
       const BatchShot* ds = b->d_shots;
-      int ng = b->n_groups, nt = b->total_items;
+      int ng = b->n_groups, nt = b->total_items[b->cfg];
       int* flag = b->grids[0]->dflag;
       unsigned long long limit = b->grids[0]->wait_limit_ns;
       void* args[] = {&dg, &ng, &ds, &nt, &parity, &flag, &limit};
-      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks)), dim3(kBatchThreads), args, size_t(b->smem),
-                               s));
+      SW_CUDA(cudaLaunchKernel((const void*)fn, dim3(unsigned(b->blocks[b->cfg])), dim3(kBatchThreads), args,
+                               size_t(smem_c), s));
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev + 1)], s, evflags));
       ++launches;
       if (b->max_src_taps > 0) {
@@ -2276,7 +2383,7 @@ void sw_destroy_batch(sw_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
-  cudaFree(b->d_groups);
+  for (int c = 0; c < 3; ++c) cudaFree(b->d_groups[c]);
   cudaFree(b->d_shots);
   delete b;
 }

@@ -802,13 +802,16 @@ inline dim3 row_grid(const FaceInfo& f) {
   return dim3(unsigned((f.nx + 255) / 256), unsigned(rows < cap ? rows : cap));
 }
 
-__global__ void absmax_kernel(const float* p, FaceInfo f, unsigned* out) {
+// max |p - q| over the nodes (q may be NULL: max |p|)
+__global__ void absmax_kernel(const float* p, const float* q, FaceInfo f, unsigned* out) {
   unsigned m = 0u;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t rows = int64_t(f.nz) * f.ny;
   if (x < f.nx)
-    for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
-      m = max(m, __float_as_uint(fabsf(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x])));
+    for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y) {
+      const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
+      m = max(m, __float_as_uint(fabsf(q ? p[k] - q[k] : p[k])));
+    }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
@@ -825,24 +828,74 @@ __device__ __forceinline__ __nv_bfloat16 to_half_kind<__nv_bfloat16>(float v) { 
 template <>
 __device__ __forceinline__ __half to_half_kind<__half>(float v) { return __float2half_rn(v); }
 
+// out = (p - q) / scale per node in 16 bits (q may be NULL: p / scale)
 template <typename T>
-__global__ void pack_snapshot_kernel(const float* p, FaceInfo f, const unsigned* scale_bits, T* out) {
+__global__ void pack_snapshot_kernel(const float* p, const float* q, FaceInfo f, const unsigned* scale_bits, T* out) {
   const float inv = 1.f / snapshot_scale(scale_bits);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t rows = int64_t(f.nz) * f.ny;
   if (x >= f.nx) return;
-  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
-    out[zy * f.nx + x] = to_half_kind<T>(p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] * inv);
+  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y) {
+    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
+    out[zy * f.nx + x] = to_half_kind<T>((q ? p[k] - q[k] : p[k]) * inv);
+  }
 }
 
+// p = base - in * scale per node (base may be NULL: p = in * scale)
 template <typename T>
-__global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, FaceInfo f, float* p) {
+__global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, FaceInfo f, const float* base,
+                                       float* p) {
   const float sc = snapshot_scale(scale_bits);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t rows = int64_t(f.nz) * f.ny;
   if (x >= f.nx) return;
-  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y)
-    p[(zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x] = float(in[zy * f.nx + x]) * sc;
+  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y) {
+    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
+    const float v = float(in[zy * f.nx + x]) * sc;
+    p[k] = base ? base[k] - v : v;
+  }
+}
+
+// 16-bit fixed point with one scale per (z, y) row of the nodes:
+// q = round(v * 32767 / s), s = max |v| over the row, v = p - base (base may
+// be NULL: v = p).  Wavefields vary smoothly along a row, so the step
+// s / 32767 is small next to the values that matter, where a 16-bit float
+// keeps only 8 or 11 bits of every value.  One CTA of 256 threads per row.
+__global__ void pack_rows_i16_kernel(const float* p, const float* base, FaceInfo f, float* scales, int16_t* out) {
+  __shared__ float red[8];
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t zy = blockIdx.x; zy < rows; zy += gridDim.x) {
+    const int64_t off = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy;
+    const float* pr = p + off;
+    const float* br = base ? base + off : nullptr;
+    float m = 0.f;
+    for (int x = threadIdx.x; x < f.nx; x += blockDim.x) m = fmaxf(m, fabsf(br ? pr[x] - br[x] : pr[x]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    m = red[0];
+    for (int i = 1; i < int(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+    const float sc = m > 0.f ? m : 1.f;
+    if (threadIdx.x == 0) scales[zy] = sc;
+    const float inv = 32767.f / sc;
+    for (int x = threadIdx.x; x < f.nx; x += blockDim.x)
+      out[zy * f.nx + x] = int16_t(__float2int_rn((br ? pr[x] - br[x] : pr[x]) * inv));
+    __syncthreads();  // red is reused by the next row
+  }
+}
+
+// p = base - v or p = v with v = q * s / 32767 (row scales s), row-mapped.
+__global__ void unpack_rows_i16_kernel(const int16_t* in, const float* scales, FaceInfo f, const float* base,
+                                       float* p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rows = int64_t(f.nz) * f.ny;
+  if (x >= f.nx) return;
+  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y) {
+    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
+    const float v = float(in[zy * f.nx + x]) * (scales[zy] * (1.f / 32767.f));
+    p[k] = base ? base[k] - v : v;
+  }
 }
 
 // Distributed forcing f(x, t_n) = sum_m F_m(x) T_m(t_n), added like a source

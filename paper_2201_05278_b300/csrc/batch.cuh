@@ -8,8 +8,8 @@
 // every shot of the group, so the update streams 12 B per node and shot plus
 // 4 B per node and group instead of 16 B per node and shot.
 //
-// Work list: every group is cut into tiles of kBatchTX columns by kBatchZB
-// rows; a work item is one tile of one shot.  Items are numbered group after
+// Work list: every group is cut into tiles of kBatchTX columns by ZB rows
+// (ZB = 16, 32 or 64, picked per batch by timing each, see sw_create_batch); a work item is one tile of one shot.  Items are numbered group after
 // group, tile-major with the shot fastest (so the shots of a tile run side by
 // side and read its kappa once from memory, then from L2), and a persistent
 // grid walks them.  One warp copies the item's p[n] rows (with both halos)
@@ -32,7 +32,7 @@ namespace sw {
 
 constexpr int kBatchTX = 128;       // columns per tile
 constexpr int kBatchThreads = 128;  // one column per thread
-constexpr int kBatchZB = 32;   // rows per tile
+constexpr int kBatchZBs[3] = {16, 32, 64};  // tile heights the tuner tries
 constexpr int kBatchU = 4;     // rows per register-queue chunk
 
 // One model shared by the shots [first, first + count) of the shot table.
@@ -65,14 +65,14 @@ struct BatchShot {
 // over columns x0 - RH .. x0 + TX + RH - 1 (RH = R rounded up to 4 floats, so
 // that every row starts on a 16-byte boundary).  p[n-1] and kappa, read once
 // and without neighbours, go straight to registers, a chunk ahead.
-template <int R>
+template <int R, int ZB>
 struct BatchSmem {
   static constexpr int RH = (R + 3) / 4 * 4;
   static constexpr int TXP = kBatchTX + 2 * RH;
-  static constexpr int PROWS = kBatchZB + 2 * R;
+  static constexpr int PROWS = ZB + 2 * R;
   static constexpr int BYTES = PROWS * TXP * 4;
 };
-static_assert(kBatchZB / kBatchU <= 8, "one mbarrier per chunk, at most 8");
+constexpr int kBatchMaxChunks = 16;  // one mbarrier per chunk: ZB / kBatchU of them
 
 // 1D bulk copy global -> shared, completing `bytes` on the mbarrier `bar`.
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -86,6 +86,7 @@ struct BatchItem {
   int g, s, x0, z0, z1, nch;
 };
 
+template <int ZB>
 __device__ __forceinline__ BatchItem batch_item(const BatchGroup* __restrict__ groups, int n_groups, int t) {
   int lo = 0, hi = n_groups - 1;  // last group whose first item is <= t
   while (lo < hi) {
@@ -103,24 +104,26 @@ __device__ __forceinline__ BatchItem batch_item(const BatchGroup* __restrict__ g
   it.g = lo;
   it.s = G.first + (local - tile * G.count);
   it.x0 = (tile - strip * G.tiles_x) * kBatchTX;
-  it.z0 = strip * kBatchZB;
-  it.z1 = min(it.z0 + kBatchZB, G.nz);
+  it.z0 = strip * ZB;
+  it.z1 = min(it.z0 + ZB, G.nz);
   it.nch = (it.z1 - it.z0 + kBatchU - 1) / kBatchU;
   return it;
 }
 
-template <int R>
+template <int R, int ZB>
 __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
     const BatchGroup* __restrict__ groups, int n_groups, const BatchShot* __restrict__ shots, int total_items,
     int parity, int* err_flag, unsigned long long limit_ns) {
-  using S = BatchSmem<R>;
+  static_assert(ZB % kBatchU == 0 && ZB / kBatchU <= kBatchMaxChunks, "tile height");
+  constexpr int NCH = ZB / kBatchU;
+  using S = BatchSmem<R, ZB>;
   constexpr int TXP = S::TXP, RH = S::RH;
   extern __shared__ __align__(128) float batch_smem[];  // the image [PROWS][TXP]
-  __shared__ __align__(8) uint64_t bars[8];            // one per chunk
+  __shared__ __align__(8) uint64_t bars[NCH];          // one per chunk
   __shared__ int abort_s;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    for (int k = 0; k < 8; ++k) mbar_init(smem_addr(&bars[k]), 1);
+    for (int k = 0; k < NCH; ++k) mbar_init(smem_addr(&bars[k]), 1);
     abort_s = 0;
     fence_barrier_init();
   }
@@ -147,12 +150,12 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
   int t = blockIdx.x;
   BatchItem cur;
   if (t < total_items) {
-    cur = batch_item(groups, n_groups, t);
+    cur = batch_item<ZB>(groups, n_groups, t);
     load_ok(cur, 0, po, kp);
   }
   for (; t < total_items; t += gridDim.x) {
     const int tn = t + gridDim.x;
-    const BatchItem nxt = tn < total_items ? batch_item(groups, n_groups, tn) : cur;
+    const BatchItem nxt = tn < total_items ? batch_item<ZB>(groups, n_groups, tn) : cur;
     const BatchGroup& G = groups[cur.g];
     const int nz = G.nz, nx = G.nx, x0 = cur.x0, z0 = cur.z0, z1 = cur.z1, nch = cur.nch;
     const int sz = int(G.sz);  // a padded field holds fewer than 2^31 elements (checked on the host)
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
   }
   // after a failed wait: let this CTA's own copies land (bounded) before it exits
   if (abort_s && tid == 0)
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < NCH; ++k)
       if (pending & (1u << k)) mbar_wait_bounded(smem_addr(&bars[k]), (phases >> k) & 1u, limit_ns);
 }
 

@@ -86,7 +86,11 @@ def test_batch_reproduces_single_runs(cuda_device):
     b = api.sw_create_batch(grids)
     try:
         assert api.sw_batch_info(b)[0] == 4  # models 1, 2, 3 and the perturbed copy of 1
-        for rep in range(3):  # direct, captured, replayed
+        rows, us = api.sw_batch_get_tile(b)
+        assert rows in (16, 32, 64) and all(t > 0 for t in us) and us[(16, 32, 64).index(rows)] == min(us)
+        # the tuned tile: direct, captured, replayed; then every tile height directly
+        for rep, tile in enumerate((rows, rows, rows, 16, 32, 64)):
+            api.sw_batch_set_tile(b, tile)
             seis = [torch.full((n, len(s.recs)), -1.0, device="cuda:0") if s.recs else None for s in shots]
             fins = [torch.zeros(s.shape, device="cuda:0") for s in shots]
             api.sw_batch_forward(b, n, seis, fins)
@@ -94,6 +98,8 @@ def test_batch_reproduces_single_runs(cuda_device):
                 if s.recs:
                     assert np.array_equal(seis[i].cpu().numpy(), alone[i][0]), (rep, i)
                 assert np.array_equal(fins[i].cpu().numpy(), alone[i][1]), (rep, i)
+        with pytest.raises(api.SimwaveError):
+            api.sw_batch_set_tile(b, 48)
         # a shorter run and host final fields
         fins = [np.zeros(s.shape, np.float32) for s in shots]
         seis = [torch.zeros((n // 2, len(s.recs)), device="cuda:0") if s.recs else None for s in shots]
@@ -186,12 +192,14 @@ def test_batch_all_radii(cuda_device, order):
     b = api.sw_create_batch(grids)
     try:
         assert api.sw_batch_info(b)[0] == 2
-        seis = [torch.zeros((40, len(s.recs)), device="cuda:0") for s in shots]
-        fins = [torch.zeros(s.shape, device="cuda:0") for s in shots]
-        api.sw_batch_forward(b, 40, seis, fins)
-        for i in range(len(shots)):
-            assert np.array_equal(seis[i].cpu().numpy(), alone[i][0])
-            assert np.array_equal(fins[i].cpu().numpy(), alone[i][1])
+        for rows in (16, 32, 64):
+            api.sw_batch_set_tile(b, rows)
+            seis = [torch.zeros((40, len(s.recs)), device="cuda:0") for s in shots]
+            fins = [torch.zeros(s.shape, device="cuda:0") for s in shots]
+            api.sw_batch_forward(b, 40, seis, fins)
+            for i in range(len(shots)):
+                assert np.array_equal(seis[i].cpu().numpy(), alone[i][0])
+                assert np.array_equal(fins[i].cpu().numpy(), alone[i][1])
     finally:
         b.close()
         for g in grids:

@@ -169,10 +169,12 @@ def test_autograd_density_gradient(cuda_device):
 # Gradient error against the FP64 oracle with 16-bit checkpoints (the
 # recomputed segments start from rounded states); bounds from the mantissa
 # widths (8 bits BF16, 11 bits FP16).
-CKPT_TOL = {api.SW_CKPT_BF16: 3e-2, api.SW_CKPT_FP16: 5e-3}
+# BF16 at the 1e-2 bar for compressed snapshots; FP16 and the row-scaled
+# fixed point well inside it (measured 3.5e-3, 3.7e-4, 7.1e-5 on this case)
+CKPT_TOL = {api.SW_CKPT_BF16: 1e-2, api.SW_CKPT_FP16: 2e-3, api.SW_CKPT_I16: 5e-4}
 
 
-@pytest.mark.parametrize("fmt", [api.SW_CKPT_BF16, api.SW_CKPT_FP16])
+@pytest.mark.parametrize("fmt", [api.SW_CKPT_BF16, api.SW_CKPT_FP16, api.SW_CKPT_I16])
 def test_gradient_with_16_bit_checkpoints(cuda_device, fmt):
     n = 60
     w, wav, obs, kw = _setup(3, 8, n, seed=12)
