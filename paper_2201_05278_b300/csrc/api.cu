@@ -118,7 +118,7 @@ struct sw_grid {
   bool starve = false;                               // failure-path test: no tensor copies
   unsigned long long wait_limit_ns = 2000000000ull;  // bound of every mbarrier wait
   int sm_count = 0;
-  CUtensorMap map_halo[2], map_inner[2], map_kappa;
+  CUtensorMap map_halo[2], map_inner[2], map_warm[2], map_kappa;
   // variable density on the pipelined path: D_z, D_y, D_x ln(rho) fields and their maps
   float* glr[3] = {nullptr, nullptr, nullptr};
   CUtensorMap map_g[3];
@@ -322,13 +322,14 @@ void tma_tile(int R, int* tx, int* ty) {
   (void)R;
 }
 
-sw_status make_map(const sw_grid* g, float* base, uint32_t box_x, uint32_t box_y, CUtensorMap* map) {
+sw_status make_map(const sw_grid* g, float* base, uint32_t box_x, uint32_t box_y, CUtensorMap* map,
+                   uint32_t box_z = 1) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return fail(SW_ECUDA, "cuTensorMapEncodeTiled is not available");
   const Layout& L = g->lay;
   cuuint64_t dims[3] = {cuuint64_t(L.pitch), cuuint64_t(L.py), cuuint64_t(L.pz)};
   cuuint64_t strides[2] = {cuuint64_t(L.sy) * 4, cuuint64_t(L.sz) * 4};
-  cuuint32_t box[3] = {box_x, box_y, 1};
+  cuuint32_t box[3] = {box_x, box_y, box_z};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -344,6 +345,7 @@ sw_status build_tma_maps(sw_grid* g) {
   for (int i = 0; i < 2; ++i) {
     SW_TRY(make_map(g, g->u[i], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &g->map_halo[i]));
     SW_TRY(make_map(g, g->u[i], uint32_t(tx), uint32_t(ty), &g->map_inner[i]));
+    SW_TRY(make_map(g, g->u[i], uint32_t(tx), uint32_t(ty), &g->map_warm[i], kTmaWarmPlanes));
   }
   SW_TRY(make_map(g, g->kappa, uint32_t(tx), uint32_t(ty), &g->map_kappa));
   g->tma_ready = true;
@@ -353,11 +355,12 @@ sw_status build_tma_maps(sw_grid* g) {
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // default bound of an mbarrier wait (2 s)
 
 // Tensor maps of one stencil launch: p[n] with halo and interior, p[n-1]
-// interior.
+// interior, p[n] warm-up boxes (kTmaWarmPlanes interior planes).
 struct StepMaps {
   const CUtensorMap* halo;
   const CUtensorMap* inner;
   const CUtensorMap* old;
+  const CUtensorMap* warm;
 };
 
 template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
@@ -379,7 +382,8 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, const StepMaps& m, c
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   const CUtensorMap* gm = VD ? g->map_g : nullptr;  // unused maps: kappa's
-  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, *m.halo, *m.inner, *m.old, g->map_kappa,
+  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, *m.halo, *m.inner, *m.warm, *m.old,
+                   g->map_kappa,
                    VD ? gm[0] : g->map_kappa, VD ? gm[1] : g->map_kappa, VD ? gm[2] : g->map_kappa, a, wk, g->dflag,
                    g->wait_limit_ns);
 }
@@ -436,7 +440,7 @@ void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepM
 
 // The time loop's step: p[n] in u[buf], p[n-1] and p[n+1] in u[buf ^ 1].
 void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStream_t st) {
-  const StepMaps m{&g->map_halo[buf], &g->map_inner[buf], &g->map_inner[buf ^ 1]};
+  const StepMaps m{&g->map_halo[buf], &g->map_inner[buf], &g->map_inner[buf ^ 1], &g->map_warm[buf]};
   launch_stencil_tma_maps(g, a, m, st, g->has_density);
 }
 
@@ -1166,7 +1170,8 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
       SW_CUDA(cudaGetLastError());
     }
   }
-  std::vector<CUtensorMap> halo(static_cast<size_t>(nfields)), inner(static_cast<size_t>(nfields));
+  std::vector<CUtensorMap> halo(static_cast<size_t>(nfields)), inner(static_cast<size_t>(nfields)),
+      warm(static_cast<size_t>(nfields));
   if (tma) {
     int tx, ty;
     tma_tile(g->R, &tx, &ty);
@@ -1174,6 +1179,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     for (int i = nck; i < nck + K + 3; ++i) {  // segment states and psi
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &halo[size_t(i)]));
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &inner[size_t(i)]));
+      SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &warm[size_t(i)], kTmaWarmPlanes));
     }
   }
   auto idx = [&](float* p) { return size_t(std::find(F.begin(), F.end(), p) - F.begin()); };
@@ -1246,7 +1252,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
         SW_CUDA(cudaMemcpyAsync(ck(n / K, 1), pn, fbytes, cudaMemcpyDeviceToDevice, st));
       }
     }
-    const StepMaps m{&g->map_halo[n & 1], &g->map_inner[n & 1], &g->map_inner[(n + 1) & 1]};
+    const StepMaps m{&g->map_halo[n & 1], &g->map_inner[n & 1], &g->map_inner[(n + 1) & 1], &g->map_warm[n & 1]};
     SW_TRY(step(pn, pm, pm, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, rec, syn));
   }
   residual_kernel<<<256, 256, 0, st>>>(syn, obs, res, macc, N, g->n_rec);
@@ -1259,7 +1265,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     nk += 5 + (vd ? 1 : 0) + (src_threads > 0);
     float* p1 = PSI((k + 1) & 1);  // psi[k+1]
     float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
-    const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)]};
+    const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)], &warm[idx(p1)]};
     a.pn = g->at0(p1);
     a.pnm1 = g->at0(p2);
     a.pout = g->at0(p2);
@@ -1321,7 +1327,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
       for (int n = from; n < to; ++n) {
         float* pn = B(cur);
         float* pm = B(cur ^ 1);
-        const StepMaps m{&halo[idx(pn)], &inner[idx(pn)], &inner[idx(pm)]};
+        const StepMaps m{&halo[idx(pn)], &inner[idx(pn)], &inner[idx(pm)], &warm[idx(pn)]};
         SW_TRY(step(pn, pm, pm, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
         cur ^= 1;
       }
@@ -1383,7 +1389,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
       }
       for (int n = k0; n <= k1 - 2; ++n) {
         const int j = n - k0 + 1;
-        const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))]};
+        const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))], &warm[idx(B(j))]};
         SW_TRY(step(B(j), B(j - 1), B(j + 1), tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));
       }
       for (int k = k1; k >= k0 + 1; --k) SW_TRY(adjoint_step(k, B(k - k0)));

@@ -12,8 +12,10 @@
 //     ring, completing on the slot's mbarrier: the centre plane p[n](c) with
 //     an R-row / XH-column halo, p[n-1](c), kappa(c), the interior of the
 //     front plane p[n](c+R) that feeds the register z-queue, and with VD the
-//     three ln(rho) gradient components at plane c.  A tile column
-//     starts with 2R bundles that carry only a front plane (queue warm-up);
+//     three ln(rho) gradient components at plane c.  A tile column starts
+//     with W = ceil(2R / WP) warm-up bundles, each one box of WP interior
+//     planes of p[n] that only fill the z-queue (fewer trips through the
+//     ring than one plane per bundle);
 //   - each thread keeps its columns' 2R+1 planes of p[n] in a register queue
 //     (shifted once per plane); the in-plane neighbours come from the centre
 //     box, each y row of a thread's window read once per plane;
@@ -49,9 +51,13 @@ struct TmaWork {
   int starve;   // failure-path test: issue no copies, so every wait runs into its bound
 };
 
+// Interior planes of p[n] in one warm-up box (its tensor map's box depth).
+constexpr int kTmaWarmPlanes = 4;
+
 // Segment of a CTA's work range: the part of one tile column inside it.
-// Its bundles j = 0 .. len+2R-1 carry front plane zb - R + j and, for
-// j >= 2R, compute plane zb + j - 2R (2R warm-up bundles, then one per plane).
+// Its bundles j = 0 .. len+W-1: for j < W the warm-up box of front planes
+// zb - R + j*WP .. zb - R + j*WP + WP - 1 (those below zb + R enter the
+// queue), for j >= W compute plane zb + j - W with front plane zb + j - W + R.
 __device__ __forceinline__ int segment_len(int u, int u1, int nz) { return min(u1 - u, nz - u % nz); }
 
 template <int R, int TY, int PPT, int NB, bool VD>
@@ -73,6 +79,9 @@ struct TmaConfig {
   static constexpr int I_FLOATS = int((I_BYTES + 127u) / 128u * 128u) / 4;
   static constexpr int NI = VD ? 6 : 3;  // interior boxes: front, p[n-1], kappa (+ d/dz, d/dy, d/dx ln rho)
   static constexpr int SLOT_FLOATS = C_FLOATS + NI * I_FLOATS;
+  static constexpr int WP = kTmaWarmPlanes;      // planes per warm-up bundle
+  static constexpr int W = (2 * R + WP - 1) / WP;  // warm-up bundles per segment
+  static_assert(WP * I_FLOATS <= SLOT_FLOATS, "a warm-up box fills one slot at most");
   static constexpr size_t SMEM = size_t(NB) * SLOT_FLOATS * 4 + size_t(NB) * 8 + size_t(NB) * 4 + 16;
   static_assert((C_FLOATS * 4) % 128 == 0 && (I_FLOATS * 4) % 128 == 0, "TMA destinations must stay 128-byte aligned");
   // tiles past the last row read zero-filled rows (tensor copies clip at the
@@ -94,12 +103,12 @@ struct RingShared {
 template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
 __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     stencil_tma_kernel(const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_f,
-                       const __grid_constant__ CUtensorMap map_o, const __grid_constant__ CUtensorMap map_k,
+                       const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_o, const __grid_constant__ CUtensorMap map_k,
                        const __grid_constant__ CUtensorMap map_gz, const __grid_constant__ CUtensorMap map_gy,
                        const __grid_constant__ CUtensorMap map_gx, const StencilArgs a, const TmaWork wk,
                        int* err_flag, unsigned long long limit_ns) {
   using C = TmaConfig<R, TY, PPT, NB, VD>;
-  constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW, NCW = C::NCW;
+  constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW, NCW = C::NCW, W = C::W, WP = C::WP;
   extern __shared__ __align__(128) unsigned char smem[];
   float* slots = reinterpret_cast<float*>(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(slots + NB * C::SLOT_FLOATS);
@@ -127,8 +136,8 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
   // (one lane); false when it lies past the end of the range.  `mark` > 0
   // is recorded as the number of bundles issued before the copies start.
   auto issue = [&](int slot, int u, int len, int jn, int mark) -> bool {
-    while (jn >= len + 2 * R) {
-      jn -= len + 2 * R;
+    while (jn >= len + W) {
+      jn -= len + W;
       u += len;
       if (u >= u1) return false;
       len = segment_len(u, u1, nz);
@@ -136,13 +145,13 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     if (mark > 0) atomicMax(&ring->issued, mark);
     const int t = u / nz;
     const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
-    const int zf = u % nz + jn;  // padded z of the front plane
     float* sb = slots + slot * C::SLOT_FLOATS;
     const uint32_t bar = full0 + 8u * slot;
-    if (jn < 2 * R) {
-      mbar_arrive_expect_tx(bar, C::I_BYTES);
-      tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
+    if (jn < W) {  // WP front planes from padded z (u % nz) + jn * WP, at the slot's start
+      mbar_arrive_expect_tx(bar, uint32_t(WP) * C::I_BYTES);
+      tma_load_3d(smem_addr(sb), &map_w, x0 + kXOff, y0 + R, u % nz + jn * WP, bar);
     } else {
+      const int zf = u % nz + jn - W + 2 * R;  // padded z of the front plane
       mbar_arrive_expect_tx(bar, C::C_BYTES + uint32_t(C::NI) * C::I_BYTES);
       tma_load_3d(smem_addr(sb), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
       tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
@@ -169,6 +178,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     fence_barrier_init();
     prefetch_tensormap(&map_c);
     prefetch_tensormap(&map_f);
+    prefetch_tensormap(&map_w);
     prefetch_tensormap(&map_o);
     prefetch_tensormap(&map_k);
     if constexpr (VD) {
@@ -252,17 +262,17 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       }
     }
     const int rowoff0 = (y0 + r0) * int(a.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
-    const int nb = len + 2 * R;
+    const int nb = len + W;
 #pragma unroll 1
     for (int j = 0; j < nb; ++j) {
       // damping coefficients of this plane's nodes: per segment outside the
       // z layer, else fetched here, before the wait, so that their latency
       // hides behind it
-      const int z = zb + j - 2 * R;
+      const int z = zb + j - W;
       const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
       const int dz2 = dzl * dzl;
-      const bool zlayer = j >= 2 * R && dz2 != 0;
-      const bool damped = zlayer || (j >= 2 * R && !xy_free);
+      const bool zlayer = j >= W && dz2 != 0;
+      const bool damped = zlayer || (j >= W && !xy_free);
       float2 da[PPT], db[PPT];
       if (zlayer) {
 #pragma unroll
@@ -278,7 +288,20 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
         return;
       }
       const float* S = slots + s * C::SLOT_FLOATS;
-      {
+      if (j < W) {  // warm-up: the planes of the box that lie below zb + R enter the queue
+        const float2* F = reinterpret_cast<const float2*>(S) + r0 * (TX / 2) + lane;
+#pragma unroll
+        for (int pp = 0; pp < WP; ++pp) {
+          if (j * WP + pp < 2 * R) {
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+#pragma unroll
+              for (int kk = 0; kk < QL - 1; ++kk) qz[i][kk] = qz[i][kk + 1];
+              qz[i][QL - 1] = F[pp * (C::I_FLOATS / 2) + i * (TX / 2)];
+            }
+          }
+        }
+      } else {
         const float2* F = reinterpret_cast<const float2*>(S + C::C_FLOATS) + r0 * (TX / 2) + lane;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
@@ -287,7 +310,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
           qz[i][QL - 1] = F[i * (TX / 2)];
         }
       }
-      if (j >= 2 * R) {
+      if (j >= W) {
         const float* cc = S + (r0 + R) * PW + C::XH + 2 * lane;  // centre of output row 0
         const float2* O = reinterpret_cast<const float2*>(S + C::C_FLOATS + C::I_FLOATS) + r0 * (TX / 2) + lane;
         const float2* K = O + C::I_FLOATS / 2;
