@@ -105,6 +105,8 @@ struct sw_grid {
   float* wavelet = nullptr;
   int64_t* tap_off = nullptr;  // source tap table of the pipelined path (n_src * taps)
   float* tap_coef = nullptr;
+  float* tap_pre = nullptr;  // pre-injection coefficients (PreInject), same order
+  int64_t src_d2_max = 0;    // largest squared layer distance of a source window node
   int* rec_first = nullptr;
   float* rec_w = nullptr;
   int4* rec_span = nullptr;  // per receiver: rows with non-zero weight along z and y
@@ -512,8 +514,10 @@ void free_acquisition(sw_grid* g) {
   const size_t ntaps = size_t(g->n_src) * g->lz * g->ly * g->lx;
   dev_free(g, g->tap_off, ntaps * sizeof(int64_t));
   dev_free(g, g->tap_coef, ntaps * sizeof(float));
+  dev_free(g, g->tap_pre, ntaps * sizeof(float));
   g->tap_off = nullptr;
   g->tap_coef = nullptr;
+  g->tap_pre = nullptr;
   dev_free(g, g->src_first, size_t(g->n_src) * 3 * sizeof(int));
   dev_free(g, g->src_w, size_t(g->n_src) * 3 * g->L * sizeof(float));
   dev_free(g, g->rec_first, size_t(g->n_rec) * 3 * sizeof(int));
@@ -818,6 +822,18 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
   g->n_src = n_src;
   g->n_rec = n_rec;
   g->nt = nt;
+  g->src_d2_max = 0;  // the window nodes deepest in the absorbing layers (per axis, a window end)
+  for (int i = 0; i < n_src; ++i) {
+    int64_t d2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (g->ndim == 2 && a == 1) continue;
+      const int lo = g->nbl[2 * a], hi = g->nbl[2 * a + 1];
+      const int64_t n0 = sf[size_t(i) * 3 + a], n1 = n0 + 2 * window_radius - 1;
+      const int64_t d = std::max<int64_t>({lo - n0, n1 - (g->n[a] - 1 - hi), 0});
+      d2 += d * d;
+    }
+    g->src_d2_max = std::max(g->src_d2_max, d2);
+  }
   g->sig_stride = wavelet_per_source ? nt : 0;
   if (n_src > 0) {
     SW_TRY(dev_alloc(g, (void**)&g->src_first, sf.size() * sizeof(int)));
@@ -908,6 +924,12 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   int64_t launches = 0;
   const int src_threads = g->n_src * g->lz * g->ly * g->lx;
   const bool tma = use_tma(g);
+  // pipelined path: each step's sources enter through the level the step
+  // reads as p[n-1] (PreInject), added in the previous step's face launch,
+  // instead of a launch of their own after the stencil
+  double src_a, src_e;  // eta dt at the source window node deepest in the layers
+  damping_coefficients(g->alpha, g->degree, g->dt, g->src_d2_max, &src_a, &src_e);
+  const bool pre_inject = tma && src_threads > 0 && src_e < 0.5;
   // everything the time loop launches, in stream order
   auto enqueue = [&](cudaStream_t st, bool capturing, int64_t* nl) -> sw_status {
   // timing events become real event nodes of a captured graph
@@ -917,11 +939,18 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     if (!g->tap_off) {
       SW_TRY(dev_alloc(g, (void**)&g->tap_off, size_t(src_threads) * sizeof(int64_t)));
       SW_TRY(dev_alloc(g, (void**)&g->tap_coef, size_t(src_threads) * sizeof(float)));
+      SW_TRY(dev_alloc(g, (void**)&g->tap_pre, size_t(src_threads) * sizeof(float)));
     }
     source_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(a.kappa, g->damp, src, f, g->tap_off,
-                                                                         g->tap_coef);
+                                                                         g->tap_coef, g->tap_pre);
     SW_CUDA(cudaGetLastError());
     ++launches;
+    if (pre_inject && n_steps > 0) {  // step 0's sources, into p[-1]
+      inject_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
+          g->at0(g->u[1]), g->tap_off, g->tap_pre, g->lz * g->ly * g->lx, g->n_src, g->wavelet, g->sig_stride, 0);
+      SW_CUDA(cudaGetLastError());
+      ++launches;
+    }
   }
   for (int step = 0; step < n_steps; ++step) {
     float* pn = g->u[step & 1];
@@ -938,7 +967,9 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       launch_stencil(g->R, g->ndim, g->has_density, a, st);
     if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev + 1], st, evflags));
     ++launches;
-    if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
+    if (pre_inject) {
+      // added to p[n-1] before the step (by the previous face launch, or before the loop)
+    } else if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
       launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pout,
                        (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
                        (const float*)g->wavelet, g->sig_stride, step);
@@ -962,7 +993,11 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     if (tma) {
       // the pipelined kernel writes node values only: the face conditions
       // follow, with the receiver samples in the same launch
-      launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st);
+      PreInject pi{};
+      if (pre_inject && step + 1 < n_steps)
+        pi = PreInject{g->at0(pn), g->tap_off, g->tap_pre, g->wavelet, g->lz * g->ly * g->lx, g->n_src, g->sig_stride,
+                       step + 1};
+      launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st, pi);
       ++launches;
     } else if (g->n_rec > 0 && g->ndim == 2) {
       launch_dependent(sample_receivers_grouped_kernel, dim3((grouped_receiver_warps(rec) + 3) / 4), dim3(128), 0,

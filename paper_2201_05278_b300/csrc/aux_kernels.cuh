@@ -117,8 +117,9 @@ __global__ void inject_sources_kernel(float* p, const float* kappa, const float2
 // prod(h), the step-independent part of the Eq. 11 increment, as
 // inject_sources_kernel forms it.  Dirichlet face nodes get offset -1 (never
 // incremented).  No ghost images: the face conditions follow the injection.
+// With tap_pre, also the coefficients of the pre-injection (PreInject).
 __global__ void source_taps_kernel(const float* kappa, const float2* damp, PointSet src, FaceInfo f,
-                                   int64_t* tap_off, float* tap_coef) {
+                                   int64_t* tap_off, float* tap_coef, float* tap_pre) {
   const int taps = src.lz * src.ly * src.lx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= src.count * taps) return;
@@ -140,8 +141,10 @@ __global__ void source_taps_kernel(const float* kappa, const float2* damp, Point
   const int dx = face_distance(x, f.nx, f.nbl[4], f.nbl[5]);
   const int d2 = dz * dz + dy * dy + dx * dx;
   const float ca = d2 ? damp[d2].x : 1.f;
+  const float e = d2 ? damp[d2].y : 0.f;
   tap_off[t] = (dir || wgt == 0.f) ? -1 : idx;
   tap_coef[t] = kappa[idx] * ca * wgt;
+  if (tap_pre) tap_pre[t] = -(kappa[idx] * wgt) / (1.f - e);  // see PreInject (used where e < 1/2 at every tap)
 }
 
 // Eq. 11 from the tap table: p[n+1]_k += coef_k S_s(t_n), one thread per tap.
@@ -436,15 +439,40 @@ __device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int t) {
 // consecutive block ranges: receivers (8 per block) first, so that their
 // longer load chains start early, then z faces, y faces and x faces.
 struct FaceGrid {
-  int rec, z, y, x;  // blocks per part
-  int total() const { return rec + z + y + x; }
+  int rec, z, y, x, pre;  // blocks per part
+  int total() const { return rec + z + y + x + pre; }
+};
+
+// Source injection of the next step, applied to the level it reads as
+// p[n-1]: the update reads p[n-1] at the node only, through
+// p[n+1] = a (2 p - (1 - e) p[n-1] + kappa L), so adding
+// d = kappa_k d_k S(t) / (1 - e_k) there before the step adds
+// kappa_k a_k d_k S(t) to p[n+1]_k, the Eq. 11 term, up to rounding.
+// `coef` holds -kappa_k d_k / (1 - e_k) (tap table order, offsets as the
+// tap table's); count = 0: nothing to do.
+struct PreInject {
+  float* p;  // the level stored as p[n-1] of the next step (node values)
+  const int64_t* off;
+  const float* coef;
+  const float* sig;
+  int taps, count, sig_stride, step;
 };
 
 template <int R>
-__global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg) {
+__global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg,
+                                       PreInject pi) {
   griddep_launch_dependents();
   griddep_wait();  // p[n+1] of the stencil and the injection launched before
   int b = blockIdx.x;
+  if (b < fg.pre) {  // a different level from the one the other parts touch
+    const int t = b * blockDim.x + threadIdx.x;
+    if (t < pi.count * pi.taps) {
+      const int64_t k = pi.off[t];
+      if (k >= 0) atomicAdd(&pi.p[k], pi.coef[t] * pi.sig[int64_t(t / pi.taps) * pi.sig_stride + pi.step]);
+    }
+    return;
+  }
+  b -= fg.pre;
   if (b < fg.rec) {
     const int r = b * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r < rec.count) sample_receiver(p, rec, f, out, step, r, threadIdx.x & 31, true);
@@ -485,26 +513,28 @@ inline void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
 }
 
 // Face conditions of p (3D, pipelined stencil) and, if rec.count > 0, the
-// receiver samples of this step, in one launch of 256-thread blocks.
+// receiver samples of this step, and, if pi.count > 0, the pre-injection of
+// the next step's sources, in one launch of 256-thread blocks.
 inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const PreInject& pi = PreInject{}) {
   FaceGrid fg;
+  fg.pre = (pi.count * pi.taps + 255) / 256;
   fg.rec = (rec.count + 7) / 8;
   fg.z = int((2 * int64_t(f.ny) * f.nx + 255) / 256);
   fg.y = int((2 * int64_t(f.nz) * f.nx + 255) / 256);
   fg.x = int((2 * int64_t(f.nz) * f.ny * R + 255) / 256);
   const unsigned grid = unsigned(fg.total());
   switch (R) {
-    case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 2: launch_dependent(face_conditions_kernel<2>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 3: launch_dependent(face_conditions_kernel<3>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 4: launch_dependent(face_conditions_kernel<4>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 5: launch_dependent(face_conditions_kernel<5>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 6: launch_dependent(face_conditions_kernel<6>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 7: launch_dependent(face_conditions_kernel<7>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 8: launch_dependent(face_conditions_kernel<8>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 9: launch_dependent(face_conditions_kernel<9>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
-    case 10: launch_dependent(face_conditions_kernel<10>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg); break;
+    case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 2: launch_dependent(face_conditions_kernel<2>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 3: launch_dependent(face_conditions_kernel<3>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 4: launch_dependent(face_conditions_kernel<4>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 5: launch_dependent(face_conditions_kernel<5>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 6: launch_dependent(face_conditions_kernel<6>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 7: launch_dependent(face_conditions_kernel<7>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 8: launch_dependent(face_conditions_kernel<8>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 9: launch_dependent(face_conditions_kernel<9>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
+    case 10: launch_dependent(face_conditions_kernel<10>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
     default: break;
   }
 }

@@ -81,6 +81,41 @@ def test_tma_kernel_many_segments(cuda_device):
     assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
 
 
+@pytest.mark.parametrize("damp_scale", [1.0, 100.0])
+def test_sources_in_the_absorbing_layers(cuda_device, damp_scale):
+    """Sources whose windows reach into the absorbing layers, on the pipelined path.
+    With eta dt below 1/2 at every source window node (damp_scale 1) each step's
+    source increments enter through the level the step reads as p[n-1], divided
+    by 1 - eta dt, inside the previous step's face launch (two launches per
+    step); with damping strong enough to pass 1/2 there (damp_scale 100),
+    through a launch of their own after the stencil (three per step).  Both
+    match the oracle (Eq. 7, Eq. 11)."""
+    import dataclasses
+    w = small_case(3, 8, False, seed=5, n_steps=70)
+    h = w.spacing
+    # off-grid sources: one in the x- layer (node 3.5 of a 4-cell layer), one in
+    # the z+ layer (node nz - 4.5 of 4 cells), one in the physical box; the
+    # deepest window node of each lies 4 cells into a layer (window radius 4)
+    src = np.array([[0.5 * (w.shape[0] - 5) * h[0], 0.5 * (w.shape[1] - 9) * h[1], -0.5 * h[2]],
+                    [(w.shape[0] - 4.5) * h[0], 0.43 * (w.shape[1] - 9) * h[1], 0.37 * (w.shape[2] - 11) * h[2]],
+                    [0.3 * (w.shape[0] - 5) * h[0], 0.6 * (w.shape[1] - 9) * h[1], 0.55 * (w.shape[2] - 11) * h[2]]])
+    w = dataclasses.replace(w, src_pos=src, damp_alpha=w.damp_alpha * damp_scale)
+    assert w.window_radius == 4
+    e_src = w.damp_alpha * 4.0 ** w.damp_degree * w.dt  # eta dt = alpha d^p dt, d in cells
+    assert (e_src < 0.5) == (damp_scale == 1.0)
+    s_gpu, p_gpu, prof = run_gpu(w, profile=True, expect_variant=api.SW_STENCIL_TMA)
+    s_ref, p_ref = run_oracle(w)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    # per forward: the tap table, the final-field copy and (first path) step 0's
+    # sources into p[-1]; per step: the stencil, the face launch (and the injection)
+    if damp_scale == 1.0:
+        assert prof[2] == 2 * w.n_steps + 3
+    else:
+        assert prof[2] == 3 * w.n_steps + 2
+
+
 def test_host_and_device_buffers_agree(cuda_device):
     w = small_case(3, 8, True, seed=3, n_steps=30)
     s_dev, p_dev = run_gpu(w, device_io=True)
