@@ -16,10 +16,12 @@
 // into shared memory with 1D bulk copies, one mbarrier per chunk of kBatchU
 // rows, and every thread computes a chunk as soon as its barrier completes,
 // so that an item's reads are all in flight at once; p[n-1] and kappa are
-// loaded into registers a chunk ahead (across items too).  A thread owns one
-// column and keeps its z-neighbours in a register queue; the x-neighbours
-// come from the shared image.  The arithmetic is the single-grid 2D kernel's
-// (laplacian_2d, leapfrog_update), so a batched shot reproduces its
+// loaded into registers a chunk ahead (across items too).  A thread owns two
+// adjacent columns, handled as a pair with packed FP32x2 arithmetic, and
+// keeps their z-neighbours in a register queue; the x-neighbours come from
+// the shared image as 64-bit pairs.  Per column the arithmetic is the
+// single-grid 2D kernel's (laplacian_2d, leapfrog_update: the same IEEE
+// operations in the same order), so a batched shot reproduces its
 // single-grid run bit for bit.
 #pragma once
 
@@ -30,8 +32,8 @@
 
 namespace sw {
 
-constexpr int kBatchTX = 128;       // columns per tile
-constexpr int kBatchThreads = 128;  // one column per thread
+constexpr int kBatchTX = 128;      // columns per tile
+constexpr int kBatchThreads = 64;  // two adjacent columns per thread
 constexpr int kBatchZBs[3] = {16, 32, 64};  // tile heights the tuner tries
 constexpr int kBatchU = 4;     // rows per register-queue chunk
 
@@ -110,8 +112,11 @@ __device__ __forceinline__ BatchItem batch_item(const BatchGroup* __restrict__ g
   return it;
 }
 
+// Radii up to 4: at most 128 registers, so that eight CTAs fit an SM (229
+// against 208 Gpts/s for the uncapped 140 registers and seven CTAs on the
+// order-8 batch; a few bytes spill); larger radii run uncapped.
 template <int R, int ZB>
-__global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
+__global__ void __launch_bounds__(kBatchThreads, R <= 4 ? 8 : 1) batch_stencil_2d_kernel(
     const BatchGroup* __restrict__ groups, int n_groups, const BatchShot* __restrict__ shots, int total_items,
     int parity, int* err_flag, unsigned long long limit_ns) {
   static_assert(ZB % kBatchU == 0 && ZB / kBatchU <= kBatchMaxChunks, "tile height");
@@ -131,22 +136,24 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
   unsigned phases = 0;   // parity of the next phase of every barrier
   unsigned pending = 0;  // barriers armed and not yet seen complete
 
-  // p[n-1] and kappa of a thread's column for one chunk (rows past z1 are not read)
-  auto load_ok = [&](const BatchItem& it, int k, float* dpo, float* dkp) {
+  // p[n-1] and kappa of a thread's column pair for one chunk (rows past z1
+  // are not read; columns past nx lie in the row padding and are not stored)
+  auto load_ok = [&](const BatchItem& it, int k, float2* dpo, float2* dkp) {
     const BatchGroup& G = groups[it.g];
     const int sz = int(G.sz);
-    const float* ob = shots[it.s].u[parity ^ 1] + it.x0 + tid;
-    const float* kb = G.kappa + it.x0 + tid;
+    const float* ob = shots[it.s].u[parity ^ 1] + it.x0 + 2 * tid;
+    const float* kb = G.kappa + it.x0 + 2 * tid;
     const int z = it.z0 + k * kBatchU;
 #pragma unroll
     for (int u = 0; u < kBatchU; ++u) {
       const bool in = z + u < it.z1;
-      dpo[u] = in ? ob[(z + u) * sz] : 0.f;
-      dkp[u] = in ? __ldg(kb + (z + u) * sz) : 0.f;
+      dpo[u] = in ? *reinterpret_cast<const float2*>(ob + (z + u) * sz) : make_float2(0.f, 0.f);
+      dkp[u] = in ? __ldg(reinterpret_cast<const float2*>(kb + (z + u) * sz)) : make_float2(0.f, 0.f);
     }
   };
 
-  float po[kBatchU], kp[kBatchU], npo[kBatchU] = {}, nkp[kBatchU] = {};
+  constexpr int H = (R + 1) / 2;  // float2 loads each side for the x neighbours
+  float2 po[kBatchU], kp[kBatchU], npo[kBatchU] = {}, nkp[kBatchU] = {};
   int t = blockIdx.x;
   BatchItem cur;
   if (t < total_items) {
@@ -177,39 +184,83 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
       }
     }
 
-    const int x = x0 + tid;
-    const bool act = x < nx;
-    float cz[R + 1], cx[R + 1];
+    const int x = x0 + 2 * tid;  // columns x (.x of a pair) and x + 1 (.y)
+    const bool act_a = x < nx, act_b = x + 1 < nx;
+    float2 cz[R + 1], cx[R + 1];
 #pragma unroll
     for (int j = 0; j <= R; ++j) {
-      cz[j] = G.cz[j];
-      cx[j] = G.cx[j];
+      cz[j] = make_float2(G.cz[j], G.cz[j]);
+      cx[j] = make_float2(G.cx[j], G.cx[j]);
     }
     // per-column constants: damping distance (0 past the grid, where the
     // damping table ends), Dirichlet column, x-face images
-    const int dx = act ? layer_distance(x, nx, G.nbl[2], G.nbl[3]) : 0;
-    const int dx2 = dx * dx;
+    const int dxa = act_a ? layer_distance(x, nx, G.nbl[2], G.nbl[3]) : 0;
+    const int dxb = act_b ? layer_distance(x + 1, nx, G.nbl[2], G.nbl[3]) : 0;
+    const int dx2a = dxa * dxa, dx2b = dxb * dxb;
     const int bz0 = G.bc[0], bz1 = G.bc[1], bx0 = G.bc[2], bx1 = G.bc[3];
-    const bool xdir = (x == 0 && bx0 == kBcDirichlet) || (x == nx - 1 && bx1 == kBcDirichlet);
-    const int xr = nx - 1 - x;
-    const bool xm_lo = bx0 != kBcNone && x >= 1 && x <= R;
-    const bool xm_hi = bx1 != kBcNone && xr >= 1 && xr <= R;
+    const bool xdir_a = (x == 0 && bx0 == kBcDirichlet) || (x == nx - 1 && bx1 == kBcDirichlet);
+    const bool xdir_b = x + 1 == nx - 1 && bx1 == kBcDirichlet;
+    const int xra = nx - 1 - x, xrb = xra - 1;
+    const bool xm_lo_a = bx0 != kBcNone && x >= 1 && x <= R, xm_lo_b = bx0 != kBcNone && x + 1 <= R;
+    const bool xm_hi_a = bx1 != kBcNone && xra >= 1 && xra <= R, xm_hi_b = bx1 != kBcNone && xrb >= 1 && xrb <= R;
+    const bool xm_any = (xm_lo_a || xm_lo_b || xm_hi_a || xm_hi_b) && act_a;
     const float xs_lo = bx0 == kBcDirichlet ? -1.f : 1.f, xs_hi = bx1 == kBcDirichlet ? -1.f : 1.f;
     const int nbz0 = G.nbl[0], nbz1 = G.nbl[1];
     const float2* damp = G.damp;
-    // damping of this column on rows outside the z layers
-    float ca_x = 1.f, e_x = 0.f;
-    if (dx2 != 0) {
-      const float2 c = __ldg(&damp[dx2]);
-      ca_x = c.x;
-      e_x = c.y;
+    // damping of these columns on rows outside the z layers
+    float2 ca_x = make_float2(1.f, 1.f), e_x = make_float2(0.f, 0.f);
+    if (dx2a != 0) {
+      const float2 c = __ldg(&damp[dx2a]);
+      ca_x.x = c.x;
+      e_x.x = c.y;
     }
+    if (dx2b != 0) {
+      const float2 c = __ldg(&damp[dx2b]);
+      ca_x.y = c.x;
+      e_x.y = c.y;
+    }
+    // node values of a row pair into p[n+1]: the pair, or column x alone at a
+    // ragged edge, then the x-face images of the columns that have one
+    auto put = [&](float* o, float2 v) {
+      if (act_b) *reinterpret_cast<float2*>(o) = v;
+      else if (act_a) o[0] = v.x;
+      if (xm_any) {
+        if (xm_lo_a) o[-2 * x] = xs_lo * v.x;
+        if (xm_lo_b) o[1 - 2 * (x + 1)] = xs_lo * v.y;
+        if (xm_hi_a) o[2 * xra] = xs_hi * v.x;
+        if (xm_hi_b && act_b) o[1 + 2 * xrb] = xs_hi * v.y;
+      }
+    };
+    // the Eq. 9 Laplacian of row u of the chunk for both columns, in the
+    // order of laplacian_2d: z and x terms alternate in one FMA chain
+    const float* col = batch_smem + RH + 2 * tid;  // this thread's columns of the image
+    float2 q[2 * R + kBatchU];  // p[n] of rows z - R .. z + R + U - 1 of the two columns
+    auto lap_row = [&](int rz, int u) {
+      const float* row = col + (rz + u + R) * TXP;
+      float2 w[2 * H + 1];  // columns x-2H .. x+1+2H, as pairs
+#pragma unroll
+      for (int mm = -H; mm <= H; ++mm)
+        w[mm + H] = (mm == 0) ? q[u + R] : *reinterpret_cast<const float2*>(row + 2 * mm);
+      const float2 pc = q[u + R];
+      const float2 p2 = f2_add(pc, pc);  // 2 p, exactly
+      float2 lap = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        lap = f2_fma(cz[j], f2_sub(f2_add(q[u + R + j], q[u + R - j]), p2), lap);
+        float2 xs;  // (x+j) + (x-j) for both columns
+        if (j % 2 == 0) {
+          xs = f2_add(w[H + j / 2], w[H - j / 2]);
+        } else {  // odd offsets straddle the pairs: two scalar adds into one pair
+          xs = make_float2(w[H + (j - 1) / 2].y + w[H - (j + 1) / 2].y, w[H + (j + 1) / 2].x + w[H - (j - 1) / 2].x);
+        }
+        lap = f2_fma(cx[j], f2_sub(xs, p2), lap);
+      }
+      return lap;
+    };
     // rows with nothing special along z: no z-face image, not a Dirichlet
     // face, outside the z absorbing layers
     const int plain_lo = max(R + 1, nbz0), plain_hi = min(nz - 2 - R, nz - 1 - nbz1);
-    const float* col = batch_smem + RH + tid;  // this thread's column of the image
-    float* out = pout + tid;
-    float q[2 * R + kBatchU];  // p[n] of rows z - R .. z + R + U - 1 of this column
+    float* out = pout + 2 * tid;
     for (int k = 0; k < nch; ++k) {
       // the next chunk's p[n-1] and kappa (the next item's first chunk after the last)
       if (k + 1 < nch) load_ok(cur, k + 1, npo, nkp);
@@ -228,29 +279,24 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
         const int rz = k * kBatchU;  // image row of p for z - R
         if (k == 0) {
 #pragma unroll
-          for (int j = 0; j < 2 * R; ++j) q[j] = col[j * TXP];
+          for (int j = 0; j < 2 * R; ++j) q[j] = *reinterpret_cast<const float2*>(col + j * TXP);
         }
 #pragma unroll
-        for (int u = 0; u < kBatchU; ++u) q[2 * R + u] = col[(rz + 2 * R + u) * TXP];  // rows past z1 + R unused
-        if (act) {
+        for (int u = 0; u < kBatchU; ++u)  // rows past z1 + R unused
+          q[2 * R + u] = *reinterpret_cast<const float2*>(col + (rz + 2 * R + u) * TXP);
+        if (act_a) {
           if (z >= plain_lo && z + kBatchU - 1 <= plain_hi && z + kBatchU <= z1) {
             // the common case: a whole chunk of plain rows
             float* o = out + z * sz;
 #pragma unroll
             for (int u = 0; u < kBatchU; ++u) {
-              const float* row = col + (rz + u + R) * TXP;
-              float qx[2 * R + 1];
-              qx[R] = q[u + R];
-#pragma unroll
-              for (int j = 1; j <= R; ++j) {
-                qx[R + j] = row[j];
-                qx[R - j] = row[-j];
-              }
-              float pnew = leapfrog_update(q[u + R], po[u], kp[u], laplacian_2d<R>(q + u, qx, cz, cx), ca_x, e_x);
-              if (xdir) pnew = 0.f;
-              o[0] = pnew;
-              if (xm_lo) o[-2 * x] = xs_lo * pnew;
-              if (xm_hi) o[2 * xr] = xs_hi * pnew;
+              const float2 lap = lap_row(rz, u);
+              const float2 pc = q[u + R];
+              // leapfrog_update for both columns
+              float2 pnew = f2_mul(ca_x, f2_add(pc, f2_fma(kp[u], lap, f2_fma(e_x, po[u], f2_sub(pc, po[u])))));
+              if (xdir_a) pnew.x = 0.f;
+              if (xdir_b) pnew.y = 0.f;
+              put(o, pnew);
               o += sz;
             }
           } else {
@@ -258,30 +304,31 @@ __global__ void __launch_bounds__(kBatchThreads) batch_stencil_2d_kernel(
             for (int u = 0; u < kBatchU; ++u) {
               const int zu = z + u;
               if (zu >= z1) break;
-              const float* row = col + (rz + u + R) * TXP;
-              float qx[2 * R + 1];
-              qx[R] = q[u + R];
-#pragma unroll
-              for (int j = 1; j <= R; ++j) {
-                qx[R + j] = row[j];
-                qx[R - j] = row[-j];
-              }
-              const float lap = laplacian_2d<R>(q + u, qx, cz, cx);
+              const float2 lap = lap_row(rz, u);
               const int dz = layer_distance(zu, nz, nbz0, nbz1);
-              const int d2 = dz * dz + dx2;
-              float ca = 1.f, e = 0.f;
-              if (d2 != 0) {
-                const float2 c = __ldg(&damp[d2]);
-                ca = c.x;
-                e = c.y;
+              const int d2a = dz * dz + dx2a, d2b = dz * dz + dx2b;
+              float2 ca = make_float2(1.f, 1.f), e = make_float2(0.f, 0.f);
+              if (d2a != 0) {
+                const float2 c = __ldg(&damp[d2a]);
+                ca.x = c.x;
+                e.x = c.y;
               }
-              float pnew = leapfrog_update(q[u + R], po[u], kp[u], lap, ca, e);
-              if (xdir || (zu == 0 && bz0 == kBcDirichlet) || (zu == nz - 1 && bz1 == kBcDirichlet)) pnew = 0.f;
+              if (d2b != 0) {
+                const float2 c = __ldg(&damp[d2b]);
+                ca.y = c.x;
+                e.y = c.y;
+              }
+              const float2 pc = q[u + R];
+              float2 pnew = f2_mul(ca, f2_add(pc, f2_fma(kp[u], lap, f2_fma(e, po[u], f2_sub(pc, po[u])))));
+              const bool zdir = (zu == 0 && bz0 == kBcDirichlet) || (zu == nz - 1 && bz1 == kBcDirichlet);
+              if (xdir_a || zdir) pnew.x = 0.f;
+              if (xdir_b || zdir) pnew.y = 0.f;
               float* o = out + zu * sz;
-              o[0] = pnew;
-              if (xm_lo) o[-2 * x] = xs_lo * pnew;
-              if (xm_hi) o[2 * xr] = xs_hi * pnew;
-              if (zu <= R || zu >= nz - 1 - R) mirror_ghosts<R>(o, 0, zu, nz, sz, bz0, bz1, pnew);
+              put(o, pnew);
+              if (zu <= R || zu >= nz - 1 - R) {
+                mirror_ghosts<R>(o, 0, zu, nz, sz, bz0, bz1, pnew.x);
+                if (act_b) mirror_ghosts<R>(o, 1, zu, nz, sz, bz0, bz1, pnew.y);
+              }
             }
           }
         }
