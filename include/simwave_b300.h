@@ -199,15 +199,24 @@ sw_status sw_get_dt(const sw_grid* g, double* dt);
 sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
 
 /*
- * Stencil kernel variant.  Two CUDA implementations of the same update:
+ * Stencil kernel variant.  CUDA implementations of the same update (Eq. 7):
  * SW_STENCIL_AUTO picks the TMA-pipelined persistent kernel for 3D
- * constant-density grids and the shared-memory-plane kernel otherwise;
- * SW_STENCIL_PLAIN forces the latter; SW_STENCIL_TMA asks for the former
- * (3D only, else SW_EINVAL; cases it does not cover still use the plain
- * kernel).  sw_get_stencil_variant reports the kernel sw_forward will launch
- * for the current model.
+ * constant-density grids, the cluster-resident run for 2D grids that fit
+ * it, and the per-step plain kernels otherwise; SW_STENCIL_PLAIN forces the
+ * per-step plain kernels; SW_STENCIL_TMA asks for the pipelined kernel (3D
+ * only, else SW_EINVAL; cases it does not cover still use the plain
+ * kernel).  SW_STENCIL_CLUSTER asks for the cluster-resident run (2D only,
+ * else SW_EINVAL): the whole forward run in one launch of one thread-block
+ * cluster (up to 16 CTAs, one per SM) whose shared memory holds both
+ * levels and kappa, for 2D grids of constant density whose rows fit (two
+ * levels of ceil(nz / C) + 2R rows of nx + 2R floats plus ceil(nz / C) rows
+ * of kappa per CTA, at most the device's per-block shared memory), without
+ * distributed forcing or snapshot frames; other cases use the plain
+ * kernels.  It gives the same values as the plain 2D kernels bit for bit.
+ * sw_get_stencil_variant reports the kernel sw_forward will launch for the
+ * current model.
  */
-enum { SW_STENCIL_AUTO = 0, SW_STENCIL_PLAIN = 1, SW_STENCIL_TMA = 2 };
+enum { SW_STENCIL_AUTO = 0, SW_STENCIL_PLAIN = 1, SW_STENCIL_TMA = 2, SW_STENCIL_CLUSTER = 3 };
 sw_status sw_set_stencil_variant(sw_grid* g, int variant);
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
 

@@ -16,6 +16,7 @@
 #include "aux_kernels.cuh"
 #include "host_setup.h"
 #include "layout.h"
+#include "cluster2d.cuh"
 #include "stencil_plain.cuh"
 #include "stencil_tma.cuh"
 
@@ -497,6 +498,89 @@ bool use_tma(const sw_grid* g) {
          n[1] > m && n[2] > m && items < (int64_t(1) << 31) && lines < (int64_t(1) << 31);
 }
 
+// ---- cluster-resident 2D forward run -----------------------------------------
+
+using ClusterFn = void (*)(const ClusterRun);
+
+ClusterFn cluster_kernel(int R) {
+  switch (R) {
+    case 1: return stencil_2d_cluster_kernel<1>;
+    case 2: return stencil_2d_cluster_kernel<2>;
+    case 3: return stencil_2d_cluster_kernel<3>;
+    case 4: return stencil_2d_cluster_kernel<4>;
+    case 5: return stencil_2d_cluster_kernel<5>;
+    case 6: return stencil_2d_cluster_kernel<6>;
+    case 7: return stencil_2d_cluster_kernel<7>;
+    case 8: return stencil_2d_cluster_kernel<8>;
+    case 9: return stencil_2d_cluster_kernel<9>;
+    case 10: return stencil_2d_cluster_kernel<10>;
+    default: return nullptr;
+  }
+}
+
+// Launch shape of the cluster-resident run: CTAs in the cluster, rows per
+// band, shared row length and bytes per CTA.
+struct ClusterShape {
+  int C = 0, B = 0, W = 0;
+  size_t smem = 0;
+};
+
+// Can the whole run of this grid live in one cluster's shared memory?  2D,
+// constant density, no distributed forcing and no snapshot frames (those
+// run per step); the largest cluster (16, 8, 4 or 2 CTAs) whose bands fit
+// the per-CTA shared memory and that the device can place.  Every band
+// holds at least one row.
+bool use_cluster(const sw_grid* g, ClusterShape* out) {
+  if (g->ndim != 2 || g->has_density || g->n_force > 0 || g->snapshots || g->variant == SW_STENCIL_PLAIN) return false;
+  if (int64_t(g->n_src) * g->lz * g->lx > kClusterThreads) return false;  // one source tap per thread
+  const int R = g->R;
+  const int64_t nz = g->n[0], nx = g->n[2];
+  if (nz <= 2 * R + 1 || nx <= 2 * R + 1 || nx > (int64_t(1) << 20)) return false;
+  ClusterFn fn = cluster_kernel(R);
+  if (!fn) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int W = cluster_row_len(int(nx), R);
+  for (int C = kClusterMaxCtas; C >= 2; C /= 2) {
+    const int B = int((nz + C - 1) / C);
+    const int Ce = int((nz + B - 1) / B);  // every band non-empty
+    const size_t smem = size_t(cluster_smem_floats(B, int(nx), R)) * sizeof(float);
+    if (smem > size_t(optin)) continue;
+    if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(Ce));
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(Ce);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (clusters < 1) continue;
+    out->C = Ce;
+    out->B = B;
+    out->W = W;
+    out->smem = smem;
+    return true;
+  }
+  return false;
+}
+
 PointSet point_set(const sw_grid* g, bool src) {
   PointSet p;
   p.first = src ? g->src_first : g->rec_first;
@@ -915,7 +999,10 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
 
   StencilArgs a = stencil_args(g);
   const PointSet src = point_set(g, true), rec = point_set(g, false);
-  const int timed = g->profiling ? (n_steps + g->profiling - 1) / g->profiling : 0;  // launches timed
+  // small 2D grids: the whole run in one launch of one cluster (timed as one launch)
+  ClusterShape cshape;
+  const bool cluster = n_steps > 0 && use_cluster(g, &cshape);
+  const int timed = !g->profiling ? 0 : (cluster ? 1 : (n_steps + g->profiling - 1) / g->profiling);  // launches timed
   if (timed && g->events.size() < size_t(2 * timed)) {
     size_t old = g->events.size();
     g->events.resize(size_t(2 * timed));
@@ -1020,7 +1107,47 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   return SW_OK;
   };
   const sw_grid::ForwardKey key{n_steps, seis_dev, g->profiling, tma, g->config_gen};
-  if (n_steps > 0 && g->graph && g->graph_key == key) {
+  if (cluster) {
+    ClusterRun run;
+    run.u[0] = g->at0(g->u[0]);
+    run.u[1] = g->at0(g->u[1]);
+    run.kappa = a.kappa;
+    run.damp = g->damp;
+    run.f = f;
+    run.B = cshape.B;
+    run.W = cshape.W;
+    for (int j = 0; j <= kMaxR; ++j) {
+      run.cz[j] = a.cz[j];
+      run.cx[j] = a.cx[j];
+    }
+    run.src = src;
+    run.rec = rec;
+    run.sig = g->wavelet;
+    run.sig_stride = g->sig_stride;
+    run.seis = g->n_rec > 0 ? seis_dev : nullptr;
+    run.n_steps = n_steps;
+    {  // receivers in registers: one pass of the cluster's warps, at most kClusterRecRows rows per window
+      const int per_warp = g->lx <= 8 ? 4 : (g->lx <= 16 ? 2 : 1);
+      const int rows = g->rec_span ? g->rec_rows_max : g->lz;
+      run.rec_fast = g->n_rec <= cshape.C * (kClusterThreads / 32) * per_warp && rows <= kClusterRecRows ? 1 : 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(cshape.C));
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = cshape.smem;
+    cfg.stream = g->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(cshape.C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (timed) SW_CUDA(cudaEventRecord(g->events[0], g->stream));
+    SW_CUDA(cudaLaunchKernelEx(&cfg, cluster_kernel(g->R), run));
+    if (timed) SW_CUDA(cudaEventRecord(g->events[1], g->stream));
+    launches = 1;
+  } else if (n_steps > 0 && g->graph && g->graph_key == key) {
     SW_CUDA(cudaGraphLaunch(g->graph, g->stream));
     launches = g->graph_launches;
   } else if (n_steps > 0 && g->last_key_valid && g->last_key == key) {
@@ -1075,7 +1202,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
                             g->stream));
   SW_TRY(check_device_flag(g));
   g->kernel_launches = launches;
-  g->stencil_launches = timed;
+  g->stencil_launches = cluster && timed ? n_steps : timed;  // the cluster run's time counts per time step
   g->stencil_ms = 0.0;
   for (int i = 0; i < timed; ++i) {
     float ms = 0.f;
@@ -1486,9 +1613,11 @@ sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out) {
 
 sw_status sw_set_stencil_variant(sw_grid* g, int variant) {
   if (!g) return fail(SW_EINVAL, "NULL grid");
-  if (variant != SW_STENCIL_AUTO && variant != SW_STENCIL_PLAIN && variant != SW_STENCIL_TMA)
+  if (variant != SW_STENCIL_AUTO && variant != SW_STENCIL_PLAIN && variant != SW_STENCIL_TMA &&
+      variant != SW_STENCIL_CLUSTER)
     return fail(SW_EINVAL, "unknown stencil variant %d", variant);
   if (variant == SW_STENCIL_TMA && g->ndim != 3) return fail(SW_EINVAL, "the pipelined stencil is 3D only");
+  if (variant == SW_STENCIL_CLUSTER && g->ndim != 2) return fail(SW_EINVAL, "the cluster-resident run is 2D only");
   g->variant = variant;
   ++g->config_gen;
   return SW_OK;
@@ -1504,7 +1633,8 @@ sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_l
 
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant) {
   if (!g || !variant) return fail(SW_EINVAL, "NULL argument");
-  *variant = use_tma(g) ? SW_STENCIL_TMA : SW_STENCIL_PLAIN;
+  ClusterShape cs;
+  *variant = use_tma(g) ? SW_STENCIL_TMA : (use_cluster(g, &cs) ? SW_STENCIL_CLUSTER : SW_STENCIL_PLAIN);
   return SW_OK;
 }
 

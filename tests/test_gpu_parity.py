@@ -70,6 +70,61 @@ def test_3d_both_stencil_kernels(cuda_device, order, density):
         assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
 
 
+@pytest.mark.parametrize("order,bcs", [(2, 0), (8, 0), (8, 1), (14, 1), (20, 0)])
+def test_2d_cluster_run_matches_the_plain_kernels(cuda_device, order, bcs):
+    """The cluster-resident 2D run (the whole forward in one launch of one
+    thread-block cluster, chosen automatically for 2D grids that fit) gives the
+    plain per-step 2D kernels' seismogram and final field bit for bit, with
+    sources on faces and in the absorbing layers, and matches the oracle."""
+    import dataclasses
+    w = small_case(2, order, False, seed=40 + order, n_steps=70)
+    if bcs == 1:  # every face kind, sources next to a Dirichlet and a Neumann face
+        h = w.spacing
+        src = np.array([[0.7 * h[0], 0.4 * (w.shape[1] - 11) * h[1]],
+                        [0.5 * (w.shape[0] - 7) * h[0], -0.5 * h[1]]])
+        w = dataclasses.replace(w, bc=["null_dirichlet", "null_neumann", "null_neumann", "null_dirichlet"],
+                                nbl=[3, 0, 4, 6], src_pos=src)
+    s_pl, p_pl = run_gpu(w, variant=api.SW_STENCIL_PLAIN, expect_variant=api.SW_STENCIL_PLAIN)
+    s_cl, p_cl, prof = run_gpu(w, profile=True, expect_variant=api.SW_STENCIL_CLUSTER)
+    assert np.array_equal(s_cl, s_pl) and np.array_equal(p_cl, p_pl)
+    assert prof[2] == 2  # the run and the final-field copy
+    s_ref, p_ref = run_oracle(w)
+    assert np.abs(s_ref).max() > 0
+    assert rel_l2(s_cl, s_ref) <= FP32_SEIS_TOL
+    assert rel_l2(p_cl, p_ref) <= FP32_SEIS_TOL
+
+
+def test_2d_cluster_run_edge_cases(cuda_device):
+    """Zero and one step, host buffers, and a grid whose bands hold one row each."""
+    import dataclasses
+    w = small_case(2, 8, False, seed=3, n_steps=30)
+    for n in (0, 1):
+        s, p = run_gpu(w, n_steps=n, variant=api.SW_STENCIL_CLUSTER)
+        s2, p2 = run_gpu(w, n_steps=n, variant=api.SW_STENCIL_PLAIN)
+        assert np.array_equal(s, s2) and np.array_equal(p, p2)
+    s, p = run_gpu(w, device_io=False, expect_variant=api.SW_STENCIL_CLUSTER)
+    s2, p2 = run_gpu(w, variant=api.SW_STENCIL_PLAIN)
+    assert np.array_equal(s, s2) and np.array_equal(p, p2)
+    # 14 rows on up to 16 CTAs: one row per band, every halo row from other CTAs
+    vel = w.velocity[:14, :]
+    h = w.spacing
+    small = dataclasses.replace(w, shape=(14, w.shape[1]), velocity=vel, nbl=[0, 2, 5, 7],
+                                src_pos=np.array([[5.3 * h[0], 11.6 * h[1]]]),
+                                rec_pos=np.array([[2.0 * h[0], 3.3 * h[1]], [6.5 * h[0], 20.0 * h[1]]]),
+                                window_radius=3)
+    s, p = run_gpu(small, expect_variant=api.SW_STENCIL_CLUSTER)
+    s2, p2 = run_gpu(small, variant=api.SW_STENCIL_PLAIN)
+    assert np.array_equal(s, s2) and np.array_equal(p, p2)
+    s_ref, p_ref = run_oracle(small)
+    assert rel_l2(s, s_ref) <= FP32_SEIS_TOL and rel_l2(p, p_ref) <= FP32_SEIS_TOL
+    # windows of radius 5: off-grid receivers have ten rows with a non-zero
+    # weight, more than the run keeps in registers (the general sampling loop)
+    wide = dataclasses.replace(w, window_radius=5)
+    s, p = run_gpu(wide, expect_variant=api.SW_STENCIL_CLUSTER)
+    s2, p2 = run_gpu(wide, variant=api.SW_STENCIL_PLAIN)
+    assert np.array_equal(s, s2) and np.array_equal(p, p2)
+
+
 def test_tma_kernel_many_segments(cuda_device):
     """A grid with more work items than CTAs of one tile: segments start and end at
     every plane offset and cross tile boundaries (ragged in x, y and z)."""
