@@ -323,7 +323,10 @@ sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_l
  * every = 0 turns timing off.  sw_get_profile returns, for the last
  * sw_forward, the summed time of the timed stencil launches, how many were
  * timed, and the number of kernels it launched in total (after sw_gradient:
- * no timed launches, and the kernels that call launched).
+ * no timed launches, and the kernels that call launched).  A 2D run on the
+ * cluster-resident kernel (SW_STENCIL_CLUSTER) is one launch for all time
+ * steps: with timing on, its time is reported with n_steps timed launches,
+ * so that the time per launch is the time per step.
  */
 sw_status sw_set_profiling(sw_grid* g, int every);
 sw_status sw_get_profile(const sw_grid* g, double* stencil_ms, int64_t* stencil_launches,
