@@ -278,6 +278,21 @@ def test_error_statuses(cuda_device):
     with pytest.raises(api.SimwaveError) as e:
         api.sw_create_grid(2, w.shape, w.spacing, 7, w.nbl, w.bc, 0.0, 3, 0.0)
     assert e.value.status == api.SW_EINVAL
+    # variants that exist for one dimension only
+    g = api.sw_create_grid(2, w.shape, w.spacing, 8, w.nbl, w.bc, 0.0, 3, 0.0)
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_stencil_variant(g, api.SW_STENCIL_TMA)
+    assert e.value.status == api.SW_EINVAL
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_stencil_variant(g, 7)
+    assert e.value.status == api.SW_EINVAL
+    g.close()
+    w3 = small_case(3, 8, False, n_steps=10)
+    g = api.sw_create_grid(3, w3.shape, w3.spacing, 8, w3.nbl, w3.bc, 0.0, 3, 0.0)
+    with pytest.raises(api.SimwaveError) as e:
+        api.sw_set_stencil_variant(g, api.SW_STENCIL_CLUSTER)
+    assert e.value.status == api.SW_EINVAL
+    g.close()
 
 
 def test_stalled_pipeline_reports_timeout(cuda_device):
