@@ -113,12 +113,17 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is in
+        (at most 3 s), so that short timed regions still get samples."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -558,6 +563,7 @@ def main():
     for _ in range(args.warmup):
         api.sw_forward(g, w.n_steps, seis, None)
     api.sw_set_profiling(g, PROFILE_EVERY)
+    cluster_run = api.sw_get_stencil_variant(g) == api.SW_STENCIL_CLUSTER
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -618,8 +624,10 @@ def main():
                         % (alg_bytes / 1e6))},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "stencil (CUDA events around every %dth launch, %d launches timed)" % (
-                             PROFILE_EVERY, stencil_launches),
+                         "kernel": ("cluster-resident 2D run (one launch per forward with CUDA events around "
+                                    "it, counted as %d time steps)" % stencil_launches) if cluster_run else
+                                   ("stencil (CUDA events around every %dth launch, %d launches timed)" % (
+                                       PROFILE_EVERY, stencil_launches)),
                          "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
             "e2e": e2e,
             "gpu_launches": int(kernels),
