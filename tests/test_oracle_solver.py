@@ -11,7 +11,9 @@
 - second-order convergence in time (Sec. 2.5, V2) and order-p convergence in
   space (V3) with manufactured solutions;
 - the variable-density operator by manufactured solutions (Sec. 2.5, V4);
-- constant density through the variable-density path equals constant density.
+- constant density through the variable-density path equals constant density;
+- conservation of the discrete energy of the undamped leapfrog scheme in a
+  closed Neumann box once the source has stopped.
 """
 import math
 
@@ -265,3 +267,70 @@ def test_variable_density_mms_paper_setup():
     errs = [_mms_error(8, h, 5e-5, 0.05, "paper") for h in (40.0, 20.0, 10.0)]
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 2e-6
+
+
+# Textbook central second-derivative weights v_0 .. v_R (orders 4 and 8),
+# written out here independently of the oracle's rational solve.
+_V_TEXTBOOK = {4: [-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0],
+               8: [-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0]}
+
+
+def _neumann_laplacian(p, spacing, order):
+    """Eq. 9 with even ghosts (p[-j] = p[j] about every face node)."""
+    v = _V_TEXTBOOK[order]
+    R = len(v) - 1
+    out = np.zeros_like(p)
+    for a, h in enumerate(spacing):
+        q = np.pad(p, [(R, R) if b == a else (0, 0) for b in range(p.ndim)], mode="reflect")
+        n = p.shape[a]
+        acc = v[0] * p
+        for j in range(1, R + 1):
+            acc = acc + v[j] * (np.take(q, np.arange(R + j, R + j + n), axis=a) +
+                                np.take(q, np.arange(R - j, R - j + n), axis=a))
+        out += acc / (h * h)
+    return out
+
+
+def _face_weights(shape):
+    """Diagonal W with 1/2 per axis on face nodes: W L is symmetric for even ghosts."""
+    w = np.ones(shape)
+    for a, n in enumerate(shape):
+        g = np.ones(n)
+        g[0] = g[-1] = 0.5
+        sh = [1] * len(shape)
+        sh[a] = n
+        w = w * g.reshape(sh)
+    return w
+
+
+@pytest.mark.parametrize("ndim,order", [(2, 4), (2, 8), (3, 8)])
+def test_energy_conserved_in_closed_neumann_box(ndim, order):
+    """With no absorbing layer (eta = 0, Eq. 4) and Neumann ghosts on every face,
+    the leapfrog recurrence of Eq. 7, p+ = 2p - p- + kappa L p, conserves
+    E = sum W/kappa (p+ - p)^2 - sum W p+ (L p) (W: face weights that make W L
+    symmetric), so E taken at two times after the source has stopped agrees to
+    round-off; a wrong ghost sign, weight or index in the oracle breaks it."""
+    rng = np.random.default_rng(11 + ndim + order)
+    if ndim == 2:
+        shape, spacing = (34, 41), (8.0, 10.0)
+        src = [(0.43 * 33 * 8.0, 0.57 * 40 * 10.0)]
+    else:
+        shape, spacing = (17, 19, 21), (9.0, 10.0, 8.0)
+        src = [(0.45 * 16 * 9.0, 0.5 * 18 * 10.0, 0.55 * 20 * 8.0)]
+    vel = 1500.0 + 1000.0 * rng.random(shape)
+    dt = 0.3 * min(spacing) / vel.max()
+    w = np.zeros(400)
+    w[:24] = oracle.ricker_samples(40.0, dt, 24, t0=12 * dt)  # a source that stops after 24 steps
+    kw = dict(src_pos=src, wavelet=w, nbl=[0] * (2 * ndim), bc=["null_neumann"] * (2 * ndim),
+              window_radius=3)
+    kappa = (vel * dt) ** 2
+    W = _face_weights(shape)
+
+    def energy(n):
+        _, p1, p0 = oracle.forward(ndim, shape, spacing, order, vel, dt, n, want_prev=True, **kw)
+        return float(np.sum(W / kappa * (p1 - p0) ** 2) - np.sum(W * p1 * _neumann_laplacian(p0, spacing, order)))
+
+    e1, e2, e3 = energy(60), energy(170), energy(300)
+    assert e1 > 0
+    assert abs(e2 - e1) <= 1e-9 * e1 and abs(e3 - e1) <= 1e-9 * e1
+
