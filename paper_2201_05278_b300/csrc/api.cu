@@ -465,14 +465,14 @@ void launch_stencil_tma(const sw_grid* g, const StencilArgs& a, int buf, cudaStr
   launch_stencil_tma_maps(g, a, m, st, g->has_density);
 }
 
-void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, const float* kappa, float* gk,
-                  const FaceInfo& f, const LapCoef& lc, cudaStream_t st) {
+void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, float* gk, const FaceInfo& f,
+                  const LapCoef& lc, cudaStream_t st) {
 #define SW_IMAGE(RR)                                                                            \
   case RR:                                                                                       \
     if (ndim == 3)                                                                               \
-      image_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, kappa, gk, f, lc);                       \
+      image_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, gk, f, lc);                              \
     else                                                                                         \
-      image_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, kappa, gk, f, lc);                       \
+      image_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, gk, f, lc);                              \
     break;
   switch (R) {
     SW_IMAGE(1) SW_IMAGE(2) SW_IMAGE(3) SW_IMAGE(4) SW_IMAGE(5)
@@ -482,16 +482,15 @@ void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, 
 #undef SW_IMAGE
 }
 
-void launch_image_vd(int R, int ndim, dim3 grid, const float* p, const float* psi, const float* kappa,
-                     float* const* gg, float* gk, float* const* ag, const FaceInfo& f, const LapCoef& lc,
-                     const VdWeights& w, cudaStream_t st) {
+void launch_image_vd(int R, int ndim, dim3 grid, const float* p, const float* psi, float* const* gg, float* gk,
+                     float* const* ag, const FaceInfo& f, const LapCoef& lc, const VdWeights& w, cudaStream_t st) {
 #define SW_IMAGE_VD(RR)                                                                                            \
   case RR:                                                                                                          \
     if (ndim == 3)                                                                                                  \
-      image_vd_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, kappa, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f, \
+      image_vd_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
                                                    lc, w);                                                          \
     else                                                                                                            \
-      image_vd_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, kappa, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f, \
+      image_vd_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
                                                    lc, w);                                                          \
     break;
   switch (R) {
@@ -1478,12 +1477,12 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
     const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
     if (vd)
-      launch_image_vd(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), a.kappa, GG, g->at0(GK), AG, f, lc, vw, st);
+      launch_image_vd(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), GG, g->at0(GK), AG, f, lc, vw, st);
     else
-      launch_image(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), a.kappa, g->at0(GK), f, lc, st);
+      launch_image(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), g->at0(GK), f, lc, st);
     if (src_threads > 0)
-      image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->at0(GK), src,
-                                                                      g->wavelet, g->sig_stride, k - 1, f);
+      image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), g->at0(GK), src, g->wavelet,
+                                                                      g->sig_stride, k - 1, f);
     SW_CUDA(cudaGetLastError());
     return SW_OK;
   };

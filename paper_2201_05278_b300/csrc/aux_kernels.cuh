@@ -613,12 +613,13 @@ __global__ void neumann_adjoint_kernel(const float* psi1, float* out, const floa
   }
 }
 
-// One term of dJ/dkappa per node: gk += psi (L p) / kappa, L the Eq. 9
+// One term of kappa dJ/dkappa per node: gk += psi (L p), L the Eq. 9
 // Laplacian of p (whose ghosts hold the face conditions), in the same
-// constant-annihilating form as the stencils.  Block (128 x, y, z).
+// constant-annihilating form as the stencils; the factor 1/kappa, the same
+// at every step, is applied once at the end (gradient_velocity_kernel), so
+// the pass reads no kappa.  Block (128 x, y, z).
 template <int R, int NDIM>
-__global__ void image_kernel(const float* p, const float* psi, const float* kappa, float* gk, FaceInfo f,
-                             LapCoef lc) {
+__global__ void image_kernel(const float* p, const float* psi, float* gk, FaceInfo f, LapCoef lc) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= f.nx) return;
@@ -633,13 +634,13 @@ __global__ void image_kernel(const float* p, const float* psi, const float* kapp
     lap = fmaf(lc.c[2][j], (p[k + j] + p[k - j]) - p2, lap);
     if constexpr (NDIM == 3) lap = fmaf(lc.c[1][j], (p[k + j * f.sy] + p[k - j * f.sy]) - p2, lap);
   }
-  gk[k] += ps * lap / kappa[k];
+  gk[k] += ps * lap;
 }
 
-// The source part of the same term: gk += psi s / kappa over the source
-// windows (s = window weights / prod(h) times S(t_n)), one thread per tap.
-__global__ void image_sources_kernel(const float* psi, const float* kappa, float* gk, PointSet src,
-                                     const float* sig, int sig_stride, int step, FaceInfo f) {
+// The source part of the same term: gk += psi s over the source windows
+// (s = window weights / prod(h) times S(t_n)), one thread per tap.
+__global__ void image_sources_kernel(const float* psi, float* gk, PointSet src, const float* sig, int sig_stride,
+                                     int step, FaceInfo f) {
   const int taps = src.lz * src.ly * src.lx;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= src.count * taps) return;
@@ -653,7 +654,7 @@ __global__ void image_sources_kernel(const float* psi, const float* kappa, float
   const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
   const int64_t k = int64_t(src.first[3 * s] + iz) * f.sz + int64_t(src.first[3 * s + 1] + iy) * f.sy +
                     (src.first[3 * s + 2] + ix);
-  atomicAdd(&gk[k], psi[k] * wgt * sig[int64_t(s) * sig_stride + step] / kappa[k]);
+  atomicAdd(&gk[k], psi[k] * wgt * sig[int64_t(s) * sig_stride + step]);
 }
 
 // Residual r = synthetic - observed, transposed to [receiver][step] (the
@@ -681,7 +682,8 @@ __global__ void residual_kernel(const float* syn, const float* obs, float* res_t
   }
 }
 
-// dJ/dc = 2 c dt^2 dJ/dkappa = 2 sqrt(kappa) dt dJ/dkappa, densely per node.
+// dJ/dc = 2 c dt^2 dJ/dkappa with dJ/dkappa = gk / kappa (gk the accumulated
+// kappa dJ/dkappa), densely per node.
 __global__ void gradient_velocity_kernel(const float* gk, const float* kappa, float* out, FaceInfo f, float dt) {
   const int64_t n = int64_t(f.nz) * f.ny * f.nx;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -690,7 +692,7 @@ __global__ void gradient_velocity_kernel(const float* gk, const float* kappa, fl
     const int y = int(zy % f.ny);
     const int z = int(zy / f.ny);
     const int64_t k = int64_t(z) * f.sz + int64_t(y) * f.sy + x;
-    out[i] = 2.f * sqrtf(kappa[k]) * dt * gk[k];
+    out[i] = 2.f * dt * gk[k] / sqrtf(kappa[k]);  // 2 c dt^2 gk / kappa, kappa = (c dt)^2
   }
 }
 
@@ -760,10 +762,10 @@ __global__ void vd_adjoint_kernel(const float* psi, const float* gz, const float
   }
 }
 
-// One term of dJ/dkappa and of dJ/dG_a with density: gk += psi L_rho p / kappa
+// One term of kappa dJ/dkappa and of dJ/dG_a with density: gk += psi L_rho p
 // and A_a -= psi D_a p (p's ghosts hold the face conditions).
 template <int R, int NDIM>
-__global__ void image_vd_kernel(const float* p, const float* psi, const float* kappa, const float* gz,
+__global__ void image_vd_kernel(const float* p, const float* psi, const float* gz,
                                 const float* gy, const float* gx, float* gk, float* az, float* ay, float* ax,
                                 FaceInfo f, LapCoef lc, VdWeights W) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -789,7 +791,7 @@ __global__ void image_vd_kernel(const float* p, const float* psi, const float* k
   }
   float adv = fmaf(gz[k], dz, gx[k] * dx);
   if constexpr (NDIM == 3) adv = fmaf(gy[k], dy, adv);
-  gk[k] += ps * (lap - adv) / kappa[k];
+  gk[k] += ps * (lap - adv);
   az[k] -= ps * dz;
   ax[k] -= ps * dx;
   if constexpr (NDIM == 3) ay[k] -= ps * dy;
