@@ -1452,7 +1452,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // one adjoint step: psi[k] from psi[k+1], psi[k+2], then its imaging
   // terms with the forward state p[k-1] (pk1, ghosts set)
   auto adjoint_step = [&](int k, float* pk1) -> sw_status {
-    nk += 5 + (vd ? 1 : 0) + (src_threads > 0);
+    nk += 4 + (vd ? 1 : 0) + (src_threads > 0);
     float* p1 = PSI((k + 1) & 1);  // psi[k+1]
     float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
     const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)], &warm[idx(p1)]};
@@ -1464,16 +1464,15 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
       launch_stencil_tma_maps(g, a, m, st, false);
     else
       launch_stencil(g->R, g->ndim, false, a, st);
-    neumann_adjoint_kernel<<<dim3(unsigned((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]),
-                                                     g->n[0] * g->n[1]) + 255) / 256), 3), 256, 0, st>>>(
-        g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R);
     if (vd)  // - sum_a D_a^T (G_a psi)
       vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
                                                                       g->damp, g->at0(p2), f, vw, g->R, g->ndim);
-    // the residuals into psi through the receiver windows (rows with non-zero weight only)
+    // its Neumann-face correction and the residuals into psi through the
+    // receiver windows (rows with non-zero weight only), in one launch
+    const int nb = int((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]), g->n[0] * g->n[1]) + 255) / 256);
     const int rthreads = rec.count * g->rec_rows_max * rec.lx;
-    inject_rows_kernel<<<(rthreads + 127) / 128, 128, 0, st>>>(g->at0(p2), a.kappa, g->damp, rec, g->rec_rows_max,
-                                                               res, N, k - 1, f, g->ndim, g->R);
+    adjoint_additions_kernel<<<unsigned(3 * nb + (rthreads + 255) / 256), 256, 0, st>>>(
+        g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R, nb, rec, g->rec_rows_max, res, N, k - 1, g->ndim);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
     const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
     if (vd)

@@ -90,10 +90,10 @@ __device__ __forceinline__ void inject_source_tap(float* p, const float* kappa, 
 // The same increments over only the window rows with a non-zero weight along
 // z and y (src.span set; max_rows = the largest such row count): one thread
 // per (point, row, column).
-__global__ void inject_rows_kernel(float* p, const float* kappa, const float2* damp, PointSet src, int max_rows,
-                                   const float* sig, int sig_stride, int step, FaceInfo f, int ndim, int R) {
+__device__ __forceinline__ void inject_row_node(float* p, const float* kappa, const float2* damp, const PointSet& src,
+                                                int max_rows, const float* sig, int sig_stride, int step,
+                                                const FaceInfo& f, int ndim, int R, int t) {
   const int per = max_rows * src.lx;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= src.count * per) return;
   const int s = t / per;
   const int rem = t - s * per;
@@ -103,6 +103,7 @@ __global__ void inject_rows_kernel(float* p, const float* kappa, const float2* d
   inject_source_node(p, kappa, damp, src, sig, sig_stride, step, f, ndim, R, s, sp.x + row / sp.w, sp.z + row % sp.w,
                      ix);
 }
+
 
 __global__ void inject_sources_kernel(float* p, const float* kappa, const float2* damp, PointSet src,
                                       const float* sig, int sig_stride, int step, FaceInfo f, int ndim,
@@ -603,14 +604,27 @@ __device__ __forceinline__ void neumann_adjoint_axis(const float* psi1, float* o
   atomicAdd(&out[k0], -a0 * kappa[k0] * back);
 }
 
-__global__ void neumann_adjoint_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
-                                       FaceInfo f, LapCoef lc, int R) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  switch (blockIdx.y) {  // axis
-    case 0: neumann_adjoint_axis<0>(psi1, out, kappa, damp, f, lc, R, t); break;
-    case 1: neumann_adjoint_axis<1>(psi1, out, kappa, damp, f, lc, R, t); break;
-    default: neumann_adjoint_axis<2>(psi1, out, kappa, damp, f, lc, R, t); break;
+// The two additions an adjoint step makes to psi after its stencil, in one
+// launch: the Neumann-face correction (blocks [0, 3 nb), nb per axis) and
+// the residuals through the receiver windows (the blocks after them).  Both
+// only add to `out` with atomics and read other arrays, so their blocks
+// run in any order.
+__global__ void adjoint_additions_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
+                                         FaceInfo f, LapCoef lc, int R, int nb, PointSet rec, int max_rows,
+                                         const float* res, int res_stride, int step, int ndim) {
+  int b = blockIdx.x;
+  if (b < 3 * nb) {
+    const int axis = b / nb;
+    const int64_t t = int64_t(b - axis * nb) * blockDim.x + threadIdx.x;
+    switch (axis) {
+      case 0: neumann_adjoint_axis<0>(psi1, out, kappa, damp, f, lc, R, t); break;
+      case 1: neumann_adjoint_axis<1>(psi1, out, kappa, damp, f, lc, R, t); break;
+      default: neumann_adjoint_axis<2>(psi1, out, kappa, damp, f, lc, R, t); break;
+    }
+    return;
   }
+  b -= 3 * nb;
+  inject_row_node(out, kappa, damp, rec, max_rows, res, res_stride, step, f, ndim, R, b * blockDim.x + threadIdx.x);
 }
 
 // One term of kappa dJ/dkappa per node: gk += psi (L p), L the Eq. 9
