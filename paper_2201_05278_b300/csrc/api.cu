@@ -2279,7 +2279,6 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
   std::vector<BatchGroup> groups;
   double v[kMaxR + 1];
   fd_second_weights(g0->order, v);
-  int tiles = 0;
   for (const auto& m : members) {
     const sw_grid* g = grids[m[0]];
     BatchGroup G;
