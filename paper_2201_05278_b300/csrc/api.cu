@@ -1451,8 +1451,9 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // backward: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
   // one adjoint step: psi[k] from psi[k+1], psi[k+2], then its imaging
   // terms with the forward state p[k-1] (pk1, ghosts set)
+  int pending_src = -1;  // the adjoint step whose source imaging is still to come
   auto adjoint_step = [&](int k, float* pk1) -> sw_status {
-    nk += 4 + (vd ? 1 : 0) + (src_threads > 0);
+    nk += 4 + (vd ? 1 : 0);
     float* p1 = PSI((k + 1) & 1);  // psi[k+1]
     float* p2 = PSI(k & 1);        // psi[k+2], overwritten by psi[k]
     const StepMaps m{&halo[idx(p1)], &inner[idx(p1)], &inner[idx(p2)], &warm[idx(p1)]};
@@ -1471,17 +1472,20 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     // receiver windows (rows with non-zero weight only), in one launch
     const int nb = int((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]), g->n[0] * g->n[1]) + 255) / 256);
     const int rthreads = rec.count * g->rec_rows_max * rec.lx;
-    adjoint_additions_kernel<<<unsigned(3 * nb + (rthreads + 255) / 256), 256, 0, st>>>(
-        g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R, nb, rec, g->rec_rows_max, res, N, k - 1, g->ndim);
+    // step k+1's source imaging: psi[k+1] is p1, which this step only reads
+    SourceImaging si{};
+    if (src_threads > 0 && pending_src == k + 1)
+      si = SourceImaging{g->at0(p1), g->at0(GK), src, g->wavelet, g->sig_stride, k, (src_threads + 255) / 256};
+    adjoint_additions_kernel<<<unsigned(si.blocks + 3 * nb + (rthreads + 255) / 256), 256, 0, st>>>(
+        g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R, nb, rec, g->rec_rows_max, res, N, k - 1, g->ndim,
+        si);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
     const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
     if (vd)
       launch_image_vd(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), GG, g->at0(GK), AG, f, lc, vw, st);
     else
       launch_image(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), g->at0(GK), f, lc, st);
-    if (src_threads > 0)
-      image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(p2), g->at0(GK), src, g->wavelet,
-                                                                      g->sig_stride, k - 1, f);
+    pending_src = k;  // its source imaging goes with the next step's additions, or follows the sweep
     SW_CUDA(cudaGetLastError());
     return SW_OK;
   };
@@ -1585,6 +1589,12 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     }
   }
 
+  if (src_threads > 0 && pending_src > 0) {  // the last adjoint step's source imaging
+    image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(PSI(pending_src & 1)), g->at0(GK), src,
+                                                                    g->wavelet, g->sig_stride, pending_src - 1, f);
+    SW_CUDA(cudaGetLastError());
+    ++nk;
+  }
   // dJ/dc, densely per node
   float* out = grad_vel;
   const bool host_out = !is_device_pointer(grad_vel);

@@ -604,15 +604,57 @@ __device__ __forceinline__ void neumann_adjoint_axis(const float* psi1, float* o
   atomicAdd(&out[k0], -a0 * kappa[k0] * back);
 }
 
+// The source part of the same term: gk += psi s over the source windows
+// (s = window weights / prod(h) times S(t_n)), one thread per tap.
+__device__ __forceinline__ void image_source_tap(const float* psi, float* gk, const PointSet& src, const float* sig,
+                                                 int sig_stride, int step, const FaceInfo& f, int t) {
+  const int taps = src.lz * src.ly * src.lx;
+  if (t >= src.count * taps) return;
+  const int s = t / taps;
+  int rem = t % taps;
+  const int ix = rem % src.lx;
+  rem /= src.lx;
+  const int iy = rem % src.ly;
+  const int iz = rem / src.ly;
+  const float* w = src.w + int64_t(s) * 3 * src.L;
+  const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
+  const int64_t k = int64_t(src.first[3 * s] + iz) * f.sz + int64_t(src.first[3 * s + 1] + iy) * f.sy +
+                    (src.first[3 * s + 2] + ix);
+  atomicAdd(&gk[k], psi[k] * wgt * sig[int64_t(s) * sig_stride + step]);
+}
+
+__global__ void image_sources_kernel(const float* psi, float* gk, PointSet src, const float* sig, int sig_stride,
+                                     int step, FaceInfo f) {
+  image_source_tap(psi, gk, src, sig, sig_stride, step, f, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The source imaging of an earlier adjoint step, folded into the next
+// step's additions launch (adjoint_additions_kernel): psi is that step's
+// final adjoint state (the next step only reads it); blocks = 0: none.
+struct SourceImaging {
+  const float* psi;
+  float* gk;
+  PointSet src;
+  const float* sig;
+  int sig_stride, step, blocks;
+};
+
+
 // The two additions an adjoint step makes to psi after its stencil, in one
-// launch: the Neumann-face correction (blocks [0, 3 nb), nb per axis) and
-// the residuals through the receiver windows (the blocks after them).  Both
-// only add to `out` with atomics and read other arrays, so their blocks
-// run in any order.
+// launch: the Neumann-face correction (3 nb blocks, nb per axis, after the
+// si.blocks of an earlier step's source imaging) and the residuals through
+// the receiver windows (the blocks after them).  Both only add to `out`
+// with atomics and read other arrays, so their blocks run in any order, as
+// do the source imaging's, which add to gk.
 __global__ void adjoint_additions_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
                                          FaceInfo f, LapCoef lc, int R, int nb, PointSet rec, int max_rows,
-                                         const float* res, int res_stride, int step, int ndim) {
+                                         const float* res, int res_stride, int step, int ndim, SourceImaging si) {
   int b = blockIdx.x;
+  if (b < si.blocks) {  // an earlier step's source imaging (adds to gk, reads other arrays than out)
+    image_source_tap(si.psi, si.gk, si.src, si.sig, si.sig_stride, si.step, f, b * blockDim.x + threadIdx.x);
+    return;
+  }
+  b -= si.blocks;
   if (b < 3 * nb) {
     const int axis = b / nb;
     const int64_t t = int64_t(b - axis * nb) * blockDim.x + threadIdx.x;
@@ -649,26 +691,6 @@ __global__ void image_kernel(const float* p, const float* psi, float* gk, FaceIn
     if constexpr (NDIM == 3) lap = fmaf(lc.c[1][j], (p[k + j * f.sy] + p[k - j * f.sy]) - p2, lap);
   }
   gk[k] += ps * lap;
-}
-
-// The source part of the same term: gk += psi s over the source windows
-// (s = window weights / prod(h) times S(t_n)), one thread per tap.
-__global__ void image_sources_kernel(const float* psi, float* gk, PointSet src, const float* sig, int sig_stride,
-                                     int step, FaceInfo f) {
-  const int taps = src.lz * src.ly * src.lx;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= src.count * taps) return;
-  const int s = t / taps;
-  int rem = t % taps;
-  const int ix = rem % src.lx;
-  rem /= src.lx;
-  const int iy = rem % src.ly;
-  const int iz = rem / src.ly;
-  const float* w = src.w + int64_t(s) * 3 * src.L;
-  const float wgt = w[iz] * w[src.L + iy] * w[2 * src.L + ix];
-  const int64_t k = int64_t(src.first[3 * s] + iz) * f.sz + int64_t(src.first[3 * s + 1] + iy) * f.sy +
-                    (src.first[3 * s + 2] + ix);
-  atomicAdd(&gk[k], psi[k] * wgt * sig[int64_t(s) * sig_stride + step]);
 }
 
 // Residual r = synthetic - observed, transposed to [receiver][step] (the
