@@ -322,7 +322,8 @@ EncodeTiledFn encode_tiled() {
 }
 
 // Tile shape of the pipelined kernel per stencil radius (must match the
-// instantiations in launch_stencil_tma).
+// instantiations in launch_stencil_tma_maps; the 64 x 32 tiles of the
+// variable-density forward have maps of their own).
 void tma_tile(int R, int* tx, int* ty) {
   *tx = 64;
   *ty = 16;
@@ -404,14 +405,18 @@ void launch_tma_t(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cud
 }
 
 // Tile height / rows per warp / ring depth / minimum CTAs per SM for each
-// radius (tile width 64), constant and variable density.  tma_tile() must
-// give the same tile shape.  Radii up to 4: four rows per thread in 4-warp
-// CTAs, three per SM, three bundles in flight each (fastest on the order-8
-// bench workload: 70.8 against 80.2 us for two rows per thread in 8-warp
-// CTAs); larger radii keep two rows per thread (four would spill).
-// Variable density: four rows per thread in 4-warp CTAs with three bundles
-// (730 against 863 us per launch at order 16 on 512 x 512 x 384) up to
-// radius 8, two rows in 8-warp CTAs above.
+// radius (tile width 64), constant and variable density.  tma_tile() gives
+// the tile shape of every launch here except the 64 x 32 tiles (m.tall),
+// whose maps sw_set_model builds separately.  Radii up to 4: four rows per
+// thread in 4-warp CTAs, three per SM, three bundles in flight each
+// (fastest on the order-8 bench workload: 70.8 against 80.2 us for two rows
+// per thread in 8-warp CTAs; three rows in four CTAs per SM, six rows on
+// 64 x 24 and eight rows on 64 x 32 tiles were slower too); larger radii
+// keep two rows per thread (four would spill).  Variable density: four rows
+// per thread in 4-warp CTAs with three bundles (730 against 863 us per
+// launch at order 16 on 512 x 512 x 384 for two rows in 8-warp CTAs) up to
+// radius 8, two rows in 8-warp CTAs above; the radius-8 forward uses 64 x 32
+// tiles in one 8-warp CTA per SM.
 void launch_stencil_tma_maps(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st,
                              bool vd) {
   if (vd && m.tall && g->R == 8) {
