@@ -334,3 +334,123 @@ def test_energy_conserved_in_closed_neumann_box(ndim, order):
     assert e1 > 0
     assert abs(e2 - e1) <= 1e-9 * e1 and abs(e3 - e1) <= 1e-9 * e1
 
+
+
+# ---- sources and forcing inside a damped region (Eq. 4, 7, 11) ---------------
+#
+# With a uniform eta and uniform kappa, every Dirichlet sine (Neumann cosine)
+# mode is an eigenvector of the Eq. 9 operator, so projecting Eq. 7 with a
+# source or forcing term onto a mode leaves the scalar recurrence
+#   (1 + e) a[n+1] = (2 - kappa lam) a[n] - (1 - e) a[n-1] + kappa g[n],
+# e = eta dt, g[n] the term's projection onto the mode.  The recurrence is
+# solved here by a scalar loop per mode; the oracle must give the same field.
+# Dropping the 1/(1 + e) from the oracle's source or forcing term, or applying
+# it to the forcing but not to the point source, fails these tests.
+
+
+def _forced_amplitudes(kappa, lam, e, g):
+    """a[1..N] of the forced, damped two-level recurrence from a[0] = a[-1] = 0;
+    lam and g[n] may be arrays over modes (g has the step as its first axis)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    a_prev = np.zeros_like(lam)
+    a = np.zeros_like(lam)
+    out = []
+    for gn in g:
+        a_next = ((2.0 - kappa * lam) * a - (1.0 - e) * a_prev + kappa * gn) / (1.0 + e)
+        a_prev, a = a, a_next
+        out.append(a)
+    return out
+
+
+@pytest.mark.parametrize("ndim,kind,order", [(2, "d", 8), (2, "n", 4), (3, "d", 8), (3, "n", 16)])
+def test_forced_mode_under_uniform_damping(ndim, kind, order):
+    """Forcing F(x) T(t_n) with F a mode and eta > 0 everywhere: p[n] = a[n] F."""
+    r = order // 2
+    shape = (r + 14, r + 11, r + 16)[:ndim] if ndim == 3 else (r + 17, r + 21)
+    spacing = (6.0, 7.0, 5.0)[:ndim] if ndim == 3 else (6.0, 5.0)
+    m = (2, 1, 3)[:ndim] if ndim == 3 else (1, 2)
+    mode, lam = _mode(shape, spacing, [kind] * ndim, m, order)
+    lam = -lam  # _mode returns the symbol (negative); the recurrence uses L mode = -lam mode
+    c, dt, eta = 1200.0, 1e-3, 150.0  # e = 0.15
+    kappa, e = (c * dt) ** 2, eta * dt
+    n_steps = 90
+    T = np.random.default_rng(7 + ndim).standard_normal(n_steps)
+    bc = {"d": oracle.BC_DIRICHLET, "n": oracle.BC_NEUMANN}[kind]
+    bc6 = [bc] * 6 if ndim == 3 else [bc, bc, 0, 0, bc, bc]
+    _, p, p_prev = oracle.run_raw(ndim, shape, spacing, order, bc6, np.full(shape, eta), dt, np.full(shape, c),
+                                  n_steps=n_steps, force_fields=mode[None], force_sigs=T[None], want_prev=True)
+    a = _forced_amplitudes(kappa, lam, e, T)
+    scale = max(abs(a[-1]), abs(a[-2]))
+    assert scale > 1e-3
+    assert np.allclose(p, a[-1] * mode, rtol=0, atol=1e-11 * scale)
+    assert np.allclose(p_prev, a[-2] * mode, rtol=0, atol=1e-11 * scale)
+
+
+@pytest.mark.parametrize("on_grid", [True, False])
+def test_point_source_under_uniform_damping_by_sine_modes(on_grid):
+    """A point source (Eq. 11) in a Dirichlet box with eta > 0 everywhere: the
+    oracle's field equals the sum over the box's sine modes of the forced,
+    damped scalar recurrence driven by the source pattern's projection."""
+    order = 8
+    shape, spacing = (23, 27), (8.0, 6.0)
+    nz, nx = shape
+    c, dt, eta = 1500.0, 1.2e-3, 110.0  # e = 0.132
+    kappa, e = (c * dt) ** 2, eta * dt
+    n_steps = 70
+    # on-grid: one node of weight 1; off-grid: the product of the two 1D windows
+    pos = (9.0 * 8.0, 14.0 * 6.0) if on_grid else (9.37 * 8.0, 13.61 * 6.0)
+    wins = oracle.point_windows([pos], 2, spacing, [0, 0], 3, shape=shape)
+    (fz, wz), _, (fx, wx) = wins[0]
+    pattern = np.zeros(shape)
+    pattern[fz:fz + len(wz), fx:fx + len(wx)] = np.outer(wz, wx) / (spacing[0] * spacing[1])
+    assert np.count_nonzero(pattern) == (1 if on_grid else 36)
+    assert not pattern[0].any() and not pattern[-1].any() and not pattern[:, 0].any() and not pattern[:, -1].any()
+    S = oracle.ricker_samples(60.0, dt, n_steps, t0=0.02)
+    _, p = oracle.run_raw(2, shape, spacing, order, [1, 1, 0, 0, 1, 1], np.full(shape, eta), dt,
+                          np.full(shape, c), src_windows=wins, src_sig=S, n_steps=n_steps)
+    # sine basis of the interior nodes: phi_m(i) = sin(pi m i / (n - 1)), m = 1 .. n-2,
+    # orthogonal with sum_i phi_m phi_m' = (n - 1) / 2 delta_mm'
+    def basis(n):
+        i = np.arange(n)[:, None]
+        mm = np.arange(1, n - 1)[None, :]
+        return np.sin(np.pi * mm * i / (n - 1)), mm[0]
+
+    Pz, mz = basis(nz)
+    Px, mx = basis(nx)
+    coef = (2.0 / (nz - 1)) * (2.0 / (nx - 1)) * (Pz.T @ pattern @ Px)  # [mode_z, mode_x]
+    assert np.allclose(Pz @ coef @ Px.T, pattern, rtol=0, atol=1e-12 * np.abs(pattern).max())
+    lam = -(np.array([_symbol(order, k * np.pi / ((nz - 1) * spacing[0]), spacing[0]) for k in mz])[:, None] +
+            np.array([_symbol(order, k * np.pi / ((nx - 1) * spacing[1]), spacing[1]) for k in mx])[None, :])
+    a = _forced_amplitudes(kappa, lam, e, [s * coef for s in S])[-1]
+    expect = Pz @ a @ Px.T
+    assert np.abs(expect).max() > 1e-6
+    assert np.allclose(p, expect, rtol=0, atol=1e-10 * np.abs(expect).max())
+
+
+def test_first_step_of_sources_in_the_absorbing_layer():
+    """One step from rest: p[1] = kappa/(1 + eta dt) S(t_0) d_k / prod(h) at every
+    window node (Eq. 7, Eq. 11) with the layer's eta (Eq. 4) at that node, and
+    zero elsewhere; two sources deep in the layer, one in the physical box."""
+    shape, spacing = (30, 34), (10.0, 8.0)
+    nbl = [0, 8, 7, 8]
+    rng = np.random.default_rng(3)
+    vel = 1600.0 + 900.0 * rng.random(shape)
+    dt = 0.35 * 8.0 / vel.max()
+    alpha, deg = 9.0, 3
+    # cell coordinates (z, x): (10.3, 3.2) in the x- layer, (25.4, 15.6) in the
+    # z+ layer, (12.2, 16.7) in the physical box (x node 7 is its first column)
+    src = [(10.3 * 10.0, (3.2 - 7) * 8.0), (25.4 * 10.0, (15.6 - 7) * 8.0), (12.2 * 10.0, (16.7 - 7) * 8.0)]
+    S0 = 0.73
+    _, p = oracle.forward(2, shape, spacing, 8, vel, dt, 1, src_pos=src, wavelet=[S0], nbl=nbl,
+                          bc=["null_neumann", "null_dirichlet", "null_dirichlet", "null_dirichlet"],
+                          damp_alpha=alpha, damp_degree=deg, window_radius=3)
+    eta = oracle.eta_field(shape, nbl, alpha, deg)
+    expect = np.zeros(shape)
+    for axes in oracle.point_windows(src, 2, spacing, [nbl[0], nbl[2]], 3, shape=shape):
+        (fz, wz), _, (fx, wx) = axes
+        expect[fz:fz + len(wz), fx:fx + len(wx)] += np.outer(wz, wx) * S0 / (spacing[0] * spacing[1])
+    kap = (vel * dt) ** 2
+    expect *= kap / (1.0 + eta * dt)
+    e_src = (eta * dt)[expect != 0]
+    assert e_src.max() > 0.05  # some source nodes are strongly damped
+    assert np.allclose(p, expect, rtol=0, atol=1e-14 * np.abs(expect).max())
