@@ -126,7 +126,6 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
  */
 sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_field);
 
-/* Time step in use (after sw_set_model when dt was automatic). */
 /*
  * Misfit gradient by the adjoint-state method.  The paper names full-waveform
  * inversion as the solver's use but prints no adjoint; this is the exact
@@ -189,6 +188,14 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
  */
 sw_status sw_set_checkpoint_budget(sw_grid* g, int max_states);
 
+/*
+ * sw_get_dt -- the time step in use, in seconds (Sec. 2.2, Eq. 8).
+ *   dt  host, one double: the user's dt, or after sw_set_model with an
+ *       automatic dt (<= 0 at sw_create_grid) the stability bound of Eq. 8,
+ *       dt = 2 / (c_max sqrt(sum_axes a / h^2)), a = |v_0| + 2 sum_j |v_j|
+ * Errors: SW_EINVAL for NULL arguments; SW_ESTATE when the time step is
+ * automatic and no model is set yet.
+ */
 sw_status sw_get_dt(const sw_grid* g, double* dt);
 
 /*
@@ -345,20 +352,30 @@ sw_status sw_get_device_bytes(const sw_grid* g, int64_t* bytes);
  *
  * Arguments mean what they mean in the four calls above, with these limits:
  *   - velocity, density (NULL for constant density), seismogram and
- *     final_field (NULL to skip) must be device memory of the current
- *     device; positions are host memory; the wavelet may be host or device.
+ *     final_field (NULL to skip) must be plain device memory (not managed)
+ *     of the current device, else SW_EINVAL; positions are host memory; the
+ *     wavelet may be host memory or device memory of the current device.
+ *     The library cannot see buffer sizes: velocity, density and final_field
+ *     hold the grid's node count, the seismogram n_steps * n_rec values and
+ *     the wavelet nt (or n_src * nt) samples.
  *   - Wavefields, model fields, damping table and window weights live in one
  *     static device array of SW_NOALLOC_SCRATCH_BYTES that every GPU which
  *     loads the library holds until the process exits.  A problem that needs
- *     more (about three padded FP32 copies of the grid, four with density)
- *     is rejected with SW_EINVAL before any device work; the message gives
- *     the bytes needed.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     more (about three padded FP32 copies of the grid, four with density),
+ *     or a grid of more than 2^34 nodes, is rejected with SW_EINVAL before
+ *     any device work; the message gives the bytes needed.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     which allocates nothing) with the caller's device current.  The first
+ *     lookup on a device may load the library's device code, so make the
+ *     first call on a device before any stream capture on it.
  *   - Every call shares the same array and leaves its contents behind (the
  *     call clears what must start at zero).  Calls whose GPU work overlaps,
  *     on one device, race on the array and give wrong results: serialise them.
+ *   - It always runs the plain per-step kernels (stencil, then source
+ *     injection and receiver sampling as separate launches), not the
+ *     pipelined 3D kernel or the cluster-resident 2D run that sw_forward
+ *     picks: its results match sw_forward's within the FP32 parity
+ *     tolerance, not bit for bit, and it runs slower.
  *   - Synchronises the stream before returning, like sw_forward.
  */
 #define SW_NOALLOC_SCRATCH_BYTES (32ull << 20)

@@ -314,11 +314,13 @@ def sw_forward_noalloc(ndim: int, shape: Sequence[int], spacing: Sequence[float]
                        seismogram=None, final_field=None, wavelet_per_source: bool = False, stream=None) -> None:
     """Forward run that allocates no device memory (see sw_forward_noalloc in the C header).
 
-    velocity / density / seismogram / final_field must be CUDA tensors; the
-    outputs must be preallocated by the caller.
+    velocity / density / seismogram / final_field must be CUDA tensors on the
+    current device; the outputs must be preallocated by the caller.  The sizes
+    are checked here against shape, the source and receiver counts and
+    n_steps before the call (the C entry point only sees raw pointers).
     """
+    import torch
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
@@ -328,14 +330,39 @@ def sw_forward_noalloc(ndim: int, shape: Sequence[int], spacing: Sequence[float]
         wav = wavelet
     else:
         wav = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float32))
-    nt = int(wav.shape[-1])
+    nt = int(wav.shape[-1]) if wav.ndim else 1
+    n_src, n_rec = int(src.shape[0]), int(rec.shape[0])
+    nodes = int(np.prod([int(s) for s in shape]))
+    here = torch.cuda.current_device()
+
+    def on_device(name, t, numel, at_least=False):
+        if t is None:
+            return
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.device.index == here):
+            raise ValueError("%s must be a CUDA tensor on the current device (cuda:%d)" % (name, here))
+        if (t.numel() < numel) if at_least else (t.numel() != numel):
+            raise ValueError("%s holds %d values, needs %s%d" % (name, t.numel(), ">= " if at_least else "", numel))
+
+    on_device("velocity", velocity, nodes)
+    on_device("density", density, nodes)
+    on_device("final_field", final_field, nodes)
+    if n_rec > 0 and n_steps > 0:
+        if seismogram is None:
+            raise ValueError("seismogram is needed with receivers")
+        on_device("seismogram", seismogram, int(n_steps) * n_rec, at_least=True)
+    if n_src > 0:
+        want = n_src * nt if wavelet_per_source else nt
+        if int(np.prod(wav.shape)) != want:
+            raise ValueError("wavelet holds %d samples, needs %d" % (int(np.prod(wav.shape)), want))
+        if hasattr(wav, "is_cuda") and wav.is_cuda and wav.device.index != here:
+            raise ValueError("the wavelet is on another device than the current one")
     dp = ctypes.POINTER(ctypes.c_double)
     shp = (ctypes.c_int64 * ndim)(*[int(s) for s in shape])
     spc = (ctypes.c_double * ndim)(*[float(s) for s in spacing])
     _check(_lib.load().sw_forward_noalloc(
         int(ndim), shp, spc, int(space_order), _faces(nbl, ndim), _faces(bc, ndim, BC_NAMES), float(damp_alpha),
-        int(damp_degree), float(dt), _ptr(velocity), _ptr(density), int(src.shape[0]), src.ctypes.data_as(dp),
-        int(rec.shape[0]), rec.ctypes.data_as(dp), nt, _ptr(wav), int(bool(wavelet_per_source)),
+        int(damp_degree), float(dt), _ptr(velocity), _ptr(density), n_src, src.ctypes.data_as(dp),
+        n_rec, rec.ctypes.data_as(dp), nt, _ptr(wav), int(bool(wavelet_per_source)),
         int(window_radius), int(n_steps), _ptr(seismogram), _ptr(final_field), ctypes.c_void_p(stream)))
 
 

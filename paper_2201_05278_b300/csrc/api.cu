@@ -8,7 +8,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -57,6 +56,37 @@ bool is_device_pointer(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Is p plain device memory (not managed, not host) of the current device?
+bool is_current_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// Is p device or managed memory of another device than the current one?
+bool is_other_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.device != dev;
 }
 
 int grid_blocks(int64_t n, int threads) {
@@ -1804,47 +1834,52 @@ void sw_destroy_grid(sw_grid* g) {
 
 // ---- allocation-free forward ------------------------------------------------
 //
-// sw_forward_noalloc runs the same forward simulation as the handle-based calls
-// (same kernels, same launch shapes) for callers that cannot allocate device
-// memory.  Everything the simulation needs besides the caller's inputs and
-// outputs lives in one file-scope device array of SW_NOALLOC_SCRATCH_BYTES.
+// sw_forward_noalloc runs the forward simulation of the handle-based calls for
+// callers that cannot allocate device memory.  It always takes the plain
+// per-step path (stencil_plain kernels, then separate source-injection and
+// receiver-sampling launches per step), not the pipelined 3D kernel or the
+// cluster-resident 2D run that sw_forward picks, so its results agree with
+// sw_forward within the FP32 parity tolerance, not bit for bit, and its
+// throughput is lower.  Everything the simulation needs besides the caller's
+// inputs and outputs lives in one file-scope device array of
+// SW_NOALLOC_SCRATCH_BYTES.
 
 static __device__ __align__(256) float noalloc_scratch[SW_NOALLOC_SCRATCH_BYTES / sizeof(float)];
 
 namespace {
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-float* g_noalloc_address[kNoAllocMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  Host code only
 // sees a host-side stand-in under the array's name, so the address is looked
-// up once per device (with that device current) and cached.
+// up on every call with the caller's device current (no allocation; nothing
+// is cached, so a torn-down and re-created context never sees a stale
+// address).  The first lookup on a device may load the library's device code.
 sw_status noalloc_scratch_address(float** out) {
-  int dev = 0;
-  SW_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SW_EINVAL, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_address[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(SW_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-    g_noalloc_address[dev] = static_cast<float*>(p);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(SW_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
   }
-  *out = g_noalloc_address[dev];
+  *out = static_cast<float*>(p);
   return SW_OK;
 }
 
 // Bump carving of the scratch array in 256-byte units (host arithmetic only).
+// A request larger than what is left marks the plan as over capacity instead
+// of adding to `used`, so the running sum can never wrap.
 struct ScratchCarver {
   float* base;
   size_t used;
   size_t cap;
+  bool over = false;
   float* take(size_t floats) {
+    if (over || floats > cap - used) {
+      over = true;
+      return nullptr;
+    }
     const size_t n = (floats + 63) / 64 * 64;
     float* p = base ? base + used : nullptr;
-    used += n;
+    used = n > cap - used ? cap : used + n;
     return p;
   }
 };
@@ -1953,6 +1988,7 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
     }
     if (nbl[2 * a] + nbl[2 * a + 1] >= shape[a]) return fail(SW_EINVAL, "absorbing layers cover the whole axis %d", a);
   }
+  if (g.n[0] * g.n[1] * g.n[2] > (int64_t(1) << 34)) return fail(SW_EINVAL, "grid too large");
   g.alpha = damp_alpha;
   g.degree = damp_degree;
   g.dt_user = dt;
@@ -1978,7 +2014,8 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
   // -- scratch plan; reject problems that do not fit before touching the device
   const size_t field = size_t(g.lay.total);
   const size_t wav_floats = size_t(n_src > 0 ? (wavelet_per_source ? n_src : 1) : 0) * size_t(nt);
-  ScratchCarver plan{nullptr, 0, 0};
+  const size_t cap = SW_NOALLOC_SCRATCH_BYTES / sizeof(float);
+  ScratchCarver plan{nullptr, 0, cap};
   plan.take(field);
   plan.take(field);
   plan.take(field);
@@ -1990,15 +2027,22 @@ extern "C" sw_status sw_forward_noalloc(int ndim, const int64_t* shape, const do
   plan.take(wav_floats);
   plan.take(size_t(n_rec) * 3);
   plan.take(size_t(n_rec) * 3 * g.L);
-  const size_t cap = SW_NOALLOC_SCRATCH_BYTES / sizeof(float);
-  if (plan.used > cap)
-    return fail(SW_EINVAL, "problem needs %zu bytes of scratch; sw_forward_noalloc is limited to %zu bytes",
-                plan.used * sizeof(float), size_t(SW_NOALLOC_SCRATCH_BYTES));
+  if (plan.over) {
+    const double need = 4.0 * (double(field) * (g.has_density ? 4.0 : 3.0) + double(wav_floats) +
+                               double(g.damp_len) * 2.0 + double(n_src + n_rec) * 3.0 * (1.0 + g.L));
+    return fail(SW_EINVAL, "problem needs about %.4g bytes of scratch; sw_forward_noalloc is limited to %zu bytes",
+                need, size_t(SW_NOALLOC_SCRATCH_BYTES));
+  }
 
-  // grid-shaped inputs and outputs must already be on the device (host staging would allocate)
-  if (!is_device_pointer(velocity) || (density && !is_device_pointer(density)) ||
-      (seismogram && !is_device_pointer(seismogram)) || (final_field && !is_device_pointer(final_field)))
-    return fail(SW_EINVAL, "sw_forward_noalloc needs device pointers for velocity, density and the outputs");
+  // grid-shaped inputs and outputs must already be device memory of the current
+  // device (host staging would allocate; another device's memory is not reachable)
+  if (!is_current_device_pointer(velocity) || (density && !is_current_device_pointer(density)) ||
+      (seismogram && !is_current_device_pointer(seismogram)) ||
+      (final_field && !is_current_device_pointer(final_field)))
+    return fail(SW_EINVAL,
+                "sw_forward_noalloc needs velocity, density and the outputs in device memory of the current device");
+  if (n_src > 0 && is_other_device_pointer(wavelet))
+    return fail(SW_EINVAL, "the wavelet is memory of another device");
 
   float* base = nullptr;
   SW_TRY(noalloc_scratch_address(&base));

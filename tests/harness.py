@@ -15,6 +15,10 @@ from paper_2201_05278_b300 import api
 from paper_2201_05278_b300.workloads import Workload
 
 FP32_SEIS_TOL = 1e-5  # relative L2 on the seismogram, FP32 forward vs FP64 oracle
+# Element-wise bar: every sample / node within this fraction of the largest
+# magnitude of the reference, so that an error confined to a few nodes (a wrong
+# face row, a stale halo, a ragged tile edge) cannot hide under the global norm.
+FP32_MAX_TOL = 1e-5
 
 
 def rel_l2(a, b) -> float:
@@ -22,6 +26,42 @@ def rel_l2(a, b) -> float:
     b = np.asarray(b, dtype=np.float64)
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+
+def max_rel(a, b) -> float:
+    """max |a - b| / max |b| (max |a - b| when b is all zero)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.size == 0 and b.size == 0:
+        return 0.0
+    d = float(np.abs(a - b).max())
+    mb = float(np.abs(b).max())
+    return d / mb if mb > 0 else d
+
+
+def _log_parity(what, e2, einf):
+    path = os.environ.get("PARITY_LOG")
+    if not path:
+        return
+    import json
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    with open(path, "a") as f:
+        f.write(json.dumps({"test": test, "what": what, "rel_l2": e2, "max_rel": einf}) + "\n")
+
+
+def parity(a, b, what=""):
+    """(relative L2, element-wise max relative) of a against the reference b, logged
+    to $PARITY_LOG when set."""
+    e2, einf = rel_l2(a, b), max_rel(a, b)
+    _log_parity(what, e2, einf)
+    return e2, einf
+
+
+def assert_parity(a, b, what="", tol=FP32_SEIS_TOL, max_tol=FP32_MAX_TOL):
+    """Both bars: relative L2 <= tol and every element within max_tol * max|b|."""
+    e2, einf = parity(a, b, what)
+    assert e2 <= tol and einf <= max_tol, "%s: rel-L2 %.3e (bar %.0e), max %.3e of peak (bar %.0e)" % (
+        what or "parity", e2, tol, einf, max_tol)
 
 
 def wavelet_of(w: Workload, nt=None):

@@ -13,9 +13,14 @@ import pytest
 
 from paper_2201_05278_b300 import api, workloads
 from paper_2201_05278_b300.workloads import Workload
-from tests.harness import FP32_SEIS_TOL, rel_l2, run_gpu, run_oracle
+from tests.harness import FP32_SEIS_TOL, assert_parity, rel_l2, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
+
+# Face slabs are compared against their own norm and peak, about a hundred
+# times smaller than the field's: the bar there is relative to the local
+# amplitude (a wrong face row or ghost image is an error of order one there).
+FACE_TOL = 1e-3
 
 
 def small_case(ndim, order, density, seed=0, n_steps=60):
@@ -52,8 +57,8 @@ def test_small_grids_all_orders(cuda_device, ndim, order, density):
     s_gpu, p_gpu = run_gpu(w)
     s_ref, p_ref = run_oracle(w)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
 
 
 @pytest.mark.parametrize("density", [False, True])
@@ -66,8 +71,8 @@ def test_3d_both_stencil_kernels(cuda_device, order, density):
     s_tma, p_tma = run_gpu(w, expect_variant=api.SW_STENCIL_TMA)
     s_pl, p_pl = run_gpu(w, variant=api.SW_STENCIL_PLAIN, expect_variant=api.SW_STENCIL_PLAIN)
     for s, p in ((s_tma, p_tma), (s_pl, p_pl)):
-        assert rel_l2(s, s_ref) <= FP32_SEIS_TOL
-        assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
+        assert_parity(s, s_ref, "seismogram")
+        assert_parity(p, p_ref, "field")
 
 
 @pytest.mark.parametrize("order,bcs", [(2, 0), (8, 0), (8, 1), (14, 1), (20, 0)])
@@ -90,8 +95,8 @@ def test_2d_cluster_run_matches_the_plain_kernels(cuda_device, order, bcs):
     assert prof[2] == 2  # the run and the final-field copy
     s_ref, p_ref = run_oracle(w)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s_cl, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_cl, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_cl, s_ref, "seismogram")
+    assert_parity(p_cl, p_ref, "field")
 
 
 def test_2d_cluster_run_edge_cases(cuda_device):
@@ -116,7 +121,8 @@ def test_2d_cluster_run_edge_cases(cuda_device):
     s2, p2 = run_gpu(small, variant=api.SW_STENCIL_PLAIN)
     assert np.array_equal(s, s2) and np.array_equal(p, p2)
     s_ref, p_ref = run_oracle(small)
-    assert rel_l2(s, s_ref) <= FP32_SEIS_TOL and rel_l2(p, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s, s_ref, "seismogram")
+    assert_parity(p, p_ref, "field")
     # windows of radius 5: off-grid receivers have ten rows with a non-zero
     # weight, more than the run keeps in registers (the general sampling loop)
     wide = dataclasses.replace(w, window_radius=5)
@@ -132,8 +138,8 @@ def test_tma_kernel_many_segments(cuda_device):
     s_ref, p_ref = run_oracle(w)
     s, p = run_gpu(w, expect_variant=api.SW_STENCIL_TMA)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s, s_ref, "seismogram")
+    assert_parity(p, p_ref, "field")
 
 
 @pytest.mark.parametrize("damp_scale", [1.0, 100.0])
@@ -161,8 +167,8 @@ def test_sources_in_the_absorbing_layers(cuda_device, damp_scale):
     s_gpu, p_gpu, prof = run_gpu(w, profile=True, expect_variant=api.SW_STENCIL_TMA)
     s_ref, p_ref = run_oracle(w)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
     # per forward: the tap table, the final-field copy and (first path) step 0's
     # sources into p[-1]; per step: the stencil, the face launch (and the injection)
     if damp_scale == 1.0:
@@ -182,15 +188,61 @@ def test_2d_homogeneous_full_length(cuda_device):
     w = workloads.make("2d_homogeneous_256")
     s_gpu, p_gpu = run_gpu(w)
     s_ref, p_ref = run_oracle(w)
-    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
 
 
-def test_3d_layered_full_grid_reduced_steps(cuda_device):
-    w = workloads.make("3d_layered_256", n_steps=24)
-    s_gpu, p_gpu = run_gpu(w)
-    s_ref, p_ref = run_oracle(w)
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+def face_sources(w):
+    """Two sources in the absorbing layers near opposite corners (3.4 to 4.6 cells
+    from the z+, y-, x- faces and from the z-, y+, x+ faces) plus the workload's
+    own, and a 25 Hz wavelet with its energy in the first 40 ms, so that a short
+    run drives every face and every layer of the full grid."""
+    import dataclasses
+    nz, ny, nx = w.shape
+    h, nbl = w.spacing, w.nbl
+    cells = [(nz - 1 - 4.3, 4.6, 3.7), (3.4, ny - 1 - 3.8, nx - 1 - 4.2)]
+    pos = [((cz - nbl[0]) * h[0], (cy - nbl[2]) * h[1], (cx - nbl[4]) * h[2]) for cz, cy, cx in cells]
+    src = np.concatenate([np.array(pos), w.src_pos])
+    return dataclasses.replace(w, src_pos=src, f_peak=25.0, t0=0.02)
+
+
+def face_slabs(shape, r):
+    """Index tuples of the r outermost node layers of each face."""
+    out = []
+    for a in range(len(shape)):
+        for side in (slice(0, r), slice(shape[a] - r, shape[a])):
+            idx = [slice(None)] * len(shape)
+            idx[a] = side
+            out.append(tuple(idx))
+    return out
+
+
+def assert_faces_driven(p, r):
+    """Each face's r outermost node layers carry a sizeable part of the field."""
+    peak = np.abs(p).max()
+    for idx in face_slabs(p.shape, r):
+        assert np.abs(p[idx]).max() > 1e-3 * peak, idx
+
+
+def assert_face_parity(p_gpu, p_ref, r):
+    """Element-wise bar on each face slab against that slab's own peak (the field
+    there is far smaller than in the interior behind the absorbing layers)."""
+    for k, idx in enumerate(face_slabs(p_ref.shape, r)):
+        assert_parity(p_gpu[idx], p_ref[idx], "face slab %d" % k, tol=FACE_TOL, max_tol=FACE_TOL)
+
+
+def test_3d_layered_full_grid_faces(cuda_device):
+    """Full 256^3 grid of the order-8 workload, 120 steps with sources next to every
+    face: every node of the field (faces, layers, ragged tiles included) and every
+    receiver sample within the bars."""
+    w = face_sources(workloads.make("3d_layered_256", n_steps=120))
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
+    s_gpu, p_gpu = run_gpu(w, wavelet=wav, expect_variant=api.SW_STENCIL_TMA)
+    s_ref, p_ref = run_oracle(w, wavelet=wav)
+    assert_faces_driven(p_ref, w.order // 2)
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
+    assert_face_parity(p_gpu, p_ref, w.order // 2)
 
 
 def test_3d_layered_reduced_grid_long(cuda_device):
@@ -198,8 +250,8 @@ def test_3d_layered_reduced_grid_long(cuda_device):
     s_gpu, p_gpu = run_gpu(w)
     s_ref, p_ref = run_oracle(w)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
 
 
 def test_3d_variable_density_reduced_grid(cuda_device):
@@ -207,16 +259,22 @@ def test_3d_variable_density_reduced_grid(cuda_device):
     s_gpu, p_gpu = run_gpu(w)
     s_ref, p_ref = run_oracle(w)
     assert np.abs(s_ref).max() > 0
-    assert rel_l2(s_gpu, s_ref) <= FP32_SEIS_TOL
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
 
 
-def test_3d_variable_density_full_grid_few_steps(cuda_device):
-    w = workloads.make("3d_vd_512x512x384", n_steps=6)
-    _, p_gpu = run_gpu(w)
-    _, p_ref = run_oracle(w)
-    assert np.abs(p_ref).max() > 0
-    assert rel_l2(p_gpu, p_ref) <= FP32_SEIS_TOL
+def test_3d_variable_density_full_grid_faces(cuda_device):
+    """Full 384 x 512 x 512 grid of the order-16 variable-density workload, 50
+    steps with sources next to every face (the wave crosses the 8-node ghost
+    reach of each face and enters every layer), element-wise."""
+    w = face_sources(workloads.make("3d_vd_512x512x384", n_steps=50))
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
+    s_gpu, p_gpu = run_gpu(w, wavelet=wav, expect_variant=api.SW_STENCIL_TMA)
+    s_ref, p_ref = run_oracle(w, wavelet=wav)
+    assert_faces_driven(p_ref, w.order // 2)
+    assert_parity(s_gpu, s_ref, "seismogram")
+    assert_parity(p_gpu, p_ref, "field")
+    assert_face_parity(p_gpu, p_ref, w.order // 2)
 
 
 def test_full_length_prefix_and_invariances(cuda_device):
@@ -228,7 +286,8 @@ def test_full_length_prefix_and_invariances(cuda_device):
     s_full, _ = run_gpu(w, wavelet=wav, final=False)
     k = 40
     s_ref, _ = run_oracle(w, n_steps=k)
-    assert rel_l2(s_full[:k], s_ref) <= FP32_SEIS_TOL or np.abs(s_ref).max() == 0
+    assert np.abs(s_ref).max() > 0
+    assert_parity(s_full[:k], s_ref, "seismogram prefix")
     m = 25
     wav_shift = np.concatenate([np.zeros(m, np.float32), wav[:-m]])
     s_shift, _ = run_gpu(w, wavelet=wav_shift, final=False)
@@ -238,7 +297,7 @@ def test_full_length_prefix_and_invariances(cuda_device):
     # leading edge of the wavefield is, and from there on the two runs round
     # independently, so the difference measures the FP32 rounding noise.
     s_double, _ = run_gpu(w, wavelet=2.0 * wav, final=False)
-    assert rel_l2(s_double, 2.0 * s_full) <= FP32_SEIS_TOL
+    assert_parity(s_double, 2.0 * s_full, "seismogram")
     assert np.all(np.isfinite(s_full)) and np.abs(s_full).max() > 0
 
 
@@ -317,7 +376,7 @@ def test_stalled_pipeline_reports_timeout(cuda_device):
         api.sw_set_pipeline_test(g, False, 0)
         api.sw_forward(g, w.n_steps, seis)
         s_ref, _ = run_oracle(w)
-        assert rel_l2(seis.cpu().numpy(), s_ref) <= FP32_SEIS_TOL
+        assert_parity(seis.cpu().numpy(), s_ref, "seismogram")
     finally:
         g.close()
 
@@ -343,7 +402,7 @@ def test_repeated_forwards_replay_identically(cuda_device, ndim):
             runs.append(seis.cpu().numpy())
         assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
         s_ref, _ = run_oracle(w)
-        assert rel_l2(runs[2], s_ref) <= FP32_SEIS_TOL
+        assert_parity(runs[2], s_ref)
         short = torch.zeros((w.n_steps // 2, len(w.rec_pos)), dtype=torch.float32, device=dev)
         api.sw_forward(g, w.n_steps // 2, short)
         assert np.array_equal(short.cpu().numpy(), runs[0][: w.n_steps // 2])
@@ -375,7 +434,7 @@ def test_snapshots_follow_the_saving_stride(cuda_device, ndim):
             api.sw_forward(g, (k + 1) * stride, seis[: (k + 1) * stride], fin)
             assert np.array_equal(snaps[k], fin.cpu().numpy())
         _, p_ref = run_oracle(w, n_steps=4 * stride)
-        assert rel_l2(snaps[3], p_ref) <= FP32_SEIS_TOL
+        assert_parity(snaps[3], p_ref, "seismogram")
         with pytest.raises(api.SimwaveError):
             api.sw_set_saving(g, 2, None, 3)
     finally:
