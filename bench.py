@@ -2,8 +2,9 @@
 
 One bench step = one complete forward simulation of the workload (every
 time step of the leapfrog loop with source injection and receiver sampling),
-inputs resident in HBM.  Default workload: 3d_layered_256 (256^3 nodes,
-order 8, 2000 time steps, 4096 receivers); Gpts/s counts every computed node
+inputs resident in HBM.  Default workload: 3d_vd_512x512x384 (384 x 512 x 512
+nodes, order 16, variable density, 3000 time steps, 16384 receivers), the
+largest single-GPU configuration; Gpts/s counts every computed node
 including the absorbing layer.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
@@ -72,6 +73,12 @@ def _peaks():
 
 STENCIL_SOURCES = ("stencil_plain.cuh", "stencil_tma.cuh", "tma.cuh", "layout.h")
 BATCH_SOURCES = ("batch.cuh", "stencil_plain.cuh", "layout.h")
+# committed ncu traffic record of each workload's dominant kernel (profiles/)
+TRAFFIC_FILES = {
+    "3d_layered_256": ("traffic_stencil_tma_3d_layered_256.txt", STENCIL_SOURCES),
+    "3d_vd_512x512x384": ("traffic_stencil_tma_vd_3d_vd_512x512x384.txt", STENCIL_SOURCES),
+    "2d_shot_batch_64": ("traffic_stencil_batch_2d_shot_batch_64.txt", BATCH_SOURCES),
+}
 
 
 def _kernel_source_hash(names=STENCIL_SOURCES):
@@ -82,21 +89,39 @@ def _kernel_source_hash(names=STENCIL_SOURCES):
     return h.hexdigest()[:16]
 
 
-def _traffic_record(workload, fname="stencil_traffic.txt", names=STENCIL_SOURCES):
-    """DRAM bytes per stencil launch from the committed ncu summary, if still current."""
-    path = os.path.join(ROOT, "profiles", fname)
+def _traffic_record(workload):
+    """DRAM bytes of one launch of the workload's dominant kernel from the
+    committed ncu record (a warm capture: earlier launches' dirty lines are
+    written back inside it, as in the timed run), if the kernel sources still
+    match; None otherwise.  Returns {"total", "read", "write"}."""
+    if workload not in TRAFFIC_FILES:
+        return None
+    fname, names = TRAFFIC_FILES[workload]
     try:
         rec = {}
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", fname)) as f:
             for ln in f:
                 if ":" in ln and not ln.startswith("#"):
                     k, v = ln.split(":", 1)
                     rec[k.strip()] = v.strip()
         if rec.get("workload") != workload or rec.get("source_sha") != _kernel_source_hash(names):
             return None
-        return float(rec["dram_bytes_per_launch"])
+        rd, wr = float(rec["dram_bytes_read"]), float(rec["dram_bytes_write"])
+        return {"total": rd + wr, "read": rd, "write": wr, "capture": rec.get("capture", "")}
     except Exception:
         return None
+
+
+def _roofline_traffic(roof, workload):
+    """Fills roofline["traffic"] (bytes per launch) and its read/write split."""
+    t = _traffic_record(workload)
+    roof["traffic"] = None if t is None else t["total"]
+    if t is not None:
+        roof["traffic_read"] = t["read"]
+        roof["traffic_write"] = t["write"]
+        roof["traffic_vs_algorithmic"] = round(t["total"] / roof["algorithmic_bytes_per_launch"], 4)
+        roof["traffic_capture"] = t["capture"]
+    return roof
 
 
 class ClockSampler:
@@ -159,36 +184,64 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(workload_name, budget_s=12.0):
-    """Times the FP64 oracle on the host cores on a bounded sample of the workload
-    (for a shot batch: on its first shot, the oracle running one shot at a time)."""
-    from paper_2201_05278_b300 import workloads
-    import oracle
-    threads = os.cpu_count() or 1
-    w = workloads.shot_batch()[0] if workload_name in workloads.BATCH_NAMES else workloads.make(workload_name)
-    wav = oracle.ricker_samples(w.f_peak, w.dt, 400, t0=w.t0)
+class OracleRunner:
+    """The FP64 oracle's forward loop on a workload, set up once: FD weights,
+    damping profile, ln(rho) and window weights are prepared before any timing
+    (oracle.forward would redo them on every call); run(k) times one call of
+    the leapfrog loop for k time steps, its per-call padding and copies
+    included.  A shot batch is timed on its first shot (the oracle runs one
+    shot at a time)."""
 
-    def run(steps):
+    def __init__(self, workload_name):
+        from paper_2201_05278_b300 import workloads
+        import oracle
+        self.oracle = oracle
+        self.threads = os.cpu_count() or 1
+        w = workloads.shot_batch()[0] if workload_name in workloads.BATCH_NAMES else workloads.make(workload_name)
+        self.w = w
+        nbl_lo = [w.nbl[2 * a] for a in range(w.ndim)]
+        self.eta = oracle.eta_field(w.shape, w.nbl, w.damp_alpha, w.damp_degree)
+        self.lnrho = None if w.density is None else np.log(w.density.astype(np.float64))
+        b = oracle.KAISER_B[w.window_radius]
+        self.src = oracle.point_windows([tuple(p) for p in w.src_pos], w.ndim, w.spacing, nbl_lo, w.window_radius, b,
+                                        w.shape)
+        self.rec = oracle.point_windows([tuple(p) for p in w.rec_pos], w.ndim, w.spacing, nbl_lo, w.window_radius, b,
+                                        w.shape)
+        bc = [{"none": 0, "null_dirichlet": 1, "null_neumann": 2}[x] for x in w.bc]
+        self.bc6 = bc if w.ndim == 3 else [bc[0], bc[1], 0, 0, bc[2], bc[3]]
+        self.vel = w.velocity.astype(np.float64)
+        self.nodes = w.nodes
+
+    def run(self, steps):
+        w = self.w
+        wav = self.oracle.ricker_samples(w.f_peak, w.dt, max(steps, 1), t0=w.t0)
         t = time.perf_counter()
-        oracle.forward(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt, steps,
-                       src_pos=[tuple(p) for p in w.src_pos], wavelet=np.asarray(wav),
-                       rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc, damp_alpha=w.damp_alpha,
-                       damp_degree=w.damp_degree,
-                       rho=None if w.density is None else w.density.astype(np.float64),
-                       window_radius=w.window_radius, threads=threads)
+        self.oracle.run_raw(w.ndim, w.shape, w.spacing, w.order, self.bc6, self.eta, w.dt, self.vel, self.lnrho,
+                            self.src, wav, self.rec, steps, threads=self.threads)
         return time.perf_counter() - t
 
-    # calibrate: a call costs set-up (windows, padded copies) plus a per-step loop
-    t1 = run(1)
-    t3 = run(3)
-    per_step = max((t3 - t1) / 2.0, 1e-4)
-    setup = max(t1 - per_step, 0.0)
-    steps = int(max(2, min(400, (budget_s - setup) / per_step)))
-    t = run(steps)
-    value = w.nodes * steps / t / 1e9  # whole call, set-up included
-    return {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%s full grid %s, %d of %d time steps, FP64, %d threads" % (
-                w.name, "x".join(map(str, w.shape)), steps, w.n_steps, threads)}, t
+    def steps_for(self, budget_s):
+        """Time steps of one call that take about budget_s (calibrated on 1 and 2 steps)."""
+        t1 = self.run(1)
+        t2 = self.run(2)
+        per_step = max(t2 - t1, 1e-4)
+        setup = max(t1 - per_step, 0.0)
+        return int(max(1, min(400, (budget_s - setup) / per_step)))
+
+    def describe(self, steps):
+        w = self.w
+        return "%s full grid %s, %d of %d time steps per call, FP64, %d threads (set-up of weights, damping " \
+               "and windows once, outside the timing)" % (w.name, "x".join(map(str, w.shape)), steps, w.n_steps,
+                                                          self.threads)
+
+
+def cpu_baseline(workload_name, budget_s=12.0):
+    """Times the FP64 oracle on the host cores on a bounded sample of the workload."""
+    r = OracleRunner(workload_name)
+    steps = r.steps_for(budget_s)
+    t = r.run(steps)
+    return {"value": round(r.nodes * steps / t / 1e9, 4), "unit": UNIT, "cores": r.threads, "kind": "oracle",
+            "sample": r.describe(steps)}, t
 
 
 def run_batch(args, world, rank, local, dev):
@@ -285,7 +338,6 @@ def run_batch(args, world, rank, local, dev):
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
     alg_bytes = 12 * shot_nodes + 4 * model_nodes
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic = _traffic_record(args.workload, "batch_traffic.txt", BATCH_SOURCES)
     for g in grids:
         g.close()
     if rank == 0:
@@ -301,11 +353,12 @@ def run_batch(args, world, rank, local, dev):
                            tile_rows, ", ".join("%.1f" % t for t in tuned_us)),
                        "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
             "unbatched": unbatched,
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "batched stencil (CUDA events around every %dth launch, %d launches timed)" % (
-                             PROFILE_EVERY, stencil_launches),
-                         "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+            "roofline": _roofline_traffic(
+                {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(achieved / peak, 4), "traffic": None,
+                 "kernel": "batched stencil (CUDA events around every %dth launch, %d launches timed)" % (
+                     PROFILE_EVERY, stencil_launches),
+                 "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}, args.workload),
             "e2e": e2e,
             "gpu_launches": int(kernels),
             "clocks": clk,
@@ -492,7 +545,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="3d_layered_256")
+    ap.add_argument("--workload", default="3d_vd_512x512x384")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="override the workload's time steps per forward (profiling runs only)")
@@ -505,15 +558,17 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        per, secs = [], 0.0
+        # each bench step: one call of the oracle's loop for a bounded number of
+        # time steps (about 3 s), the set-up done once before the warm-up
+        runner = OracleRunner(args.workload)
+        k = runner.steps_for(3.0)
         for _ in range(args.warmup):
-            cpu_baseline(args.workload, budget_s=2.0)
+            runner.run(k)
+        secs = 0.0
         for _ in range(args.steps):
-            cb, t = cpu_baseline(args.workload, budget_s=6.0)
-            per.append(cb["value"])
-            secs += t
-        v = statistics.median(per)
-        cb["value"] = v
+            secs += runner.run(k)
+        v = round(runner.nodes * k * args.steps / secs / 1e9, 5)
+        cb = {"value": v, "unit": UNIT, "cores": runner.threads, "kind": "oracle", "sample": runner.describe(k)}
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -607,7 +662,6 @@ def main():
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
     alg_bytes = BYTES_PER_UPDATE[vd] * w.nodes
     achieved = alg_bytes / avg_launch_s / 1e9
-    traffic = _traffic_record(args.workload)
     api.sw_destroy_grid(g)
 
     if rank == 0:
@@ -622,13 +676,14 @@ def main():
                        if alg_bytes > 126e6 else
                        ("working set fits in L2 (%.1f MB per time step): latency-bound, HBM is not the bound"
                         % (alg_bytes / 1e6))},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": ("cluster-resident 2D run (one launch per forward with CUDA events around "
-                                    "it, counted as %d time steps)" % stencil_launches) if cluster_run else
-                                   ("stencil (CUDA events around every %dth launch, %d launches timed)" % (
-                                       PROFILE_EVERY, stencil_launches)),
-                         "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+            "roofline": _roofline_traffic(
+                {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(achieved / peak, 4), "traffic": None,
+                 "kernel": ("cluster-resident 2D run (one launch per forward with CUDA events around "
+                            "it, counted as %d time steps)" % stencil_launches) if cluster_run else
+                           ("stencil (CUDA events around every %dth launch, %d launches timed)" % (
+                               PROFILE_EVERY, stencil_launches)),
+                 "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}, args.workload),
             "e2e": e2e,
             "gpu_launches": int(kernels),
             "clocks": clk,

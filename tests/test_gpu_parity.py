@@ -19,8 +19,9 @@ pytestmark = pytest.mark.gpu
 
 # Face slabs are compared against their own norm and peak, about a hundred
 # times smaller than the field's: the bar there is relative to the local
-# amplitude (a wrong face row or ghost image is an error of order one there).
-FACE_TOL = 1e-3
+# amplitude (a wrong face row or ghost image is an error of order one there;
+# FP32 rounding measured 8e-6 at most on the full-grid runs).
+FACE_TOL = 5e-5
 
 
 def small_case(ndim, order, density, seed=0, n_steps=60):

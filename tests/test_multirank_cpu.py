@@ -31,7 +31,7 @@ def _rank(rank, world, port, local_seconds, out):
 def test_two_replicas_report_the_slowest_rank():
     world = 2
     local = [0.5, 2.0]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), local, out), nprocs=world, join=True)
         res = dict(out)
