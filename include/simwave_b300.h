@@ -172,6 +172,34 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
                       float* grad_rho, int checkpoint_every, int checkpoint_format);
 
 /*
+ * sw_gradient_shots -- the misfit and its gradient summed over several shots
+ * (the objective of full-waveform inversion, the use the paper names in
+ * Sec. 1 and 6, is a sum over shots; the paper prints no adjoint).  Shot s
+ * runs the acquisition's sources moved to its own positions, with the
+ * acquisition's receivers and wavelet, against its own observed data; the
+ * call returns J = sum_s J_s, dJ/dc = sum_s dJ_s/dc and, with a density
+ * model, dJ/drho = sum_s dJ_s/drho.  Each shot runs exactly what
+ * sw_gradient runs; the gradient accumulators, checkpoints and segment
+ * buffers are allocated once for all shots, and the velocity gradient is
+ * formed once from the summed accumulator.
+ *   n_shots          >= 1
+ *   shot_src_pos     host FP64 [n_shots][n_src][ndim]: every shot's source
+ *                    positions (metres, as in sw_set_acquisition; n_src is
+ *                    the acquisition's source count, >= 1); all windows are
+ *                    checked before any device work
+ *   observed         [n_shots][n_steps][n_rec] FP32, device or host
+ *   misfit, grad_vel, grad_rho, checkpoint_every, checkpoint_format: as in
+ *                    sw_gradient (the sums over the shots)
+ * The acquisition keeps its own source positions afterwards.  Device memory
+ * as one sw_gradient call.  Errors: as sw_gradient; SW_EINVAL for
+ * n_shots < 1, NULL positions, an acquisition without sources or a shot
+ * window that leaves the grid.
+ */
+sw_status sw_gradient_shots(sw_grid* g, int n_shots, const double* shot_src_pos, int n_steps, const float* observed,
+                            double* misfit, float* grad_vel, float* grad_rho, int checkpoint_every,
+                            int checkpoint_format);
+
+/*
  * Memory-capped schedule for sw_gradient: with max_states = s > 0 the adjoint
  * sweep keeps at most s forward states (pairs of padded FP32 levels) besides
  * two working levels and follows the binomial checkpointing schedule (the

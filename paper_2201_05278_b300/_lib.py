@@ -35,6 +35,9 @@ SIGNATURES = {
     "sw_set_initial_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sw_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sw_gradient_shots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_int]),
     "sw_get_stencil_variant": (ctypes.c_int, [ctypes.c_void_p, _c_ip]),
     "sw_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sw_get_profile": (ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_i64p, _c_i64p]),

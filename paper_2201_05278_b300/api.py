@@ -141,6 +141,26 @@ def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int
     return j.value
 
 
+def sw_gradient_shots(g: Grid, shot_src_pos, n_steps: int, observed, grad_vel, checkpoint_every: int = 0,
+                      checkpoint_format: int = SW_CKPT_FP32, grad_rho=None) -> float:
+    """Misfit and gradient summed over shots: shot s moves the acquisition's
+    sources to shot_src_pos[s] ([n_shots][n_src][ndim] or [n_shots][ndim] for
+    one source per shot, metres) and is compared with observed[s]
+    ([n_shots][n_steps][n_rec]); returns sum_s J_s, writes sum_s dJ_s/dc into
+    grad_vel (and sum_s dJ_s/drho into grad_rho)."""
+    pos = np.ascontiguousarray(np.asarray(shot_src_pos, dtype=np.float64))
+    n_shots = int(pos.shape[0])
+    if n_shots < 1 or pos.size % (n_shots * g.ndim) != 0:
+        raise ValueError("shot_src_pos must be [n_shots][n_src][ndim]")
+    if int(np.prod(observed.shape)) != n_shots * int(n_steps) * g.n_rec:
+        raise ValueError("observed must hold [n_shots][n_steps][n_rec] = %d values" % (n_shots * n_steps * g.n_rec))
+    j = ctypes.c_double()
+    _check(_lib.load().sw_gradient_shots(g.handle, n_shots, pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(n_steps), _ptr(observed), ctypes.byref(j), _ptr(grad_vel),
+                                         _ptr(grad_rho), int(checkpoint_every), int(checkpoint_format)))
+    return j.value
+
+
 def _f32(a):
     """A contiguous FP32 view of a tensor or array (tensors pass through)."""
     if a is None or hasattr(a, "data_ptr"):

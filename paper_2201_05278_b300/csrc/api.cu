@@ -1275,9 +1275,15 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   return SW_OK;
 }
 
-sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
-                      float* grad_rho, int checkpoint_every, int checkpoint_format) {
-  g_last_error.clear();
+// The misfit gradient of sw_gradient (n_shots = 1, shot_src_pos = NULL: the
+// acquisition's own sources) and of sw_gradient_shots (shot s runs with the
+// sources at shot_src_pos + s * n_src * ndim and the observed data at
+// observed + s * n_steps * n_rec).  Misfit and gradient accumulators,
+// checkpoints and segment buffers are shared by all shots; the acquisition's
+// own source windows are put back afterwards.
+static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_pos, int n_steps, const float* observed,
+                        double* misfit, float* grad_vel, float* grad_rho, int checkpoint_every,
+                        int checkpoint_format) {
   if (!g || !observed || !misfit || !grad_vel) return fail(SW_EINVAL, "NULL argument");
   if (!g->has_model) return fail(SW_ESTATE, "sw_gradient before sw_set_model");
   if (!g->has_acq) return fail(SW_ESTATE, "sw_gradient before sw_set_acquisition");
@@ -1287,6 +1293,18 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   if (g->n_rec <= 0) return fail(SW_EINVAL, "the gradient needs receivers");
   if (n_steps < 1) return fail(SW_EINVAL, "n_steps < 1");
   if (g->n_src > 0 && n_steps > g->nt) return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length (%d)", n_steps, g->nt);
+  if (n_shots < 1) return fail(SW_EINVAL, "n_shots < 1");
+  if (shot_src_pos && g->n_src < 1) return fail(SW_EINVAL, "shots need an acquisition with sources");
+  // every shot's source windows, built (and checked) before any device work
+  std::vector<std::vector<int>> shot_first;
+  std::vector<std::vector<float>> shot_w;
+  if (shot_src_pos) {
+    shot_first.resize(size_t(n_shots));
+    shot_w.resize(size_t(n_shots));
+    for (int sh = 0; sh < n_shots; ++sh)
+      SW_TRY(build_windows(g, g->n_src, shot_src_pos + size_t(sh) * g->n_src * g->ndim, true,
+                           shot_first[size_t(sh)], shot_w[size_t(sh)]));
+  }
   if (checkpoint_every < 0) return fail(SW_EINVAL, "checkpoint_every < 0");
   if (checkpoint_format != SW_CKPT_FP32 && checkpoint_format != SW_CKPT_BF16 && checkpoint_format != SW_CKPT_FP16 &&
       checkpoint_format != SW_CKPT_I16)
@@ -1362,7 +1380,6 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     SW_CUDA(cudaMemsetAsync(scales, 0, sizeof(unsigned) * 2 * nseg, st));
     if (i16) SW_TRY(dev_alloc(g, (void**)&row_scales, sizeof(float) * size_t(nrows) * 2 * nseg));
   }
-  SW_CUDA(cudaMemcpyAsync(obs, observed, sbytes, cudaMemcpyDefault, st));
   SW_CUDA(cudaMemsetAsync(macc, 0, sizeof(double), st));
   auto ck = [&](int sgm, int i) { return F[size_t(2 * sgm + i)]; };  // FP32: i = 0: p[k0-1], 1: p[k0]
   auto B = [&](int j) { return F[size_t(nck + j)]; };                 // p[k0 + j - 1]
@@ -1421,6 +1438,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     lc.c[2][j] = a.cx[j];
   }
   int64_t nk = 0;  // kernels launched by this call
+  int pending_src = -1;  // the adjoint step whose source imaging is still to come
   // one step p[n] (pn), p[n-1] (pm) -> p[n+1] (po), with sources at step n
   auto step = [&](float* pn, float* pm, float* po, const StepMaps* m, int n, const float* sig, int sig_stride,
                   const PointSet& pts, const PointSet& recs, float* seis) -> sw_status {
@@ -1441,6 +1459,43 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     return SW_OK;
   };
 
+  // the acquisition's own source windows, put back after the shots
+  std::vector<int> own_first;
+  std::vector<float> own_w;
+  const size_t nfirst = size_t(g->n_src) * 3, nw = size_t(g->n_src) * 3 * g->L;
+  if (shot_src_pos) {
+    own_first.resize(nfirst);
+    own_w.resize(nw);
+    SW_CUDA(cudaMemcpyAsync(own_first.data(), g->src_first, nfirst * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(cudaMemcpyAsync(own_w.data(), g->src_w, nw * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(cudaStreamSynchronize(st));
+  }
+  struct RestoreSources {
+    sw_grid* g;
+    const std::vector<int>* f;
+    const std::vector<float>* w;
+    bool on;
+    ~RestoreSources() {
+      if (!on) return;
+      cudaMemcpyAsync(g->src_first, f->data(), f->size() * sizeof(int), cudaMemcpyHostToDevice, g->stream);
+      cudaMemcpyAsync(g->src_w, w->data(), w->size() * sizeof(float), cudaMemcpyHostToDevice, g->stream);
+      cudaStreamSynchronize(g->stream);
+    }
+  } restore{g, &own_first, &own_w, shot_src_pos != nullptr};
+
+  for (int shot = 0; shot < n_shots; ++shot) {
+  if (shot_src_pos) {  // this shot's sources (the copies are ordered before the shot's kernels)
+    SW_CUDA(cudaMemcpyAsync(g->src_first, shot_first[size_t(shot)].data(), nfirst * sizeof(int),
+                            cudaMemcpyHostToDevice, st));
+    SW_CUDA(cudaMemcpyAsync(g->src_w, shot_w[size_t(shot)].data(), nw * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
+  SW_CUDA(cudaMemcpyAsync(obs, observed + size_t(shot) * N * g->n_rec, sbytes, cudaMemcpyDefault, st));
+  if (shot > 0) {  // the adjoint levels and the 16-bit scales start from zero for every shot
+    SW_CUDA(cudaMemsetAsync(PSI(0), 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(PSI(1), 0, fbytes, st));
+    if (packed) SW_CUDA(cudaMemsetAsync(scales, 0, sizeof(unsigned) * 2 * nseg, st));
+  }
+  pending_src = -1;
   // forward, keeping (p[k0-1], p[k0]) at every segment start
   SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
   SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
@@ -1486,7 +1541,6 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   // backward: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
   // one adjoint step: psi[k] from psi[k+1], psi[k+2], then its imaging
   // terms with the forward state p[k-1] (pk1, ghosts set)
-  int pending_src = -1;  // the adjoint step whose source imaging is still to come
   auto adjoint_step = [&](int k, float* pk1) -> sw_status {
     nk += 4 + (vd ? 1 : 0);
     float* p1 = PSI((k + 1) & 1);  // psi[k+1]
@@ -1630,6 +1684,7 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
     SW_CUDA(cudaGetLastError());
     ++nk;
   }
+  }  // shots
   // dJ/dc, densely per node
   float* out = grad_vel;
   const bool host_out = !is_device_pointer(grad_vel);
@@ -1658,10 +1713,28 @@ sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* mi
   SW_TRY(check_device_flag(g));
   // + residual and velocity gradient, density gradient, ln rho gradients,
   // and per 16-bit checkpoint segment absmax + pack and unpack + faces of two levels
-  g->kernel_launches = nk + 2 + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) + (packed ? (i16 ? 6 : 8) * int64_t(nseg) : 0);
+  g->kernel_launches = nk + 1 + n_shots + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) +
+                       (packed ? (i16 ? 6 : 8) * int64_t(nseg) * n_shots : 0);
   g->stencil_launches = 0;
   g->stencil_ms = 0.0;
   return SW_OK;
+}
+
+sw_status sw_gradient(sw_grid* g, int n_steps, const float* observed, double* misfit, float* grad_vel,
+                      float* grad_rho, int checkpoint_every, int checkpoint_format) {
+  g_last_error.clear();
+  return gradient_impl(g, 1, nullptr, n_steps, observed, misfit, grad_vel, grad_rho, checkpoint_every,
+                       checkpoint_format);
+}
+
+sw_status sw_gradient_shots(sw_grid* g, int n_shots, const double* shot_src_pos, int n_steps, const float* observed,
+                            double* misfit, float* grad_vel, float* grad_rho, int checkpoint_every,
+                            int checkpoint_format) {
+  g_last_error.clear();
+  if (!shot_src_pos) return fail(SW_EINVAL, "NULL shot positions");
+  if (g) ++g->config_gen;  // the source windows change during the call (and are put back)
+  return gradient_impl(g, n_shots, shot_src_pos, n_steps, observed, misfit, grad_vel, grad_rho, checkpoint_every,
+                       checkpoint_format);
 }
 
 sw_status sw_get_dt(const sw_grid* g, double* dt) {

@@ -212,3 +212,146 @@ def test_binomial_checkpointing_gives_the_same_gradient(cuda_device, ndim):
             api.sw_set_checkpoint_budget(g, -1)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("density,fmt", [(False, api.SW_CKPT_FP32), (True, api.SW_CKPT_FP32),
+                                         (False, api.SW_CKPT_BF16)])
+def test_gradient_over_shots_is_the_sum_of_the_shots(cuda_device, density, fmt):
+    """sw_gradient_shots over three shots (two sources each) equals the sum of
+    three sw_gradient calls, matches the sum of the FP64 oracle's per-shot
+    gradients, and leaves the acquisition's own sources in place."""
+    import torch
+    from paper_2201_05278_b300 import fwi
+    n = 50
+    w = small_case(3, 8, density, seed=71, n_steps=n)
+    wav = np.asarray(oracle.ricker_samples(w.f_peak, w.dt, n, t0=w.t0), dtype=np.float32)
+    rng = np.random.default_rng(12)
+    v_true = w.velocity.astype(np.float64) * (1.0 + 0.03 * rng.standard_normal(w.shape))
+    r_true = None if not density else w.density.astype(np.float64) * (1.0 + 0.05 * rng.standard_normal(w.shape))
+    h = np.asarray(w.spacing)
+    shots = np.stack([w.src_pos + np.array([1.3, -2.1, 2.7]) * h * k for k in range(3)])  # [3][2][3]
+    kw = dict(rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc, damp_alpha=w.damp_alpha,
+              damp_degree=w.damp_degree, window_radius=w.window_radius)
+    obs = np.stack([oracle.forward(3, w.shape, w.spacing, w.order, v_true, w.dt, n, src_pos=[tuple(p) for p in s],
+                                   wavelet=wav.astype(np.float64), rho=r_true, **kw)[0] for s in shots])
+    obs = obs.astype(np.float32)
+    dev = torch.device("cuda:0")
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev),
+                         None if not density else torch.from_numpy(w.density).to(dev))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        before = torch.zeros((n, len(w.rec_pos)), dtype=torch.float32, device=dev)
+        api.sw_forward(g, n, before)
+        gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+        gr = torch.zeros(w.shape, dtype=torch.float32, device=dev) if density else None
+        obs_d = torch.from_numpy(obs).to(dev)
+        J = api.sw_gradient_shots(g, shots, n, obs_d, gv, 9, fmt, grad_rho=gr)
+        after = torch.zeros_like(before)
+        api.sw_forward(g, n, after)
+        assert torch.equal(before, after)
+        # the same through the shot-partition layer (no process group: every shot here)
+        out = fwi.misfit_gradient(g, shots, obs_d, n, 9, fmt, density=density)
+        assert out[0] == pytest.approx(J, rel=1e-9)  # atomic sums: equal up to their order
+        assert rel_l2(out[1].cpu().numpy(), gv.cpu().numpy()) <= 1e-6
+        # shot by shot
+        J1, gv1 = 0.0, torch.zeros_like(gv)
+        gr1 = torch.zeros_like(gv) if density else None
+        for k in range(3):
+            api.sw_set_acquisition(g, shots[k], w.rec_pos, wav, window_radius=w.window_radius)
+            tv = torch.zeros_like(gv)
+            tr = torch.zeros_like(gv) if density else None
+            J1 += api.sw_gradient(g, n, obs_d[k], tv, 9, fmt, grad_rho=tr)
+            gv1 += tv
+            if density:
+                gr1 += tr
+    finally:
+        g.close()
+    assert J == pytest.approx(J1, rel=1e-6)
+    assert rel_l2(gv.cpu().numpy(), gv1.cpu().numpy()) <= 1e-6
+    if density:
+        assert rel_l2(gr.cpu().numpy(), gr1.cpu().numpy()) <= 1e-6
+    if fmt == api.SW_CKPT_FP32:
+        J_ref, gv_ref, gr_ref = 0.0, 0.0, 0.0
+        for k in range(3):
+            pb = A.make_problem(3, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
+                                src_pos=[tuple(p) for p in shots[k]],
+                                rho=None if not density else w.density.astype(np.float64), **kw)
+            j, a, b, _ = A.adjoint_gradient_full(pb, wav.astype(np.float64), obs[k].astype(np.float64), n)
+            J_ref, gv_ref, gr_ref = J_ref + j, gv_ref + a, gr_ref + (b if density else 0.0)
+        assert J == pytest.approx(J_ref, rel=1e-4)
+        assert rel_l2(gv.cpu().numpy(), gv_ref) <= GRAD_TOL
+        if density:
+            assert rel_l2(gr.cpu().numpy(), gr_ref) <= GRAD_TOL
+
+
+def test_gradient_over_shots_rejects_bad_shots(cuda_device):
+    import torch
+    w, wav, obs, _ = _setup(3, 8, 20, seed=5)
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    try:
+        api.sw_set_model(g, np.ascontiguousarray(w.velocity, np.float32))
+        api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
+        gv = torch.zeros(w.shape, dtype=torch.float32, device="cuda:0")
+        bad = np.stack([w.src_pos, w.src_pos + 1e6])  # the second shot's windows leave the grid
+        with pytest.raises(api.SimwaveError) as e:
+            api.sw_gradient_shots(g, bad, 20, np.stack([obs, obs]), gv)
+        assert e.value.status == api.SW_EINVAL
+        with pytest.raises(ValueError):
+            api.sw_gradient_shots(g, np.stack([w.src_pos] * 2), 20, obs, gv)  # observed for one shot only
+    finally:
+        g.close()
+
+
+# The misfit-gradient workload (256^3, 1500 steps, checkpoints every 10
+# steps) reduced to 96^3 and 200 steps (20 checkpoints), against the FP64
+# adjoint oracle.  Bars: FP32 checkpoints carry only the FP32 forward and
+# adjoint (GRAD_TOL); the 16-bit formats add the rounding of the states the
+# recomputed segments start from.  The 1e-2 bar for compressed snapshots is
+# met by FP16 and the row-scaled 16-bit fixed point; BF16 (8 mantissa bits)
+# is reported, with a loose bound that only catches a broken path.
+REDUCED_FWI_TOL = {api.SW_CKPT_FP32: GRAD_TOL, api.SW_CKPT_I16: 1e-2, api.SW_CKPT_FP16: 1e-2,
+                   api.SW_CKPT_BF16: 0.3}
+
+
+def test_checkpoint_formats_on_the_reduced_fwi_workload(cuda_device):
+    import json
+    import os
+    import torch
+    from paper_2201_05278_b300 import workloads
+    c = workloads.fwi_gradient_256(n_steps=200, shape=(96, 96, 96))
+    w = c.base
+    n = w.n_steps
+    dev = torch.device("cuda:0")
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, n)
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    grads, Js = {}, {}
+    try:
+        api.sw_set_model(g, torch.from_numpy(c.v_true).to(dev))
+        api.sw_set_acquisition(g, c.shots[:1], w.rec_pos, wav, window_radius=w.window_radius)
+        obs = torch.zeros((n, len(w.rec_pos)), dtype=torch.float32, device=dev)
+        api.sw_forward(g, n, obs)
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+        for fmt in REDUCED_FWI_TOL:
+            gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+            Js[fmt] = api.sw_gradient(g, n, obs, gv, c.checkpoint_every, fmt)
+            grads[fmt] = gv.cpu().numpy()
+        obs = obs.cpu().numpy()
+    finally:
+        g.close()
+    pb = A.make_problem(3, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
+                        src_pos=[tuple(c.shots[0])], rec_pos=[tuple(p) for p in w.rec_pos], nbl=w.nbl, bc=w.bc,
+                        damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
+    J_ref, g_ref, _ = A.adjoint_gradient(pb, np.asarray(wav, np.float64), obs.astype(np.float64), n)
+    errs = {fmt: rel_l2(grads[fmt], g_ref) for fmt in grads}
+    names = {api.SW_CKPT_FP32: "fp32", api.SW_CKPT_BF16: "bf16", api.SW_CKPT_FP16: "fp16", api.SW_CKPT_I16: "i16"}
+    print("reduced fwi workload, gradient rel-L2 against the FP64 oracle: " +
+          ", ".join("%s %.3e" % (names[f], e) for f, e in errs.items()))
+    log = os.environ.get("PARITY_LOG")
+    if log:
+        with open(log, "a") as f:
+            f.write(json.dumps({"test": "reduced_fwi_checkpoint_formats",
+                                "rel_l2": {names[k]: v for k, v in errs.items()}}) + "\n")
+    for fmt, e in errs.items():
+        assert Js[fmt] == pytest.approx(J_ref, rel=1e-4)
+        assert e <= REDUCED_FWI_TOL[fmt], (names[fmt], e)
