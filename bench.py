@@ -394,18 +394,62 @@ def gradient_cpu_baseline(budget_s=15.0):
     steps = int(max(2, min(60, budget_s / max(t1, 1e-3))))
     t = run(steps)
     return {"value": round(w.nodes * steps / t / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "3d_fwi_gradient_256 recipe on a 96^3 grid with 64 receivers, %d time steps (forward "
-                      "states, adjoint sweep, imaging), FP64 numpy" % steps}, t
+            "sample": "3d_fwi_gradient_256 recipe on a 96^3 grid with 64 receivers, one shot, %d time steps "
+                      "(forward states, adjoint sweep, imaging), FP64 numpy" % steps}, t
+
+
+CKPT_NAMES = {0: "fp32", 1: "bf16", 2: "fp16", 3: "i16"}
+
+
+def gradient_error_reduced(dev):
+    """Each checkpoint format's gradient error against the FP64 adjoint oracle
+    on the misfit-gradient recipe reduced to 96^3 and 200 time steps (20
+    checkpoints of 10 steps), one shot; observed data from the true model by
+    the GPU forward.  The oracle part takes about a minute of CPU."""
+    import torch
+    from paper_2201_05278_b300 import api, workloads
+    from oracle import adjoint as A
+    c = workloads.fwi_gradient_256(n_steps=200, shape=(96, 96, 96))
+    w = c.base
+    n = w.n_steps
+    wav = api.sw_ricker(w.f_peak, w.t0, w.dt, n)
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
+    grads = {}
+    try:
+        api.sw_set_model(g, torch.from_numpy(c.v_true).to(dev))
+        api.sw_set_acquisition(g, c.shots[:1], w.rec_pos, wav, window_radius=w.window_radius)
+        obs = torch.zeros((n, len(w.rec_pos)), dtype=torch.float32, device=dev)
+        api.sw_forward(g, n, obs)
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+        for fmt in CKPT_NAMES:
+            gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+            api.sw_gradient(g, n, obs, gv, c.checkpoint_every, fmt)
+            grads[fmt] = gv.cpu().numpy().astype(np.float64)
+        obs = obs.cpu().numpy().astype(np.float64)
+    finally:
+        g.close()
+    pb = A.make_problem(3, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
+                        src_pos=[tuple(c.shots[0])], rec_pos=[tuple(q) for q in w.rec_pos], nbl=w.nbl, bc=w.bc,
+                        damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
+    _, g_ref, _ = A.adjoint_gradient(pb, np.asarray(wav, np.float64), obs, n)
+    nr = float(np.linalg.norm(g_ref))
+    return {CKPT_NAMES[f] + "_rel_l2": round(float(np.linalg.norm(grads[f] - g_ref)) / nr, 6) for f in CKPT_NAMES}
 
 
 def run_gradient(args, world, rank, local, dev):
-    """Misfit gradients of 3d_fwi_gradient_256: a bench step is one shot's
-    sw_gradient (forward with BF16 checkpoints every 10 steps, residual,
-    adjoint sweep with recomputation and imaging), the shots taken in turn;
-    Gpts/s counts the forward's grid-point updates per second of gradient."""
+    """Misfit gradient of 3d_fwi_gradient_256: a bench step is the gradient of
+    the whole 16-shot objective, J = sum_s J_s and dJ/dc = sum_s dJ_s/dc
+    (fwi.misfit_gradient: under torchrun rank r runs shots r, r + N, ... with
+    one sw_gradient_shots call and one all-reduce sums misfit and gradient;
+    strong scaling, the 16 shots are the whole job).  Each shot: forward with
+    16-bit checkpoints every 10 steps (SW_CKPT_I16, the format within the
+    1e-2 bar at this scale), residual, adjoint sweep with recomputation and
+    imaging.  Gpts/s counts the forward's grid-point updates of all shots per
+    second of gradient computation."""
     import torch
-    from paper_2201_05278_b300 import api, workloads
+    from paper_2201_05278_b300 import api, fwi, workloads
 
+    fmt = api.SW_CKPT_I16
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
     c = workloads.fwi_gradient_256(n_steps=args.time_steps or None, shape=shape)
     w = c.base
@@ -416,21 +460,17 @@ def run_gradient(args, world, rank, local, dev):
     wav = api.sw_ricker(w.f_peak, w.t0, w.dt, N)
     n_rec = len(w.rec_pos)
     n_shots = len(c.shots)
-    used = [i % n_shots for i in range(args.warmup + args.steps + max(args.e2e_steps, 0))]
+    mine = fwi.shots_of_rank(n_shots, world, rank)
 
-    def shot(i):
-        api.sw_set_acquisition(g, c.shots[i:i + 1], w.rec_pos, wav, window_radius=w.window_radius)
-
-    # observed data from the true model (FP32 forward on the GPU), before timing
+    # observed data of this rank's shots from the true model (FP32 forward on the GPU), before timing
     api.sw_set_model(g, torch.from_numpy(c.v_true).to(dev))
-    obs = {}
-    for i in sorted(set(used)):
-        shot(i)
-        obs[i] = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
+    obs = torch.zeros((n_shots, N, n_rec), dtype=torch.float32, device=dev)
+    for i in mine:
+        api.sw_set_acquisition(g, c.shots[i:i + 1], w.rec_pos, wav, window_radius=w.window_radius)
         api.sw_forward(g, N, obs[i], None)
     api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+    api.sw_set_acquisition(g, c.shots[:1], w.rec_pos, wav, window_radius=w.window_radius)
     # the forward stencil's launch time on this grid, for the roofline line
-    shot(used[0])
     api.sw_set_profiling(g, PROFILE_EVERY)
     tmp = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -441,87 +481,88 @@ def run_gradient(args, world, rank, local, dev):
     forward_ms = f0.elapsed_time(f1)
     st_ms, st_n, _ = api.sw_get_profile(g)
     api.sw_set_profiling(g, 0)
-    grad = torch.empty(w.shape, dtype=torch.float32, device=dev)
 
-    def one(k):
-        shot(used[k])
-        return api.sw_gradient(g, N, obs[used[k]], grad, c.checkpoint_every, api.SW_CKPT_BF16)
+    def step():
+        return fwi.misfit_gradient(g, c.shots, obs, N, c.checkpoint_every, fmt)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    for k in range(args.warmup):
-        one(k)
-    # error of the BF16 checkpoints at this scale: the same shot's gradient
-    # with FP32 checkpoints (untimed; the FP32 path matches the FP64 oracle
-    # within 2e-3 on the test grids)
-    shot(used[0])
-    g_ref = torch.empty_like(grad)
-    api.sw_gradient(g, N, obs[used[0]], g_ref, c.checkpoint_every, api.SW_CKPT_FP32)
-    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_FP16)
-    fp16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
-    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_I16)
-    i16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
-    api.sw_gradient(g, N, obs[used[0]], grad, c.checkpoint_every, api.SW_CKPT_BF16)
-    bf16_err = float(torch.linalg.vector_norm(grad - g_ref) / torch.linalg.vector_norm(g_ref))
-    del g_ref
+    for _ in range(args.warmup):
+        step()
+    # checkpoint formats at this scale against FP32 checkpoints (first shot, untimed)
+    at_scale = {}
+    if not args.no_cpu_baseline:
+        ref = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+        api.sw_gradient_shots(g, c.shots[:1], N, obs[:1], ref, c.checkpoint_every, api.SW_CKPT_FP32)
+        for f in (api.SW_CKPT_BF16, api.SW_CKPT_FP16, api.SW_CKPT_I16):
+            gv = torch.zeros_like(ref)
+            api.sw_gradient_shots(g, c.shots[:1], N, obs[:1], gv, c.checkpoint_every, f)
+            at_scale[CKPT_NAMES[f] + "_vs_fp32_checkpoints_rel_l2"] = round(
+                float(torch.linalg.vector_norm(gv - ref) / torch.linalg.vector_norm(ref)), 6)
+        del ref
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kernels = 0
     start.record(stream)
-    for k in range(args.warmup, args.warmup + args.steps):
-        one(k)
+    for _ in range(args.steps):
+        J, grad = step()
         kernels += api.sw_get_profile(g)[2]
     stop.record(stream)
     barrier()
     clk = clocks.stop()
     elapsed_ms = job_seconds(start.elapsed_time(stop) * 1e-3, world, dev) * 1e3
-    value = job_throughput(w.nodes * N, args.steps, world, elapsed_ms * 1e-3)
+    value = job_throughput(w.nodes * N * n_shots, args.steps, 1, elapsed_ms * 1e-3)
 
-    # e2e: observed data from pinned host memory, the gradient back to it
+    # e2e: every shot's observed data from pinned host memory, the summed gradient back to it
     e2e = None
     if args.e2e_steps > 0:
+        obs_h = obs.cpu().pin_memory()
         grad_h = torch.empty(w.shape, dtype=torch.float32).pin_memory()
-        obs_h = {i: obs[i].cpu().pin_memory() for i in set(used)}
         barrier()
         t0 = time.perf_counter()
-        base = args.warmup + args.steps
-        for k in range(base, base + args.e2e_steps):
-            shot(used[k])
-            api.sw_gradient(g, N, obs_h[used[k]], grad_h, c.checkpoint_every, api.SW_CKPT_BF16)
+        for _ in range(args.e2e_steps):
+            od = obs_h.to(dev, non_blocking=True)
+            J, grad = fwi.misfit_gradient(g, c.shots, od, N, c.checkpoint_every, fmt)
+            grad_h.copy_(grad, non_blocking=True)
+            torch.cuda.synchronize(dev)
             _ = float(grad_h[0, 0, 0])
         barrier()
         e2e_s = job_seconds(time.perf_counter() - t0, world, dev)
-        e2e = {"value": round(job_throughput(w.nodes * N, args.e2e_steps, world, e2e_s), 3), "unit": UNIT,
-               "h2d_bytes_per_step": N * n_rec * 4, "d2h_bytes_per_step": w.nodes * 4}
+        e2e = {"value": round(job_throughput(w.nodes * N * n_shots, args.e2e_steps, 1, e2e_s), 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(obs_h.numel() * 4), "d2h_bytes_per_step": w.nodes * 4}
     g.close()
 
     peak, peak_kind = _peaks()
     alg_bytes = BYTES_PER_UPDATE[False] * w.nodes
     achieved = alg_bytes / (st_ms * 1e-3 / max(st_n, 1)) / 1e9
     if rank == 0:
+        errors = dict(at_scale)
+        if not args.no_cpu_baseline and world == 1:
+            errors["vs_fp64_oracle_reduced"] = gradient_error_reduced(dev)
+            errors["vs_fp64_oracle_reduced_recipe"] = ("the same recipe at 96^3, 200 time steps, checkpoints every "
+                                                       "10 steps, one shot, against the FP64 adjoint oracle")
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "grid": list(w.shape), "space_order": w.order,
                        "time_steps": N, "shots": n_shots, "receivers": n_rec,
-                       "checkpoints": "BF16 pairs with per-snapshot scale every %d steps" % c.checkpoint_every,
-                       "shots_per_s": round(world * args.steps / (elapsed_ms * 1e-3), 4),
+                       "checkpoints": "16-bit fixed point with per-row scale (SW_CKPT_I16) every %d steps"
+                                      % c.checkpoint_every,
+                       "shots_per_s": round(n_shots * args.steps / (elapsed_ms * 1e-3), 4),
+                       "ms_per_shot": round(elapsed_ms / args.steps / n_shots * world, 3),
                        "forward_ms_per_shot": round(forward_ms, 3),
-                       "gradient_error": {"bf16_vs_fp32_checkpoints_rel_l2": round(bf16_err, 6),
-                                          "fp16_vs_fp32_checkpoints_rel_l2": round(fp16_err, 6),
-                                          "i16_vs_fp32_checkpoints_rel_l2": round(i16_err, 6),
-                                          "vs_fp64_oracle": "test grids (tests/test_gpu_gradient.py): "
-                                                            "FP32 checkpoints <= 2e-3, BF16 <= 1e-2, FP16 <= "
-                                                            "2e-3, I16 <= 5e-4"},
-                       "quantity": "forward grid-point updates per second of gradient computation (forward, "
-                                   "residual, adjoint sweep with recomputation, imaging)",
-                       "parallelism": "replicas" if world > 1 else "single",
+                       "gradient_error": errors,
+                       "quantity": "forward grid-point updates of all 16 shots per second of the summed misfit "
+                                   "gradient (per shot: forward, residual, adjoint sweep with recomputation, "
+                                   "imaging)",
+                       "parallelism": ("shots partitioned over %d ranks, one all-reduce of misfit and gradient"
+                                       % world) if world > 1 else "single",
                        "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
@@ -552,11 +593,31 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3, help="forwards timed end to end (0 skips)")
     ap.add_argument("--shape", default="",
                     help="override the workload's grid as nz,ny,nx (profiling runs on a smaller case only)")
+    ap.add_argument("--stencil", default="", choices=["", "auto", "plain", "tb2"],
+                    help="kernel variant (default: the library's choice; tb2 for 2d_layered_4096, with the "
+                         "per-step kernels timed beside it)")
     args = ap.parse_args()
     world, rank, local = _dist()
 
     if args.impl == "reference":
         if rank != 0:
+            return
+        from paper_2201_05278_b300 import workloads as _w
+        if args.workload in _w.GRADIENT_NAMES:  # the FP64 adjoint oracle on the reduced recipe
+            per, secs = [], 0.0
+            for _ in range(args.warmup):
+                gradient_cpu_baseline(budget_s=2.0)
+            for _ in range(args.steps):
+                cb, t = gradient_cpu_baseline(budget_s=3.0)
+                per.append(cb["value"])
+                secs += t
+            v = statistics.median(per)
+            cb["value"] = v
+            print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+                              "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": {"workload": args.workload}, "cpu_baseline": cb,
+                              "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
             return
         # each bench step: one call of the oracle's loop for a bounded number of
         # time steps (about 3 s), the set-up done once before the warm-up
@@ -605,6 +666,11 @@ def main():
     vel_d = torch.from_numpy(w.velocity).to(dev)
     rho_d = None if w.density is None else torch.from_numpy(w.density).to(dev)
     api.sw_set_model(g, vel_d, rho_d)
+    stencil = args.stencil or ("tb2" if args.workload == "2d_layered_4096" else "")
+    variants = {"auto": api.SW_STENCIL_AUTO, "plain": api.SW_STENCIL_PLAIN, "tb2": api.SW_STENCIL_TB2}
+    if stencil:
+        api.sw_set_stencil_variant(g, variants[stencil])
+    two_step = api.sw_get_stencil_variant(g) == api.SW_STENCIL_TB2
     wav = api.sw_ricker(w.f_peak, w.t0, w.dt, w.n_steps)
     api.sw_set_acquisition(g, w.src_pos, w.rec_pos, wav, window_radius=w.window_radius)
     n_rec = len(w.rec_pos)
@@ -658,9 +724,32 @@ def main():
         e2e = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": seis_h.numel() * 4}
 
+    # the two-step run beside the per-step kernels on the same grid
+    per_step = None
+    if two_step and args.workload == "2d_layered_4096" and not args.stencil:
+        api.sw_set_stencil_variant(g, api.SW_STENCIL_PLAIN)
+        api.sw_set_profiling(g, PROFILE_EVERY)
+        for _ in range(2):
+            api.sw_forward(g, w.n_steps, seis, None)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            api.sw_forward(g, w.n_steps, seis, None)
+        p1.record(stream)
+        barrier()
+        pms, pn, _ = api.sw_get_profile(g)
+        api.sw_set_profiling(g, 0)
+        pl_ms = p0.elapsed_time(p1) / args.steps
+        per_step = {"value": round(w.updates / (pl_ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms": round(pl_ms, 3),
+                    "stencil_us_per_step": round(pms * 1e3 / max(pn, 1), 3),
+                    "how": "the same forward on the per-step 2D kernels (SW_STENCIL_PLAIN), same GPU and process"}
     peak, peak_kind = _peaks()
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
-    alg_bytes = BYTES_PER_UPDATE[vd] * w.nodes
+    # algorithmic bytes of one timed launch: one step reads p[n], p[n-1],
+    # kappa (, ln rho) and writes p[n+1]; a two-step launch reads the first
+    # three once and writes two levels
+    alg_bytes = (20 if two_step else BYTES_PER_UPDATE[vd]) * w.nodes
     achieved = alg_bytes / avg_launch_s / 1e9
     api.sw_destroy_grid(g)
 
@@ -681,6 +770,8 @@ def main():
                  "frac": round(achieved / peak, 4), "traffic": None,
                  "kernel": ("cluster-resident 2D run (one launch per forward with CUDA events around "
                             "it, counted as %d time steps)" % stencil_launches) if cluster_run else
+                           ("two-step 2D kernel, two time steps per launch (CUDA events around every %dth "
+                            "launch, %d launches timed)" % (PROFILE_EVERY, stencil_launches)) if two_step else
                            ("stencil (CUDA events around every %dth launch, %d launches timed)" % (
                                PROFILE_EVERY, stencil_launches)),
                  "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}, args.workload),
@@ -688,6 +779,10 @@ def main():
             "gpu_launches": int(kernels),
             "clocks": clk,
         }
+        if two_step:
+            line["config"]["stencil"] = "two time steps per launch (temporal blocking, SW_STENCIL_TB2)"
+        if per_step is not None:
+            line["per_step_kernels"] = per_step
         if not args.no_cpu_baseline and world == 1:
             cb, _ = cpu_baseline(args.workload)
             line["cpu_baseline"] = cb

@@ -248,10 +248,22 @@ sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
  * of kappa per CTA, at most the device's per-block shared memory), without
  * distributed forcing or snapshot frames; other cases use the plain
  * kernels.  It gives the same values as the plain 2D kernels bit for bit.
+ * SW_STENCIL_TB2 asks for temporal blocking (2D only, else SW_EINVAL): two
+ * leapfrog steps per launch, each tile staging p[n] with a 2R ring and
+ * p[n-1], kappa with an R ring in shared memory, computing p[n+1] on the
+ * tile and its ring (step n's sources and the face images included) and
+ * p[n+2] on the tile, then a face pass per new level (ghosts, receivers)
+ * with step n+1's sources in between; 20 bytes of memory traffic per two
+ * node updates instead of 32.  For 2D grids of constant density without
+ * distributed forcing or snapshot frames (others use the plain kernels);
+ * an odd last step runs on the plain kernels; the grid allocates two more
+ * wavefield levels on its first such run.  The levels equal the plain
+ * kernels' bit for bit when no two source taps share a node (the
+ * seismograms agree to rounding: another receiver sampler).
  * sw_get_stencil_variant reports the kernel sw_forward will launch for the
  * current model.
  */
-enum { SW_STENCIL_AUTO = 0, SW_STENCIL_PLAIN = 1, SW_STENCIL_TMA = 2, SW_STENCIL_CLUSTER = 3 };
+enum { SW_STENCIL_AUTO = 0, SW_STENCIL_PLAIN = 1, SW_STENCIL_TMA = 2, SW_STENCIL_CLUSTER = 3, SW_STENCIL_TB2 = 4 };
 sw_status sw_set_stencil_variant(sw_grid* g, int variant);
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant);
 

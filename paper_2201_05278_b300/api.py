@@ -16,7 +16,7 @@ from . import _lib
 
 SW_OK, SW_EINVAL, SW_ECFL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_ESTATE = range(7)
 SW_BC_NONE, SW_BC_DIRICHLET, SW_BC_NEUMANN = 0, 1, 2
-SW_STENCIL_AUTO, SW_STENCIL_PLAIN, SW_STENCIL_TMA, SW_STENCIL_CLUSTER = 0, 1, 2, 3
+SW_STENCIL_AUTO, SW_STENCIL_PLAIN, SW_STENCIL_TMA, SW_STENCIL_CLUSTER, SW_STENCIL_TB2 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "SW_OK", 1: "SW_EINVAL", 2: "SW_ECFL", 3: "SW_ENOMEM", 4: "SW_ECUDA",
                 5: "SW_ETIMEOUT", 6: "SW_ESTATE"}
 BC_NAMES = {"none": SW_BC_NONE, "null_dirichlet": SW_BC_DIRICHLET, "dirichlet": SW_BC_DIRICHLET,

@@ -18,6 +18,7 @@
 #include "cluster2d.cuh"
 #include "stencil_plain.cuh"
 #include "stencil_tma.cuh"
+#include "tb2d.cuh"
 
 using namespace sw;
 
@@ -113,6 +114,8 @@ struct sw_grid {
   Layout lay;
 
   float* u[2] = {nullptr, nullptr};
+  // two more levels for the two-step 2D kernel (SW_STENCIL_TB2), allocated on first use
+  float* u2[2] = {nullptr, nullptr};
   float* kappa = nullptr;
   float* lnrho = nullptr;
   float2* damp = nullptr;
@@ -550,6 +553,47 @@ bool use_tma(const sw_grid* g) {
          n[1] > m && n[2] > m && items < (int64_t(1) << 31) && lines < (int64_t(1) << 31);
 }
 
+// ---- two-step 2D kernel (temporal blocking) ---------------------------------
+
+// The two-step kernel runs 2D constant-density grids when asked for, without
+// distributed forcing or snapshot frames (those need every level).
+bool use_tb2(const sw_grid* g) {
+  return g->variant == SW_STENCIL_TB2 && g->ndim == 2 && !g->has_density && g->n_force == 0 && !g->snapshots &&
+         g->n[0] > 2 * int64_t(g->R) + 1 && g->n[2] > 2 * int64_t(g->R) + 1;
+}
+
+using Tb2Fn = void (*)(const Tb2Args);
+
+template <int R>
+Tb2Fn tb2_fn() {
+  static bool ready = false;
+  if (!ready) {
+    cudaFuncSetAttribute(tb2_2d_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Tb2Smem<R>::BYTES));
+    ready = true;
+  }
+  return tb2_2d_kernel<R>;
+}
+
+void launch_tb2(int R, const Tb2Args& t, unsigned blocks, cudaStream_t st) {
+#define SW_TB2(RR) \
+  case RR: launch_dependent(tb2_fn<RR>(), dim3(blocks), dim3(kTb2Threads), Tb2Smem<RR>::BYTES, st, t); break;
+  switch (R) {
+    SW_TB2(1) SW_TB2(2) SW_TB2(3) SW_TB2(4) SW_TB2(5) SW_TB2(6) SW_TB2(7) SW_TB2(8) SW_TB2(9) SW_TB2(10)
+    default: break;
+  }
+#undef SW_TB2
+}
+
+// Level buffers of a two-step run after `n_steps` steps: the run reads
+// (u0, u1), writes (u2a, u2b), reads those, writes (u0, u1), ...; an odd
+// last step runs in place over the older of the two current levels.
+// Returns the index (0, 1: u, 2, 3: u2) of the buffer holding p[n_steps].
+int tb2_last_level(int n_steps) {
+  const int pairs = n_steps / 2;
+  const int in_n = pairs == 0 ? 0 : (pairs % 2 ? 3 : 1), in_m = pairs == 0 ? 1 : (pairs % 2 ? 2 : 0);
+  return n_steps % 2 ? in_m : in_n;
+}
+
 // ---- cluster-resident 2D forward run -----------------------------------------
 
 using ClusterFn = void (*)(const ClusterRun);
@@ -583,7 +627,9 @@ struct ClusterShape {
 // the per-CTA shared memory and that the device can place.  Every band
 // holds at least one row.
 bool use_cluster(const sw_grid* g, ClusterShape* out) {
-  if (g->ndim != 2 || g->has_density || g->n_force > 0 || g->snapshots || g->variant == SW_STENCIL_PLAIN) return false;
+  if (g->ndim != 2 || g->has_density || g->n_force > 0 || g->snapshots || g->variant == SW_STENCIL_PLAIN ||
+      g->variant == SW_STENCIL_TB2)
+    return false;
   if (int64_t(g->n_src) * g->lz * g->lx > kClusterThreads) return false;  // one source tap per thread
   const int R = g->R;
   const int64_t nz = g->n[0], nx = g->n[2];
@@ -1065,7 +1111,20 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   // small 2D grids: the whole run in one launch of one cluster (timed as one launch)
   ClusterShape cshape;
   const bool cluster = n_steps > 0 && use_cluster(g, &cshape);
-  const int timed = !g->profiling ? 0 : (cluster ? 1 : (n_steps + g->profiling - 1) / g->profiling);  // launches timed
+  // two steps per launch (SW_STENCIL_TB2): n_steps / 2 launches, then an odd last step per step
+  const bool tb2 = n_steps >= 2 && use_tb2(g);
+  const int pairs = tb2 ? n_steps / 2 : 0;
+  const int timed = !g->profiling ? 0
+                    : (cluster ? 1
+                               : (tb2 ? (pairs + g->profiling - 1) / g->profiling
+                                      : (n_steps + g->profiling - 1) / g->profiling));  // launches timed
+  if (tb2 && !g->u2[0]) {
+    for (int i = 0; i < 2; ++i) {
+      SW_TRY(dev_alloc(g, (void**)&g->u2[i], fbytes));
+      SW_CUDA(cudaMemsetAsync(g->u2[i], 0, fbytes, g->stream));
+    }
+  }
+  float* const lv[4] = {g->u[0], g->u[1], g->u2[0], g->u2[1]};  // level buffers of a two-step run
   if (timed && g->events.size() < size_t(2 * timed)) {
     size_t old = g->events.size();
     g->events.resize(size_t(2 * timed));
@@ -1102,13 +1161,65 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       ++launches;
     }
   }
-  for (int step = 0; step < n_steps; ++step) {
-    float* pn = g->u[step & 1];
-    float* pnm1 = g->u[(step + 1) & 1];
+  int in_n = 0, in_m = 1;  // buffers (of lv) of p[step] and p[step - 1]
+  int first_step = 0;
+  if (tb2) {
+    Tb2Args t;
+    t.kappa = a.kappa;
+    t.damp = g->damp;
+    t.sz = g->lay.sz;
+    t.nz = int(g->n[0]);
+    t.nx = int(g->n[2]);
+    const int fmap[4] = {0, 1, 4, 5};  // z low, z high, x low, x high
+    for (int i = 0; i < 4; ++i) {
+      t.nbl[i] = g->nbl[fmap[i]];
+      t.bc[i] = g->bc[fmap[i]];
+    }
+    for (int j = 0; j <= kMaxR; ++j) {
+      t.cz[j] = a.cz[j];
+      t.cx[j] = a.cx[j];
+    }
+    t.src = src;
+    t.sig = g->wavelet;
+    t.sig_stride = g->sig_stride;
+    t.tiles_x = int((g->n[2] + kTb2TX - 1) / kTb2TX);
+    const unsigned blocks = unsigned(t.tiles_x * ((g->n[0] + kTb2TZ - 1) / kTb2TZ));
+    for (int pr = 0; pr < pairs; ++pr) {
+      const int step = 2 * pr;
+      const int o1 = in_n < 2 ? 2 : 0, o2 = o1 + 1;  // the other two buffers: p[step + 1], p[step + 2]
+      t.pn = g->at0(lv[in_n]);
+      t.pm = g->at0(lv[in_m]);
+      t.out1 = g->at0(lv[o1]);
+      t.out2 = g->at0(lv[o2]);
+      t.step = step;
+      const bool time_it = g->profiling && pr % g->profiling == 0;
+      const int ev = time_it ? 2 * (pr / g->profiling) : 0;
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
+      launch_tb2(g->R, t, blocks, st);
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev + 1], st, evflags));
+      // p[step + 1]: ghosts and its receivers
+      launch_face_conditions(t.out1, f, g->R, rec, seis_dev, step, st);
+      // p[step + 2]: step + 1's sources, then ghosts and its receivers
+      if (src_threads > 0) {
+        launch_dependent(inject_sources_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, t.out2,
+                         (const float*)a.kappa, (const float2*)g->damp, src, (const float*)g->wavelet, g->sig_stride,
+                         step + 1, f, g->ndim, g->R);
+        ++launches;
+      }
+      launch_face_conditions(t.out2, f, g->R, rec, seis_dev, step + 1, st);
+      launches += 3;
+      in_n = o2;
+      in_m = o1;
+    }
+    first_step = 2 * pairs;
+  }
+  for (int step = first_step; step < n_steps; ++step) {
+    float* pn = tb2 ? lv[in_n] : g->u[step & 1];
+    float* pnm1 = tb2 ? lv[in_m] : g->u[(step + 1) & 1];
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pnm1);
     a.pout = g->at0(pnm1);
-    const bool time_it = g->profiling && step % g->profiling == 0;
+    const bool time_it = !tb2 && g->profiling && step % g->profiling == 0;  // with tb2: its launches only
     const int ev = time_it ? 2 * (step / g->profiling) : 0;
     if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
     if (tma)
@@ -1246,7 +1357,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   g->last_key = key;
   g->last_key_valid = true;
   if (final_field) {
-    float* last = g->at0(g->u[n_steps & 1]);
+    float* last = g->at0(tb2 ? lv[tb2_last_level(n_steps)] : g->u[n_steps & 1]);
     const bool fh = !is_device_pointer(final_field);
     float* dst = final_field;
     if (fh) {
@@ -1759,10 +1870,11 @@ sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out) {
 sw_status sw_set_stencil_variant(sw_grid* g, int variant) {
   if (!g) return fail(SW_EINVAL, "NULL grid");
   if (variant != SW_STENCIL_AUTO && variant != SW_STENCIL_PLAIN && variant != SW_STENCIL_TMA &&
-      variant != SW_STENCIL_CLUSTER)
+      variant != SW_STENCIL_CLUSTER && variant != SW_STENCIL_TB2)
     return fail(SW_EINVAL, "unknown stencil variant %d", variant);
   if (variant == SW_STENCIL_TMA && g->ndim != 3) return fail(SW_EINVAL, "the pipelined stencil is 3D only");
   if (variant == SW_STENCIL_CLUSTER && g->ndim != 2) return fail(SW_EINVAL, "the cluster-resident run is 2D only");
+  if (variant == SW_STENCIL_TB2 && g->ndim != 2) return fail(SW_EINVAL, "the two-step kernel is 2D only");
   g->variant = variant;
   ++g->config_gen;
   return SW_OK;
@@ -1779,7 +1891,8 @@ sw_status sw_set_pipeline_test(sw_grid* g, int starve, unsigned long long wait_l
 sw_status sw_get_stencil_variant(const sw_grid* g, int* variant) {
   if (!g || !variant) return fail(SW_EINVAL, "NULL argument");
   ClusterShape cs;
-  *variant = use_tma(g) ? SW_STENCIL_TMA : (use_cluster(g, &cs) ? SW_STENCIL_CLUSTER : SW_STENCIL_PLAIN);
+  *variant = use_tma(g) ? SW_STENCIL_TMA
+                        : (use_tb2(g) ? SW_STENCIL_TB2 : (use_cluster(g, &cs) ? SW_STENCIL_CLUSTER : SW_STENCIL_PLAIN));
   return SW_OK;
 }
 
@@ -1886,6 +1999,8 @@ void sw_destroy_grid(sw_grid* g) {
   const size_t fbytes = size_t(g->lay.total) * sizeof(float);
   dev_free(g, g->u[0], fbytes);
   dev_free(g, g->u[1], fbytes);
+  dev_free(g, g->u2[0], fbytes);
+  dev_free(g, g->u2[1], fbytes);
   dev_free(g, g->kappa, fbytes);
   dev_free(g, g->lnrho, fbytes);
   for (int i = 0; i < 3; ++i) dev_free(g, g->glr[i], fbytes);

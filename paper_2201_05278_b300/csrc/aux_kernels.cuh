@@ -513,7 +513,8 @@ inline void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
   cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
-// Face conditions of p (3D, pipelined stencil) and, if rec.count > 0, the
+// Face conditions of p (after the 3D pipelined stencil, the two-step 2D
+// kernel and in the gradient's passes) and, if rec.count > 0, the
 // receiver samples of this step, and, if pi.count > 0, the pre-injection of
 // the next step's sources, in one launch of 256-thread blocks.
 inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
@@ -521,9 +522,13 @@ inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const Poi
   FaceGrid fg;
   fg.pre = (pi.count * pi.taps + 255) / 256;
   fg.rec = (rec.count + 7) / 8;
-  fg.z = int((2 * int64_t(f.ny) * f.nx + 255) / 256);
-  fg.y = int((2 * int64_t(f.nz) * f.nx + 255) / 256);
-  fg.x = int((2 * int64_t(f.nz) * f.ny * R + 255) / 256);
+  // an axis whose two faces have no condition has nothing to write (its
+  // ghosts stay zero): no blocks for it (the y axis of a 2D grid)
+  const bool zf = f.bc[0] != kBcNone || f.bc[1] != kBcNone, yf = f.bc[2] != kBcNone || f.bc[3] != kBcNone,
+             xf = f.bc[4] != kBcNone || f.bc[5] != kBcNone;
+  fg.z = zf ? int((2 * int64_t(f.ny) * f.nx + 255) / 256) : 0;
+  fg.y = yf ? int((2 * int64_t(f.nz) * f.nx + 255) / 256) : 0;
+  fg.x = xf ? int((2 * int64_t(f.nz) * f.ny * R + 255) / 256) : 0;
   const unsigned grid = unsigned(fg.total());
   switch (R) {
     case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;

@@ -22,6 +22,12 @@ available, so synthetic layered models of the same kind stand in for them:
                        model plus two dipping interfaces (+500 m/s each),
                        Gardner density rho = 310 v^0.25, 3000 steps, 10 Hz,
                        50-cell layer, 128 x 128 receivers at the surface
+  2d_layered_4096      4096 x 4096, h = 5 m, order 8, the layered model of
+                       3d_layered_256 in 2D (8 layers, smoothed 5% noise),
+                       1000 steps, 15 Hz Ricker 5 cells deep, 40-cell layer,
+                       256 receivers 2 cells deep: a 2D grid whose fields
+                       (67 MB each) do not stay in L2, for the two-step
+                       kernel against the per-step kernels
 
   2d_shot_batch_64     64 shots for batched runs: 8 models (seeds 0..7) of
                        (nz, nx) drawn from U{300..800} x U{400..1200}, h = 10 m,
@@ -184,6 +190,21 @@ def make(name: str, n_steps: Optional[int] = None, shape: Optional[Tuple[int, ..
         rec = np.stack([np.zeros(yy.size), yy.ravel(), xx.ravel()], 1)
         return Workload(name, 3, shp, h, 16, nbl, ["null_neumann"] + ["null_dirichlet"] * 5,
                         _alpha(c_max, nb, h[0]), 3, dt, n_steps or 3000, f, 1.0 / f, src, rec, 4, vel, rho)
+    if name == "2d_layered_4096":
+        shp = tuple(shape) if shape else (4096, 4096)
+        h = (5.0, 5.0)
+        nb = min(40, max(4, shp[1] // 6))
+        nbl = [0, nb, nb, nb]
+        vel = layered_velocity(shp, seed=seed)
+        c_max = float(vel.max())
+        dt = 0.4 * h[0] / c_max
+        f = 15.0
+        phys_x = (shp[1] - 2 * nb - 1) * h[1]
+        src = np.array([[5 * h[0], 0.5 * phys_x]])
+        rec = np.stack([np.full(256, 2 * h[0]), _grid_positions(0.0, phys_x, 256)], 1)
+        return Workload(name, 2, shp, h, 8, nbl, ["null_neumann", "null_dirichlet", "null_dirichlet",
+                                                   "null_dirichlet"],
+                        _alpha(c_max, nb, h[0]), 3, dt, n_steps or 1000, f, 1.0 / f, src, rec, 4, vel)
     raise KeyError(name)
 
 
@@ -256,6 +277,6 @@ def fwi_gradient_256(n_steps: Optional[int] = None, shape: Optional[Tuple[int, .
     return GradientCase(base, v_true, shots, 10)
 
 
-NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384"]
+NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384", "2d_layered_4096"]
 GRADIENT_NAMES = ["3d_fwi_gradient_256"]
 BATCH_NAMES = ["2d_shot_batch_64"]
