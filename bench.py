@@ -73,11 +73,13 @@ def _peaks():
 
 STENCIL_SOURCES = ("stencil_plain.cuh", "stencil_tma.cuh", "tma.cuh", "layout.h")
 BATCH_SOURCES = ("batch.cuh", "stencil_plain.cuh", "layout.h")
+TB2_SOURCES = ("tb2d.cuh", "stencil_plain.cuh", "tma.cuh", "layout.h")
 # committed ncu traffic record of each workload's dominant kernel (profiles/)
 TRAFFIC_FILES = {
     "3d_layered_256": ("traffic_stencil_tma_3d_layered_256.txt", STENCIL_SOURCES),
     "3d_vd_512x512x384": ("traffic_stencil_tma_vd_3d_vd_512x512x384.txt", STENCIL_SOURCES),
     "2d_shot_batch_64": ("traffic_stencil_batch_2d_shot_batch_64.txt", BATCH_SOURCES),
+    "2d_layered_4096": ("traffic_tb2_2d_2d_layered_4096.txt", TB2_SOURCES),
 }
 
 

@@ -114,8 +114,12 @@ struct sw_grid {
   Layout lay;
 
   float* u[2] = {nullptr, nullptr};
-  // two more levels for the two-step 2D kernel (SW_STENCIL_TB2), allocated on first use
+  // two more levels for the two-step 2D kernel (SW_STENCIL_TB2), allocated on
+  // first use, and its tensor maps over the four levels (as p[n] and as
+  // p[n-1]) and kappa
   float* u2[2] = {nullptr, nullptr};
+  bool tb2_ready = false;
+  CUtensorMap tb2_n[4], tb2_m[4], tb2_k;
   float* kappa = nullptr;
   float* lnrho = nullptr;
   float2* damp = nullptr;
@@ -562,26 +566,52 @@ bool use_tb2(const sw_grid* g) {
          g->n[0] > 2 * int64_t(g->R) + 1 && g->n[2] > 2 * int64_t(g->R) + 1;
 }
 
-using Tb2Fn = void (*)(const Tb2Args);
+using Tb2Fn = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const Tb2Args, int*,
+                      unsigned long long);
 
+// The kernel of a radius with its shared memory set up, and its resident
+// CTAs per SM (once per radius).
 template <int R>
-Tb2Fn tb2_fn() {
-  static bool ready = false;
-  if (!ready) {
-    cudaFuncSetAttribute(tb2_2d_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Tb2Smem<R>::BYTES));
-    ready = true;
+Tb2Fn tb2_fn(int* per_sm) {
+  static int blocks = 0;
+  if (!blocks) {
+    cudaFuncSetAttribute(tb2_2d_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Tb2Cfg<R>::BYTES));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tb2_2d_kernel<R>, kTb2Threads, Tb2Cfg<R>::BYTES);
+    if (blocks < 1) blocks = 1;
   }
+  *per_sm = blocks;
   return tb2_2d_kernel<R>;
 }
 
-void launch_tb2(int R, const Tb2Args& t, unsigned blocks, cudaStream_t st) {
-#define SW_TB2(RR) \
-  case RR: launch_dependent(tb2_fn<RR>(), dim3(blocks), dim3(kTb2Threads), Tb2Smem<RR>::BYTES, st, t); break;
-  switch (R) {
+void launch_tb2(const sw_grid* g, const CUtensorMap& mn, const CUtensorMap& mm, const Tb2Args& t, cudaStream_t st) {
+#define SW_TB2(RR)                                                                                              \
+  case RR: {                                                                                                    \
+    int per_sm = 1;                                                                                             \
+    Tb2Fn fn = tb2_fn<RR>(&per_sm);                                                                             \
+    const unsigned grid = unsigned(std::min<int64_t>(t.tiles, int64_t(g->sm_count) * per_sm));                 \
+    launch_dependent(fn, dim3(grid), dim3(kTb2Threads), Tb2Cfg<RR>::BYTES, st, mn, mm, g->tb2_k, t, g->dflag,  \
+                     g->wait_limit_ns);                                                                         \
+    break;                                                                                                      \
+  }
+  switch (g->R) {
     SW_TB2(1) SW_TB2(2) SW_TB2(3) SW_TB2(4) SW_TB2(5) SW_TB2(6) SW_TB2(7) SW_TB2(8) SW_TB2(9) SW_TB2(10)
     default: break;
   }
 #undef SW_TB2
+}
+
+// Tensor maps of the two-step kernel over the four level buffers and kappa.
+sw_status build_tb2_maps(sw_grid* g) {
+  int w0, h0, w1, h1;
+  tb2_boxes(g->R, &w0, &h0, &w1, &h1);
+  float* lv[4] = {g->u[0], g->u[1], g->u2[0], g->u2[1]};
+  for (int i = 0; i < 4; ++i) {
+    SW_TRY(make_map(g, lv[i], uint32_t(w0), 1, &g->tb2_n[i], uint32_t(h0)));
+    SW_TRY(make_map(g, lv[i], uint32_t(w1), 1, &g->tb2_m[i], uint32_t(h1)));
+  }
+  SW_TRY(make_map(g, g->kappa, uint32_t(w1), 1, &g->tb2_k, uint32_t(h1)));
+  g->tb2_ready = true;
+  return SW_OK;
 }
 
 // Level buffers of a two-step run after `n_steps` steps: the run reads
@@ -1124,6 +1154,10 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       SW_CUDA(cudaMemsetAsync(g->u2[i], 0, fbytes, g->stream));
     }
   }
+  if (tb2 && !g->tb2_ready) {
+    if (!g->sm_count) cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+    SW_TRY(build_tb2_maps(g));
+  }
   float* const lv[4] = {g->u[0], g->u[1], g->u2[0], g->u2[1]};  // level buffers of a two-step run
   if (timed && g->events.size() < size_t(2 * timed)) {
     size_t old = g->events.size();
@@ -1165,7 +1199,6 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
   int first_step = 0;
   if (tb2) {
     Tb2Args t;
-    t.kappa = a.kappa;
     t.damp = g->damp;
     t.sz = g->lay.sz;
     t.nz = int(g->n[0]);
@@ -1183,19 +1216,17 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     t.sig = g->wavelet;
     t.sig_stride = g->sig_stride;
     t.tiles_x = int((g->n[2] + kTb2TX - 1) / kTb2TX);
-    const unsigned blocks = unsigned(t.tiles_x * ((g->n[0] + kTb2TZ - 1) / kTb2TZ));
+    t.tiles = int(t.tiles_x * ((g->n[0] + kTb2TZ - 1) / kTb2TZ));
     for (int pr = 0; pr < pairs; ++pr) {
       const int step = 2 * pr;
       const int o1 = in_n < 2 ? 2 : 0, o2 = o1 + 1;  // the other two buffers: p[step + 1], p[step + 2]
-      t.pn = g->at0(lv[in_n]);
-      t.pm = g->at0(lv[in_m]);
       t.out1 = g->at0(lv[o1]);
       t.out2 = g->at0(lv[o2]);
       t.step = step;
       const bool time_it = g->profiling && pr % g->profiling == 0;
       const int ev = time_it ? 2 * (pr / g->profiling) : 0;
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
-      launch_tb2(g->R, t, blocks, st);
+      launch_tb2(g, g->tb2_n[in_n], g->tb2_m[in_m], t, st);
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev + 1], st, evflags));
       // p[step + 1]: ghosts and its receivers
       launch_face_conditions(t.out1, f, g->R, rec, seis_dev, step, st);
