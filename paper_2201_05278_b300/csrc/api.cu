@@ -406,13 +406,14 @@ struct StepMaps {
   const CUtensorMap* inner;
   const CUtensorMap* old;
   const CUtensorMap* warm;
-  bool tall = false;  // 64 x 32 tiles (variable density, radius 8; the tall_* maps)
+  bool tall = false;
+  const CUtensorMap* kap = nullptr;  // replaces kappa's map (the imaging pass: gk)  // 64 x 32 tiles (variable density, radius 8; the tall_* maps)
 };
 
-template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD, bool IMG = false>
 void launch_tma_iso(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
   using C = TmaConfig<R, TY, PPT, NB, VD>;
-  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO, VD>;
+  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO, VD, IMG>;
   static int blocks_per_sm = 0;  // per instantiation; the library drives one device type
   if (!blocks_per_sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
@@ -428,17 +429,36 @@ void launch_tma_iso(const sw_grid* g, const StencilArgs& a, const StepMaps& m, c
   long long grid = (long long)g->sm_count * blocks_per_sm;
   if (grid > wk.total) grid = wk.total;
   const CUtensorMap* gm = VD ? (m.tall ? g->tall_g : g->map_g) : nullptr;  // unused maps: kappa's
-  const CUtensorMap& km = m.tall ? g->tall_kappa : g->map_kappa;
+  const CUtensorMap& km = m.kap ? *m.kap : (m.tall ? g->tall_kappa : g->map_kappa);
   launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, *m.halo, *m.inner, *m.warm, *m.old, km,
                    VD ? gm[0] : km, VD ? gm[1] : km, VD ? gm[2] : km, a, wk, g->dflag, g->wait_limit_ns);
 }
 
-template <int R, int TY, int PPT, int NB, int MINB, bool VD>
+template <int R, int TY, int PPT, int NB, int MINB, bool VD, bool IMG = false>
 void launch_tma_t(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
   if (g->h[0] == g->h[1] && g->h[1] == g->h[2])
-    launch_tma_iso<R, TY, PPT, NB, MINB, true, VD>(g, a, m, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, true, VD, IMG>(g, a, m, st);
   else
-    launch_tma_iso<R, TY, PPT, NB, MINB, false, VD>(g, a, m, st);
+    launch_tma_iso<R, TY, PPT, NB, MINB, false, VD, IMG>(g, a, m, st);
+}
+
+// The imaging pass of the gradient (constant density) on the pipelined
+// kernel: m.halo/inner/warm over the forward state p, m.old over psi, m.kap
+// over gk; a.pout = gk.  The tile shapes of the constant-density forward.
+void launch_image_tma(const sw_grid* g, const StencilArgs& a, const StepMaps& m, cudaStream_t st) {
+  switch (g->R) {
+    case 1: launch_tma_t<1, 16, 4, 3, 3, false, true>(g, a, m, st); break;
+    case 2: launch_tma_t<2, 16, 4, 3, 3, false, true>(g, a, m, st); break;
+    case 3: launch_tma_t<3, 16, 4, 3, 3, false, true>(g, a, m, st); break;
+    case 4: launch_tma_t<4, 16, 4, 3, 3, false, true>(g, a, m, st); break;
+    case 5: launch_tma_t<5, 16, 2, 4, 2, false, true>(g, a, m, st); break;
+    case 6: launch_tma_t<6, 16, 2, 4, 2, false, true>(g, a, m, st); break;
+    case 7: launch_tma_t<7, 16, 2, 4, 1, false, true>(g, a, m, st); break;
+    case 8: launch_tma_t<8, 16, 2, 4, 1, false, true>(g, a, m, st); break;
+    case 9: launch_tma_t<9, 16, 2, 4, 1, false, true>(g, a, m, st); break;
+    case 10: launch_tma_t<10, 16, 2, 4, 1, false, true>(g, a, m, st); break;
+    default: break;
+  }
 }
 
 // Tile height / rows per warp / ring depth / minimum CTAs per SM for each
@@ -1560,7 +1580,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     int tx, ty;
     tma_tile(g->R, &tx, &ty);
     const uint32_t xh = uint32_t((g->R + 3) / 4 * 4);
-    for (int i = nck; i < nck + K + 3; ++i) {  // segment states and psi
+    for (int i = nck; i < nck + K + 4; ++i) {  // segment states, psi and gk
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx) + 2 * xh, uint32_t(ty + 2 * g->R), &halo[size_t(i)]));
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &inner[size_t(i)]));
       SW_TRY(make_map(g, F[size_t(i)], uint32_t(tx), uint32_t(ty), &warm[size_t(i)], kTmaWarmPlanes));
@@ -1656,7 +1676,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
           unsigned* sc = scales + slot;
           char* dst = static_cast<char*>(packs) + pbytes * slot;
           if (i16) {
-            pack_rows_i16_kernel<<<unsigned(std::min<int64_t>(nrows, 4096)), 256, 0, st>>>(
+            pack_rows_i16_kernel<<<unsigned(std::min<int64_t>((nrows + 7) / 8, 4736)), 256, 0, st>>>(
                 a_f, b_f, f, row_scales + size_t(nrows) * slot, reinterpret_cast<int16_t*>(dst));
             continue;
           }
@@ -1712,10 +1732,17 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
         si);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
     const dim3 ig(unsigned((g->n[2] + 127) / 128), unsigned(g->n[1]), unsigned(g->n[0]));
-    if (vd)
+    if (vd) {
       launch_image_vd(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), GG, g->at0(GK), AG, f, lc, vw, st);
-    else
+    } else if (tma) {  // gk += psi[k] L p[k-1] on the pipelined kernel
+      StepMaps im{&halo[idx(pk1)], &inner[idx(pk1)], &inner[idx(p2)], &warm[idx(pk1)]};
+      im.kap = &inner[idx(GK)];
+      StencilArgs ai = a;
+      ai.pout = g->at0(GK);
+      launch_image_tma(g, ai, im, st);
+    } else {
       launch_image(g->R, g->ndim, ig, g->at0(pk1), g->at0(p2), g->at0(GK), f, lc, st);
+    }
     pending_src = k;  // its source imaging goes with the next step's additions, or follows the sweep
     SW_CUDA(cudaGetLastError());
     return SW_OK;
@@ -1794,7 +1821,8 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
           const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
           const float* base = i == 0 ? g->at0(B(1)) : nullptr;
           if (i16)
-            unpack_rows_i16_kernel<<<row_grid(f), 256, 0, st>>>(reinterpret_cast<const int16_t*>(src_p),
+            unpack_rows_i16_kernel<<<unsigned(std::min<int64_t>((nrows + 7) / 8, 4736)), 256, 0, st>>>(
+                reinterpret_cast<const int16_t*>(src_p),
                                                                 row_scales + size_t(nrows) * slot, f, base,
                                                                 g->at0(B(i)));
           else if (checkpoint_format == SW_CKPT_BF16)

@@ -935,39 +935,85 @@ __global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, 
 // s / 32767 is small next to the values that matter, where a 16-bit float
 // keeps only 8 or 11 bits of every value.  One CTA of 256 threads per row.
 __global__ void pack_rows_i16_kernel(const float* p, const float* base, FaceInfo f, float* scales, int16_t* out) {
-  __shared__ float red[8];
+  // one warp per (z, y) row; rows of a multiple of 4 nodes in float4 / 4 x int16 pieces
+  // (row starts are 128-byte aligned in the padded layout), others one node per lane
+  const int lane = threadIdx.x & 31;
   const int64_t rows = int64_t(f.nz) * f.ny;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t zy = blockIdx.x; zy < rows; zy += gridDim.x) {
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const bool vec = (f.nx & 3) == 0;
+  for (int64_t zy = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; zy < rows; zy += nw) {
     const int64_t off = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy;
     const float* pr = p + off;
     const float* br = base ? base + off : nullptr;
+    int16_t* orow = out + zy * f.nx;
     float m = 0.f;
-    for (int x = threadIdx.x; x < f.nx; x += blockDim.x) m = fmaxf(m, fabsf(br ? pr[x] - br[x] : pr[x]));
+    if (vec) {
+      for (int x = 4 * lane; x < f.nx; x += 128) {
+        float4 v = *reinterpret_cast<const float4*>(pr + x);
+        if (br) {
+          const float4 b = *reinterpret_cast<const float4*>(br + x);
+          v = make_float4(v.x - b.x, v.y - b.y, v.z - b.z, v.w - b.w);
+        }
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+    } else {
+      for (int x = lane; x < f.nx; x += 32) m = fmaxf(m, fabsf(br ? pr[x] - br[x] : pr[x]));
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) red[warp] = m;
-    __syncthreads();
-    m = red[0];
-    for (int i = 1; i < int(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
     const float sc = m > 0.f ? m : 1.f;
-    if (threadIdx.x == 0) scales[zy] = sc;
+    if (lane == 0) scales[zy] = sc;
     const float inv = 32767.f / sc;
-    for (int x = threadIdx.x; x < f.nx; x += blockDim.x)
-      out[zy * f.nx + x] = int16_t(__float2int_rn((br ? pr[x] - br[x] : pr[x]) * inv));
-    __syncthreads();  // red is reused by the next row
+    if (vec) {
+      for (int x = 4 * lane; x < f.nx; x += 128) {
+        float4 v = *reinterpret_cast<const float4*>(pr + x);
+        if (br) {
+          const float4 b = *reinterpret_cast<const float4*>(br + x);
+          v = make_float4(v.x - b.x, v.y - b.y, v.z - b.z, v.w - b.w);
+        }
+        short4 q;
+        q.x = int16_t(__float2int_rn(v.x * inv));
+        q.y = int16_t(__float2int_rn(v.y * inv));
+        q.z = int16_t(__float2int_rn(v.z * inv));
+        q.w = int16_t(__float2int_rn(v.w * inv));
+        *reinterpret_cast<short4*>(orow + x) = q;
+      }
+    } else {
+      for (int x = lane; x < f.nx; x += 32)
+        orow[x] = int16_t(__float2int_rn((br ? pr[x] - br[x] : pr[x]) * inv));
+    }
   }
 }
 
-// p = base - v or p = v with v = q * s / 32767 (row scales s), row-mapped.
+// p = base - v or p = v with v = q * s / 32767 (row scales s); one warp per
+// (z, y) row, in 4-node pieces when the row length allows.
 __global__ void unpack_rows_i16_kernel(const int16_t* in, const float* scales, FaceInfo f, const float* base,
                                        float* p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int64_t rows = int64_t(f.nz) * f.ny;
-  if (x >= f.nx) return;
-  for (int64_t zy = blockIdx.y; zy < rows; zy += gridDim.y) {
-    const int64_t k = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy + x;
-    const float v = float(in[zy * f.nx + x]) * (scales[zy] * (1.f / 32767.f));
-    p[k] = base ? base[k] - v : v;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const bool vec = (f.nx & 3) == 0;
+  for (int64_t zy = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; zy < rows; zy += nw) {
+    const int64_t off = (zy / f.ny) * f.sz + (zy % f.ny) * f.sy;
+    const float s = scales[zy] * (1.f / 32767.f);
+    const int16_t* irow = in + zy * f.nx;
+    float* pr = p + off;
+    const float* br = base ? base + off : nullptr;
+    if (vec) {
+      for (int x = 4 * lane; x < f.nx; x += 128) {
+        const short4 q = *reinterpret_cast<const short4*>(irow + x);
+        float4 v = make_float4(float(q.x) * s, float(q.y) * s, float(q.z) * s, float(q.w) * s);
+        if (br) {
+          const float4 b = *reinterpret_cast<const float4*>(br + x);
+          v = make_float4(b.x - v.x, b.y - v.y, b.z - v.z, b.w - v.w);
+        }
+        *reinterpret_cast<float4*>(pr + x) = v;
+      }
+    } else {
+      for (int x = lane; x < f.nx; x += 32) {
+        const float v = float(irow[x]) * s;
+        pr[x] = br ? br[x] - v : v;
+      }
+    }
   }
 }
 

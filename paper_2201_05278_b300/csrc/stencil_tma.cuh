@@ -100,13 +100,18 @@ struct RingShared {
 // handled as a float2 with packed FP32x2 arithmetic.
 // ISO: all three spacings are equal, so one coefficient per j serves every
 // axis (fewer registers; same arithmetic).
-template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD>
+// IMG (constant density only): the imaging pass of the misfit gradient on
+// the same pipeline.  The bundle's p[n-1] box carries psi and its kappa box
+// the accumulator gk, and the store writes gk + psi (L p) to a.pout (= gk):
+// with p the forward state, this accumulates kappa dJ/dkappa.
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD, bool IMG = false>
 __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     stencil_tma_kernel(const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_f,
                        const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_o, const __grid_constant__ CUtensorMap map_k,
                        const __grid_constant__ CUtensorMap map_gz, const __grid_constant__ CUtensorMap map_gy,
                        const __grid_constant__ CUtensorMap map_gx, const StencilArgs a, const TmaWork wk,
                        int* err_flag, unsigned long long limit_ns) {
+  static_assert(!(IMG && VD), "the imaging pass is constant density");
   using C = TmaConfig<R, TY, PPT, NB, VD>;
   constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW, NCW = C::NCW, W = C::W, WP = C::WP;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -271,8 +276,8 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       const int z = zb + j - W;
       const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
       const int dz2 = dzl * dzl;
-      const bool zlayer = j >= W && dz2 != 0;
-      const bool damped = zlayer || (j >= W && !xy_free);
+      const bool zlayer = !IMG && j >= W && dz2 != 0;
+      const bool damped = !IMG && (zlayer || (j >= W && !xy_free));
       float2 da[PPT], db[PPT];
       if (zlayer) {
 #pragma unroll
@@ -368,7 +373,11 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
             kl[i] = f2_sub(kl[i], adv);
           }
         }
-        if (!damped) {
+        if constexpr (IMG) {
+          // gk + psi (L p), psi from the p[n-1] box, gk from the kappa box
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) kl[i] = f2_fma(O[i * (TX / 2)], kl[i], K[i * (TX / 2)]);
+        } else if (!damped) {
           // outside the absorbing layer: a = 1, e = 0
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
