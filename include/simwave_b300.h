@@ -235,9 +235,10 @@ sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
 
 /*
  * Stencil kernel variant.  CUDA implementations of the same update (Eq. 7):
- * SW_STENCIL_AUTO picks the TMA-pipelined persistent kernel for 3D
- * constant-density grids, the cluster-resident run for 2D grids that fit
- * it, and the per-step plain kernels otherwise; SW_STENCIL_PLAIN forces the
+ * SW_STENCIL_AUTO picks the TMA-pipelined persistent kernel for 3D grids
+ * (constant or variable density), the cluster-resident run for 2D grids that
+ * fit it, the two-step kernel (below) for other 2D grids of constant density
+ * with 4M nodes or more, and the per-step plain kernels otherwise; SW_STENCIL_PLAIN forces the
  * per-step plain kernels; SW_STENCIL_TMA asks for the pipelined kernel (3D
  * only, else SW_EINVAL; cases it does not cover still use the plain
  * kernel).  SW_STENCIL_CLUSTER asks for the cluster-resident run (2D only,
@@ -259,7 +260,9 @@ sw_status sw_ricker(double f_peak, double t0, double dt, int nt, float* out);
  * an odd last step runs on the plain kernels; the grid allocates two more
  * wavefield levels on its first such run.  The levels equal the plain
  * kernels' bit for bit when no two source taps share a node (the
- * seismograms agree to rounding: another receiver sampler).
+ * seismograms agree to rounding: another receiver sampler).  SW_STENCIL_AUTO
+ * picks it for such 2D grids of 4M nodes or more (where it is faster than
+ * the per-step kernels; below, their fields stay in L2 and it is slower).
  * sw_get_stencil_variant reports the kernel sw_forward will launch for the
  * current model.
  */

@@ -113,3 +113,21 @@ def test_two_step_kernel_is_2d_only(cuda_device):
         assert e.value.status == api.SW_EINVAL
     finally:
         g.close()
+
+
+def test_auto_picks_the_two_step_kernel_on_large_2d_grids(cuda_device):
+    """From 4M nodes on (fields beyond L2) the default variant is the two-step
+    kernel; smaller 2D grids keep the cluster run or the per-step kernels, and
+    an explicit SW_STENCIL_PLAIN is honoured."""
+    import torch
+    for shape, big in (((2048, 2048), True), ((1024, 1024), False)):
+        g = api.sw_create_grid(2, shape, (5.0, 5.0), 8, [0, 10, 10, 10],
+                               ["null_neumann", "null_dirichlet", "null_dirichlet", "null_dirichlet"], 1.0, 3, 0.0)
+        try:
+            api.sw_set_model(g, torch.full(shape, 2000.0, dtype=torch.float32, device="cuda:0"))
+            v = api.sw_get_stencil_variant(g)
+            assert (v == api.SW_STENCIL_TB2) == big
+            api.sw_set_stencil_variant(g, api.SW_STENCIL_PLAIN)
+            assert api.sw_get_stencil_variant(g) == api.SW_STENCIL_PLAIN
+        finally:
+            g.close()
