@@ -141,6 +141,11 @@ struct sw_grid {
   int* src_first = nullptr;
   float* src_w = nullptr;
   float* wavelet = nullptr;
+  // per time step: does some source have a nonzero sample?  (The injection
+  // and source-imaging launches of steps where every sample is exactly zero,
+  // the tail of a Ricker wavelet in FP32, add nothing and are skipped.)
+  std::vector<uint8_t> sig_live;
+  bool live(int n) const { return n >= 0 && size_t(n) < sig_live.size() && sig_live[size_t(n)]; }
   int64_t* tap_off = nullptr;  // source tap table of the pipelined path (n_src * taps)
   float* tap_coef = nullptr;
   float* tap_pre = nullptr;  // pre-injection coefficients (PreInject), same order
@@ -767,6 +772,7 @@ void free_acquisition(sw_grid* g) {
   g->src_first = g->rec_first = nullptr;
   g->src_w = g->rec_w = g->wavelet = nullptr;
   g->has_acq = false;
+  g->sig_live.clear();
 }
 
 // Window weights of a set of points: per point and axis the first node and the
@@ -1092,6 +1098,12 @@ sw_status sw_set_acquisition(sw_grid* g, int n_src, const double* src_pos, int n
     const size_t wl = size_t(wavelet_per_source ? n_src : 1) * nt;
     SW_TRY(dev_alloc(g, (void**)&g->wavelet, size_t(n_src) * nt * sizeof(float)));
     SW_CUDA(cudaMemcpyAsync(g->wavelet, wavelet, wl * sizeof(float), cudaMemcpyDefault, g->stream));
+    std::vector<float> host_w(wl);
+    SW_CUDA(cudaMemcpyAsync(host_w.data(), g->wavelet, wl * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    SW_CUDA(cudaStreamSynchronize(g->stream));
+    g->sig_live.assign(size_t(nt), 0);
+    for (size_t i = 0; i < wl; ++i)
+      if (host_w[i] != 0.f) g->sig_live[i % size_t(nt)] = 1;
   }
   if (n_rec > 0) {
     SW_TRY(dev_alloc(g, (void**)&g->rec_first, rf.size() * sizeof(int)));
@@ -1214,7 +1226,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
                                                                          g->tap_coef, g->tap_pre);
     SW_CUDA(cudaGetLastError());
     ++launches;
-    if (pre_inject && n_steps > 0) {  // step 0's sources, into p[-1]
+    if (pre_inject && n_steps > 0 && g->live(0)) {  // step 0's sources, into p[-1]
       inject_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
           g->at0(g->u[1]), g->tap_off, g->tap_pre, g->lz * g->ly * g->lx, g->n_src, g->wavelet, g->sig_stride, 0);
       SW_CUDA(cudaGetLastError());
@@ -1249,6 +1261,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       t.out1 = g->at0(lv[o1]);
       t.out2 = g->at0(lv[o2]);
       t.step = step;
+      t.src.count = g->live(step) ? src.count : 0;  // step n's taps, in the kernel
       const bool time_it = g->profiling && pr % g->profiling == 0;
       const int ev = time_it ? 2 * (pr / g->profiling) : 0;
       if (time_it) SW_CUDA(cudaEventRecordWithFlags(g->events[ev], st, evflags));
@@ -1257,7 +1270,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       // p[step + 1]: ghosts and its receivers
       launch_face_conditions(t.out1, f, g->R, rec, seis_dev, step, st);
       // p[step + 2]: step + 1's sources, then ghosts and its receivers
-      if (src_threads > 0) {
+      if (src_threads > 0 && g->live(step + 1)) {
         launch_dependent(inject_sources_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, t.out2,
                          (const float*)a.kappa, (const float2*)g->damp, src, (const float*)g->wavelet, g->sig_stride,
                          step + 1, f, g->ndim, g->R);
@@ -1287,17 +1300,17 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     ++launches;
     if (pre_inject) {
       // added to p[n-1] before the step (by the previous face launch, or before the loop)
-    } else if (src_threads > 0 && tma) {  // before the face conditions, which mirror its increments
+    } else if (src_threads > 0 && tma && g->live(step)) {  // before the face conditions, which mirror its increments
       launch_dependent(inject_taps_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pout,
                        (const int64_t*)g->tap_off, (const float*)g->tap_coef, g->lz * g->ly * g->lx, g->n_src,
                        (const float*)g->wavelet, g->sig_stride, step);
       ++launches;
-    } else if (src_threads > 0 && g->ndim == 2) {
+    } else if (src_threads > 0 && g->ndim == 2 && g->live(step)) {
       launch_dependent(inject_sources_kernel, dim3((src_threads + 127) / 128), dim3(128), 0, st, a.pout,
                        (const float*)a.kappa, (const float2*)g->damp, src, (const float*)g->wavelet, g->sig_stride,
                        step, f, g->ndim, g->R);
       ++launches;
-    } else if (src_threads > 0) {
+    } else if (src_threads > 0 && g->live(step)) {
       inject_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
           a.pout, a.kappa, g->damp, src, g->wavelet, g->sig_stride, step, f, g->ndim, g->R);
       ++launches;
@@ -1312,7 +1325,7 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
       // the pipelined kernel writes node values only: the face conditions
       // follow, with the receiver samples in the same launch
       PreInject pi{};
-      if (pre_inject && step + 1 < n_steps)
+      if (pre_inject && step + 1 < n_steps && g->live(step + 1))
         pi = PreInject{g->at0(pn), g->tap_off, g->tap_pre, g->wavelet, g->lz * g->ly * g->lx, g->n_src, g->sig_stride,
                        step + 1};
       launch_face_conditions(a.pout, f, g->R, rec, seis_dev, step, st, pi);
@@ -1610,7 +1623,8 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   // one step p[n] (pn), p[n-1] (pm) -> p[n+1] (po), with sources at step n
   auto step = [&](float* pn, float* pm, float* po, const StepMaps* m, int n, const float* sig, int sig_stride,
                   const PointSet& pts, const PointSet& recs, float* seis) -> sw_status {
-    nk += 2 + (pts.count > 0);
+    const int taps = g->live(n) ? pts.count * pts.lz * pts.ly * pts.lx : 0;  // no launch for a silent step
+    nk += 2 + (taps > 0);
     a.pn = g->at0(pn);
     a.pnm1 = g->at0(pm);
     a.pout = g->at0(po);
@@ -1618,7 +1632,6 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
       launch_stencil_tma_maps(g, a, *m, st, vd);
     else
       launch_stencil(g->R, g->ndim, vd, a, st);
-    const int taps = pts.count * pts.lz * pts.ly * pts.lx;
     if (taps > 0)
       inject_sources_kernel<<<(taps + 127) / 128, 128, 0, st>>>(a.pout, a.kappa, g->damp, pts, sig, sig_stride, n,
                                                                 f, g->ndim, g->R);
@@ -1727,13 +1740,18 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
                                                                       g->damp, g->at0(p2), f, vw, g->R, g->ndim);
     // its Neumann-face correction and the residuals into psi through the
     // receiver windows (rows with non-zero weight only), in one launch
-    const int nb = int((2 * std::max(std::max(g->n[1] * g->n[2], g->n[0] * g->n[2]), g->n[0] * g->n[1]) + 255) / 256);
+    // blocks of the Neumann correction per axis: both faces' lines, none for an axis without a Neumann face
+    auto neumann_blocks = [&](int ax, int64_t face) {
+      return g->bc[2 * ax] == SW_BC_NEUMANN || g->bc[2 * ax + 1] == SW_BC_NEUMANN ? int((2 * face + 255) / 256) : 0;
+    };
+    const int3 nb = make_int3(neumann_blocks(0, g->n[1] * g->n[2]), neumann_blocks(1, g->n[0] * g->n[2]),
+                              neumann_blocks(2, g->n[0] * g->n[1]));
     const int rthreads = rec.count * g->rec_rows_max * rec.lx;
     // step k+1's source imaging: psi[k+1] is p1, which this step only reads
     SourceImaging si{};
-    if (src_threads > 0 && pending_src == k + 1)
+    if (src_threads > 0 && pending_src == k + 1 && g->live(k))
       si = SourceImaging{g->at0(p1), g->at0(GK), src, g->wavelet, g->sig_stride, k, (src_threads + 255) / 256};
-    adjoint_additions_kernel<<<unsigned(si.blocks + 3 * nb + (rthreads + 255) / 256), 256, 0, st>>>(
+    adjoint_additions_kernel<<<unsigned(si.blocks + nb.x + nb.y + nb.z + (rthreads + 255) / 256), 256, 0, st>>>(
         g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R, nb, rec, g->rec_rows_max, res, N, k - 1, g->ndim,
         si);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
@@ -1854,7 +1872,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     }
   }
 
-  if (src_threads > 0 && pending_src > 0) {  // the last adjoint step's source imaging
+  if (src_threads > 0 && pending_src > 0 && g->live(pending_src - 1)) {  // the last adjoint step's source imaging
     image_sources_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(PSI(pending_src & 1)), g->at0(GK), src,
                                                                     g->wavelet, g->sig_stride, pending_src - 1, f);
     SW_CUDA(cudaGetLastError());

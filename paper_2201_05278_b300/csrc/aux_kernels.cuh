@@ -646,13 +646,15 @@ struct SourceImaging {
 
 
 // The two additions an adjoint step makes to psi after its stencil, in one
-// launch: the Neumann-face correction (3 nb blocks, nb per axis, after the
+// launch: the Neumann-face correction (nb.x + nb.y + nb.z blocks, after the
 // si.blocks of an earlier step's source imaging) and the residuals through
 // the receiver windows (the blocks after them).  Both only add to `out`
 // with atomics and read other arrays, so their blocks run in any order, as
 // do the source imaging's, which add to gk.
+// nb: blocks of the Neumann correction per axis (0 for an axis without a
+// Neumann face).
 __global__ void adjoint_additions_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
-                                         FaceInfo f, LapCoef lc, int R, int nb, PointSet rec, int max_rows,
+                                         FaceInfo f, LapCoef lc, int R, int3 nb, PointSet rec, int max_rows,
                                          const float* res, int res_stride, int step, int ndim, SourceImaging si) {
   int b = blockIdx.x;
   if (b < si.blocks) {  // an earlier step's source imaging (adds to gk, reads other arrays than out)
@@ -660,17 +662,21 @@ __global__ void adjoint_additions_kernel(const float* psi1, float* out, const fl
     return;
   }
   b -= si.blocks;
-  if (b < 3 * nb) {
-    const int axis = b / nb;
-    const int64_t t = int64_t(b - axis * nb) * blockDim.x + threadIdx.x;
-    switch (axis) {
-      case 0: neumann_adjoint_axis<0>(psi1, out, kappa, damp, f, lc, R, t); break;
-      case 1: neumann_adjoint_axis<1>(psi1, out, kappa, damp, f, lc, R, t); break;
-      default: neumann_adjoint_axis<2>(psi1, out, kappa, damp, f, lc, R, t); break;
-    }
+  if (b < nb.x) {
+    neumann_adjoint_axis<0>(psi1, out, kappa, damp, f, lc, R, int64_t(b) * blockDim.x + threadIdx.x);
     return;
   }
-  b -= 3 * nb;
+  b -= nb.x;
+  if (b < nb.y) {
+    neumann_adjoint_axis<1>(psi1, out, kappa, damp, f, lc, R, int64_t(b) * blockDim.x + threadIdx.x);
+    return;
+  }
+  b -= nb.y;
+  if (b < nb.z) {
+    neumann_adjoint_axis<2>(psi1, out, kappa, damp, f, lc, R, int64_t(b) * blockDim.x + threadIdx.x);
+    return;
+  }
+  b -= nb.z;
   inject_row_node(out, kappa, damp, rec, max_rows, res, res_stride, step, f, ndim, R, b * blockDim.x + threadIdx.x);
 }
 
