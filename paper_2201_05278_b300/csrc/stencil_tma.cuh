@@ -24,7 +24,9 @@
 //     brings the count to the number of warps issues the bundle NB ahead
 //     into that slot;
 //   - each lane computes two adjacent columns with 64-bit shared loads and
-//     packed FP32x2 arithmetic, the Laplacian in three per-axis chains;
+//     packed FP32x2 arithmetic; with equal spacings the six neighbours at
+//     each offset are summed before the one multiply (else three per-axis
+//     chains);
 //     rows with no damping skip the damping lookup;
 //   - the kernel writes node values only (ragged tiles masked); Dirichlet
 //     face nodes and the ghost images of the face conditions are written by
@@ -333,22 +335,45 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
             w[mm + H] = (mm == 0) ? yw[i + R] : *reinterpret_cast<const float2*>(c + 2 * mm);
           const float2 pc = qz[i][R];
           const float2 p2 = f2_add(pc, pc);
-          // three independent accumulation chains (one per axis) for latency
-          float2 lz = make_float2(0.f, 0.f), lx = lz, ly = lz;
+          if constexpr (ISO) {
+            // one coefficient per offset on all three axes: the six
+            // neighbours at offset jj are summed first, less 6p (the form
+            // still annihilates constants); two chains (even / odd jj)
+            const float2 p6 = f2_add(p2, f2_add(p2, p2));
+            float2 le = make_float2(0.f, 0.f), lo = le;
 #pragma unroll
-          for (int jj = 1; jj <= R; ++jj) {
-            lz = f2_fma(cz2[jj], f2_sub(f2_add(qz[i][R + jj], qz[i][R - jj]), p2), lz);
-            float2 xs;  // (x+jj) + (x-jj) for both columns
-            if (jj % 2 == 0) {
-              xs = f2_add(w[H + jj / 2], w[H - jj / 2]);
-            } else {  // odd offsets straddle the pairs: two scalar adds into one pair
-              xs = make_float2(w[H + (jj - 1) / 2].y + w[H - (jj + 1) / 2].y,
-                               w[H + (jj + 1) / 2].x + w[H - (jj - 1) / 2].x);
+            for (int jj = 1; jj <= R; ++jj) {
+              float2 xs;  // (x+jj) + (x-jj) for both columns
+              if (jj % 2 == 0) {
+                xs = f2_add(w[H + jj / 2], w[H - jj / 2]);
+              } else {  // odd offsets straddle the pairs: two scalar adds into one pair
+                xs = make_float2(w[H + (jj - 1) / 2].y + w[H - (jj + 1) / 2].y,
+                                 w[H + (jj + 1) / 2].x + w[H - (jj - 1) / 2].x);
+              }
+              const float2 zy = f2_add(f2_add(qz[i][R + jj], qz[i][R - jj]), f2_add(yw[i + R + jj], yw[i + R - jj]));
+              const float2 t = f2_sub(f2_add(zy, xs), p6);
+              if (jj % 2) lo = f2_fma(cx2[jj], t, lo);
+              else le = f2_fma(cx2[jj], t, le);
             }
-            lx = f2_fma(cx2[jj], f2_sub(xs, p2), lx);
-            ly = f2_fma(cy2[jj], f2_sub(f2_add(yw[i + R + jj], yw[i + R - jj]), p2), ly);
+            kl[i] = f2_add(le, lo);
+          } else {
+            // three independent accumulation chains (one per axis) for latency
+            float2 lz = make_float2(0.f, 0.f), lx = lz, ly = lz;
+#pragma unroll
+            for (int jj = 1; jj <= R; ++jj) {
+              lz = f2_fma(cz2[jj], f2_sub(f2_add(qz[i][R + jj], qz[i][R - jj]), p2), lz);
+              float2 xs;  // (x+jj) + (x-jj) for both columns
+              if (jj % 2 == 0) {
+                xs = f2_add(w[H + jj / 2], w[H - jj / 2]);
+              } else {  // odd offsets straddle the pairs: two scalar adds into one pair
+                xs = make_float2(w[H + (jj - 1) / 2].y + w[H - (jj + 1) / 2].y,
+                                 w[H + (jj + 1) / 2].x + w[H - (jj - 1) / 2].x);
+              }
+              lx = f2_fma(cx2[jj], f2_sub(xs, p2), lx);
+              ly = f2_fma(cy2[jj], f2_sub(f2_add(yw[i + R + jj], yw[i + R - jj]), p2), ly);
+            }
+            kl[i] = f2_add(f2_add(lz, lx), ly);
           }
-          kl[i] = f2_add(f2_add(lz, lx), ly);
           if constexpr (VD) {
             // - grad(ln rho) . grad(p): first derivatives of p from the same
             // neighbours (Eq. 10), ln rho's from the gradient boxes
