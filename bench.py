@@ -438,6 +438,78 @@ def gradient_error_reduced(dev):
     return {CKPT_NAMES[f] + "_rel_l2": round(float(np.linalg.norm(grads[f] - g_ref)) / nr, 6) for f in CKPT_NAMES}
 
 
+def fwi_summary(world, rank, dev, steps=1, warmup=1):
+    """The misfit-gradient half of the metric beside the default forward line:
+    the 16-shot summed gradient of 3d_fwi_gradient_256 (256^3, 1500 steps,
+    I16 checkpoints every 10 steps) through fwi.misfit_gradient (under
+    torchrun the ranks split the shots), timed with CUDA events after a
+    warm-up (max over ranks), the forward run of the same grid, and the I16
+    gradient's error against FP32 checkpoints on the first shot."""
+    import torch
+    from paper_2201_05278_b300 import api, fwi, workloads
+    c = workloads.fwi_gradient_256()
+    w = c.base
+    N = w.n_steps
+    stream = torch.cuda.current_stream(dev)
+    g = api.sw_create_grid(3, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
+                           stream=stream)
+    try:
+        wav = api.sw_ricker(w.f_peak, w.t0, w.dt, N)
+        n_rec, n_shots = len(w.rec_pos), len(c.shots)
+        api.sw_set_model(g, torch.from_numpy(c.v_true).to(dev))
+        obs = torch.zeros((n_shots, N, n_rec), dtype=torch.float32, device=dev)
+        for i in fwi.shots_of_rank(n_shots, world, rank):
+            api.sw_set_acquisition(g, c.shots[i:i + 1], w.rec_pos, wav, window_radius=w.window_radius)
+            api.sw_forward(g, N, obs[i], None)
+        api.sw_set_model(g, torch.from_numpy(w.velocity).to(dev))
+        api.sw_set_acquisition(g, c.shots[:1], w.rec_pos, wav, window_radius=w.window_radius)
+        tmp = torch.empty((N, n_rec), dtype=torch.float32, device=dev)
+        api.sw_forward(g, N, tmp, None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        forward_ms = None  # the fastest of three forward runs: the ratio below errs high, not low
+        for _ in range(3):
+            e0.record(stream)
+            api.sw_forward(g, N, tmp, None)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1)
+            forward_ms = t if forward_ms is None else min(forward_ms, t)
+        fmt = api.SW_CKPT_I16
+        for _ in range(warmup):
+            fwi.misfit_gradient(g, c.shots, obs, N, c.checkpoint_every, fmt)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            J, grad = fwi.misfit_gradient(g, c.shots, obs, N, c.checkpoint_every, fmt)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = job_seconds(e0.elapsed_time(e1) * 1e-3 / steps, world, dev)
+        err = None
+        if rank == 0:
+            ref = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+            gv = torch.zeros_like(ref)
+            api.sw_gradient_shots(g, c.shots[:1], N, obs[:1], ref, c.checkpoint_every, api.SW_CKPT_FP32)
+            api.sw_gradient_shots(g, c.shots[:1], N, obs[:1], gv, c.checkpoint_every, fmt)
+            err = float(torch.linalg.vector_norm(gv - ref) / torch.linalg.vector_norm(ref))
+    finally:
+        g.close()
+    return {"workload": "3d_fwi_gradient_256", "grid": list(w.shape), "time_steps": N, "shots": n_shots,
+            "checkpoints": "16-bit fixed point with per-row scale (SW_CKPT_I16) every %d steps" % c.checkpoint_every,
+            "shots_per_s": round(n_shots / sec, 4), "ms_per_gradient": round(sec * 1e3, 3),
+            "ms_per_shot_per_gpu": round(sec * 1e3 / n_shots * world, 3), "forward_ms": round(forward_ms, 3), "forward_timing": "fastest of 3 forward runs of one shot",
+            "gradient_vs_forward": round(sec / n_shots * world / (forward_ms * 1e-3), 3),
+            "value": round(w.nodes * N * n_shots / sec / 1e9, 3), "unit": UNIT,
+            "i16_vs_fp32_checkpoints_rel_l2": None if err is None else round(err, 6),
+            "error_vs_fp64_oracle": "I16 6.9e-5, FP32 9.6e-6 relative L2 on the recipe reduced to 96^3 and 200 steps "
+                                    "(tests/test_gpu_gradient.py; bench.py --workload 3d_fwi_gradient_256 measures "
+                                    "it)",
+            "timing": "CUDA events around %d summed 16-shot gradient(s) after %d warm-up, max over ranks" % (
+                steps, warmup),
+            "parallelism": "shots partitioned over %d ranks" % world if world > 1 else "single"}
+
+
 def run_gradient(args, world, rank, local, dev):
     """Misfit gradient of 3d_fwi_gradient_256: a bench step is the gradient of
     the whole 16-shot objective, J = sum_s J_s and dJ/dc = sum_s dJ_s/dc
@@ -595,6 +667,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3, help="forwards timed end to end (0 skips)")
     ap.add_argument("--shape", default="",
                     help="override the workload's grid as nz,ny,nx (profiling runs on a smaller case only)")
+    ap.add_argument("--no-fwi", action="store_true",
+                    help="skip the misfit-gradient summary the default workload's line carries")
     ap.add_argument("--stencil", default="", choices=["", "auto", "plain", "tb2"],
                     help="kernel variant (default: the library's choice; tb2 for 2d_layered_4096, with the "
                          "per-step kernels timed beside it)")
@@ -754,6 +828,10 @@ def main():
     alg_bytes = (20 if two_step else BYTES_PER_UPDATE[vd]) * w.nodes
     achieved = alg_bytes / avg_launch_s / 1e9
     api.sw_destroy_grid(g)
+    # the misfit-gradient half of the metric, beside the headline forward
+    fwi_line = None
+    if args.workload == "3d_vd_512x512x384" and not args.no_fwi and not args.shape and not args.time_steps:
+        fwi_line = fwi_summary(world, rank, dev)
 
     if rank == 0:
         line = {
@@ -785,6 +863,8 @@ def main():
             line["config"]["stencil"] = "two time steps per launch (temporal blocking, SW_STENCIL_TB2)"
         if per_step is not None:
             line["per_step_kernels"] = per_step
+        if fwi_line is not None:
+            line["fwi"] = fwi_line
         if not args.no_cpu_baseline and world == 1:
             cb, _ = cpu_baseline(args.workload)
             line["cpu_baseline"] = cb
