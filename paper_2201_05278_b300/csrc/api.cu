@@ -537,9 +537,9 @@ void launch_image(int R, int ndim, dim3 grid, const float* p, const float* psi, 
 #define SW_IMAGE(RR)                                                                            \
   case RR:                                                                                       \
     if (ndim == 3)                                                                               \
-      image_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, gk, f, lc);                              \
+      launch_dependent(image_kernel<RR, 3>, grid, dim3(128), 0, st, p, psi, gk, f, lc);                              \
     else                                                                                         \
-      image_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, gk, f, lc);                              \
+      launch_dependent(image_kernel<RR, 2>, grid, dim3(128), 0, st, p, psi, gk, f, lc);                              \
     break;
   switch (R) {
     SW_IMAGE(1) SW_IMAGE(2) SW_IMAGE(3) SW_IMAGE(4) SW_IMAGE(5)
@@ -554,10 +554,10 @@ void launch_image_vd(int R, int ndim, dim3 grid, const float* p, const float* ps
 #define SW_IMAGE_VD(RR)                                                                                            \
   case RR:                                                                                                          \
     if (ndim == 3)                                                                                                  \
-      image_vd_kernel<RR, 3><<<grid, 128, 0, st>>>(p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
+      launch_dependent(image_vd_kernel<RR, 3>, grid, dim3(128), 0, st, p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
                                                    lc, w);                                                          \
     else                                                                                                            \
-      image_vd_kernel<RR, 2><<<grid, 128, 0, st>>>(p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
+      launch_dependent(image_vd_kernel<RR, 2>, grid, dim3(128), 0, st, p, psi, gg[0], gg[1], gg[2], gk, ag[0], ag[1], ag[2], f,        \
                                                    lc, w);                                                          \
     break;
   switch (R) {
@@ -1633,7 +1633,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     else
       launch_stencil(g->R, g->ndim, vd, a, st);
     if (taps > 0)
-      inject_sources_kernel<<<(taps + 127) / 128, 128, 0, st>>>(a.pout, a.kappa, g->damp, pts, sig, sig_stride, n,
+      launch_dependent(inject_sources_kernel, dim3((taps + 127) / 128), dim3(128), 0, st, a.pout, a.kappa, g->damp, pts, sig, sig_stride, n,
                                                                 f, g->ndim, g->R);
     launch_face_conditions(a.pout, f, g->R, recs, seis, n, st);
     SW_CUDA(cudaGetLastError());
@@ -1695,7 +1695,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
           unsigned* sc = scales + slot;
           char* dst = static_cast<char*>(packs) + pbytes * slot;
           if (i16) {
-            pack_rows_i16_kernel<<<unsigned(std::min<int64_t>((nrows + 7) / 8, 4736)), 256, 0, st>>>(
+            launch_dependent(pack_rows_i16_kernel, dim3(unsigned(std::min<int64_t>((nrows + 7) / 8, 4736))), dim3(256), 0, st, 
                 a_f, b_f, f, row_scales + size_t(nrows) * slot, reinterpret_cast<int16_t*>(dst));
             continue;
           }
@@ -1736,7 +1736,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     else
       launch_stencil(g->R, g->ndim, false, a, st);
     if (vd)  // - sum_a D_a^T (G_a psi)
-      vd_adjoint_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
+      launch_dependent(vd_adjoint_kernel, dim3(grid_blocks(g->nodes(), 256)), dim3(256), 0, st, g->at0(p1), GG[0], GG[1], GG[2], a.kappa,
                                                                       g->damp, g->at0(p2), f, vw, g->R, g->ndim);
     // its Neumann-face correction and the residuals into psi through the
     // receiver windows (rows with non-zero weight only), in one launch
@@ -1751,7 +1751,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     SourceImaging si{};
     if (src_threads > 0 && pending_src == k + 1 && g->live(k))
       si = SourceImaging{g->at0(p1), g->at0(GK), src, g->wavelet, g->sig_stride, k, (src_threads + 255) / 256};
-    adjoint_additions_kernel<<<unsigned(si.blocks + nb.x + nb.y + nb.z + (rthreads + 255) / 256), 256, 0, st>>>(
+    launch_dependent(adjoint_additions_kernel, dim3(unsigned(si.blocks + nb.x + nb.y + nb.z + (rthreads + 255) / 256)), dim3(256), 0, st, 
         g->at0(p1), g->at0(p2), a.kappa, g->damp, f, lc, g->R, nb, rec, g->rec_rows_max, res, N, k - 1, g->ndim,
         si);
     launch_face_conditions(g->at0(p2), f, g->R, none, nullptr, 0, st);
@@ -1845,7 +1845,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
           const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
           const float* base = i == 0 ? g->at0(B(1)) : nullptr;
           if (i16)
-            unpack_rows_i16_kernel<<<unsigned(std::min<int64_t>((nrows + 7) / 8, 4736)), 256, 0, st>>>(
+            launch_dependent(unpack_rows_i16_kernel, dim3(unsigned(std::min<int64_t>((nrows + 7) / 8, 4736))), dim3(256), 0, st, 
                 reinterpret_cast<const int16_t*>(src_p),
                                                                 row_scales + size_t(nrows) * slot, f, base,
                                                                 g->at0(B(i)));

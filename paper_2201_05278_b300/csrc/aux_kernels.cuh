@@ -377,36 +377,31 @@ __global__ void mirror_even_kernel(float* f_, FaceInfo f, int axis, int R) {
 // (even) face gets its mirror image in that face's ghost layer; a node on any
 // Dirichlet face is mirrored as zero.  z and y faces: one thread per (side,
 // position on the face), consecutive threads at consecutive x, walking the R
-// nodes next to the face.  x faces: one thread per (side, row, offset j), so
-// that a warp reads and writes whole runs of a few rows.  Ghost layers of
+// nodes next to the face; a block covers 256 consecutive x of one line of
+// the face, so a thread finds its position without a division.  x faces:
+// kFaceLanes lanes per row, lane l writing ghost column l + 1 of its side, so
+// that each row's ghosts go out as one whole 32- or 64-byte run; the columns
+// past R get zeros (nothing reads them: the stencils use R ghost columns, and
+// the x pad holds zeros there from the allocation on).  Ghost layers of
 // different axes are disjoint, and a node read for mirroring while another
 // thread zeroes it is taken as zero either way.  Needs every axis longer than
 // 2R+1 (a node is within R of one face only).
 template <int AX, int R>
-__device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int t) {
-  // the two axes spanning the face: a (slow) and b (fast)
-  const int na = AX == 0 ? f.ny : f.nz;
-  const int nb = AX == 2 ? f.ny : f.nx;
-  const int n = AX == 0 ? f.nz : (AX == 1 ? f.ny : f.nx);
+__device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int side, int ia, int ib) {
+  // ia: position along the slower axis spanning the face (y for z faces, z
+  // for y faces), ib: x
+  const int n = AX == 0 ? f.nz : f.ny;
   const int64_t sa = AX == 0 ? f.sy : f.sz;
-  const int64_t sb = AX == 2 ? f.sy : 1;
-  const int64_t s = AX == 0 ? f.sz : (AX == 1 ? f.sy : 1);
-  const int face = na * nb;
-  const int side = t >= face ? 1 : 0;
-  const int e = t - side * face;
+  const int64_t s = AX == 0 ? f.sz : f.sy;
   const int bc = side ? f.bc[2 * AX + 1] : f.bc[2 * AX];
   if (bc == kBcNone) return;
-  const int ia = e / nb, ib = e - (e / nb) * nb;
   // is the line on a Dirichlet face of another axis? (then every node of it is zero)
-  int cz = 0, cy = 0, cx = 0;
-  if (AX == 0) { cy = ia; cx = ib; }
-  if (AX == 1) { cz = ia; cx = ib; }
-  if (AX == 2) { cz = ia; cy = ib; }
+  const int cz = AX == 1 ? ia : 0, cy = AX == 0 ? ia : 0;
   const bool zero = (AX != 0 && ((cz == 0 && f.bc[0] == kBcDirichlet) || (cz == f.nz - 1 && f.bc[1] == kBcDirichlet))) ||
                     (AX != 1 && ((cy == 0 && f.bc[2] == kBcDirichlet) || (cy == f.ny - 1 && f.bc[3] == kBcDirichlet))) ||
-                    (AX != 2 && ((cx == 0 && f.bc[4] == kBcDirichlet) || (cx == f.nx - 1 && f.bc[5] == kBcDirichlet)));
-  float* q = p + ia * sa + ib * sb + (side ? int64_t(n - 1) * s : 0);  // the face node
-  const int64_t in = side ? -s : s;                                    // inwards
+                    ((ib == 0 && f.bc[4] == kBcDirichlet) || (ib == f.nx - 1 && f.bc[5] == kBcDirichlet));
+  float* q = p + ia * sa + ib + (side ? int64_t(n - 1) * s : 0);  // the face node
+  const int64_t in = side ? -s : s;                                // inwards
   const float sign = (bc == kBcDirichlet) ? -1.f : 1.f;
   float v[R + 1];
 #pragma unroll
@@ -417,20 +412,23 @@ __device__ __forceinline__ void face_line(float* p, const FaceInfo& f, int t) {
 }
 
 template <int R>
-__device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int t) {
-  const int line = t / R, j = t - line * R + 1;
-  const int face = f.nz * f.ny;
-  const int side = line >= face ? 1 : 0;
-  const int e = line - side * face;
+constexpr int face_lanes() { return R <= 8 ? 8 : 16; }
+
+// Ghost column j (1 .. face_lanes<R>()) of the row (side, z, y) on an x face.
+template <int R>
+__device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int side, int z, int y, int j) {
   const int bc = side ? f.bc[5] : f.bc[4];
   if (bc == kBcNone) return;
-  const int z = e / f.ny, y = e - (e / f.ny) * f.ny;
   const bool zero = (z == 0 && f.bc[0] == kBcDirichlet) || (z == f.nz - 1 && f.bc[1] == kBcDirichlet) ||
                     (y == 0 && f.bc[2] == kBcDirichlet) || (y == f.ny - 1 && f.bc[3] == kBcDirichlet);
   float* q = p + int64_t(z) * f.sz + int64_t(y) * f.sy + (side ? f.nx - 1 : 0);  // the face node
   const int in = side ? -1 : 1;
-  const float v = q[j * in];
-  q[-j * in] = zero ? 0.f : ((bc == kBcDirichlet) ? -v : v);
+  float v = 0.f;
+  if (j <= R && !zero) {
+    v = q[j * in];
+    if (bc == kBcDirichlet) v = -v;
+  }
+  q[-j * in] = v;
   if (j == 1 && (bc == kBcDirichlet || zero)) q[0] = 0.f;
 }
 
@@ -441,6 +439,8 @@ __device__ __forceinline__ void face_x(float* p, const FaceInfo& f, int t) {
 // longer load chains start early, then z faces, y faces and x faces.
 struct FaceGrid {
   int rec, z, y, x, pre;  // blocks per part
+  int bxz;                // blocks per face line along x (z and y faces)
+  int bxx;                // blocks per z plane of an x face
   int total() const { return rec + z + y + x + pre; }
 };
 
@@ -480,20 +480,28 @@ __global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float
     return;
   }
   b -= fg.rec;
-  if (b < fg.z) {
-    const int t = b * blockDim.x + threadIdx.x;
-    if (t < 2 * f.ny * f.nx) face_line<0, R>(p, f, t);
+  if (b < fg.z + fg.y) {  // block: 256 consecutive x of one (side, y) or (side, z) line
+    const bool zf = b < fg.z;
+    if (!zf) b -= fg.z;
+    const int line = b / fg.bxz;
+    const int ib = (b - line * fg.bxz) * 256 + threadIdx.x;
+    if (ib >= f.nx) return;
+    const int na = zf ? f.ny : f.nz;
+    const int side = line >= na ? 1 : 0;
+    if (zf)
+      face_line<0, R>(p, f, side, line - side * na, ib);
+    else
+      face_line<1, R>(p, f, side, line - side * na, ib);
     return;
   }
-  b -= fg.z;
-  if (b < fg.y) {
-    const int t = b * blockDim.x + threadIdx.x;
-    if (t < 2 * f.nz * f.nx) face_line<1, R>(p, f, t);
-    return;
-  }
-  b -= fg.y;
-  const int t = b * blockDim.x + threadIdx.x;
-  if (t < 2 * f.nz * f.ny * R) face_x<R>(p, f, t);
+  b -= fg.z + fg.y;
+  // block: 256 / kFaceLanes consecutive rows of one (side, z) plane of an x face
+  constexpr int LPR = face_lanes<R>();
+  const int plane = b / fg.bxx;
+  const int y = (b - plane * fg.bxx) * (256 / LPR) + int(threadIdx.x) / LPR;
+  if (y >= f.ny) return;
+  const int side = plane >= f.nz ? 1 : 0;
+  face_x<R>(p, f, side, plane - side * f.nz, y, int(threadIdx.x) % LPR + 1);
 }
 
 // Launch with programmatic stream serialization: the kernel may start before
@@ -526,9 +534,12 @@ inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const Poi
   // ghosts stay zero): no blocks for it (the y axis of a 2D grid)
   const bool zf = f.bc[0] != kBcNone || f.bc[1] != kBcNone, yf = f.bc[2] != kBcNone || f.bc[3] != kBcNone,
              xf = f.bc[4] != kBcNone || f.bc[5] != kBcNone;
-  fg.z = zf ? int((2 * int64_t(f.ny) * f.nx + 255) / 256) : 0;
-  fg.y = yf ? int((2 * int64_t(f.nz) * f.nx + 255) / 256) : 0;
-  fg.x = xf ? int((2 * int64_t(f.nz) * f.ny * R + 255) / 256) : 0;
+  const int lpr = R <= 8 ? 8 : 16;  // face_lanes<R>()
+  fg.bxz = (f.nx + 255) / 256;
+  fg.bxx = (f.ny + 256 / lpr - 1) / (256 / lpr);
+  fg.z = zf ? 2 * f.ny * fg.bxz : 0;
+  fg.y = yf ? 2 * f.nz * fg.bxz : 0;
+  fg.x = xf ? 2 * f.nz * fg.bxx : 0;
   const unsigned grid = unsigned(fg.total());
   switch (R) {
     case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
@@ -656,6 +667,8 @@ struct SourceImaging {
 __global__ void adjoint_additions_kernel(const float* psi1, float* out, const float* kappa, const float2* damp,
                                          FaceInfo f, LapCoef lc, int R, int3 nb, PointSet rec, int max_rows,
                                          const float* res, int res_stride, int step, int ndim, SourceImaging si) {
+  griddep_launch_dependents();
+  griddep_wait();  // the adjoint stencil launched before
   int b = blockIdx.x;
   if (b < si.blocks) {  // an earlier step's source imaging (adds to gk, reads other arrays than out)
     image_source_tap(si.psi, si.gk, si.src, si.sig, si.sig_stride, si.step, f, b * blockDim.x + threadIdx.x);
@@ -687,6 +700,8 @@ __global__ void adjoint_additions_kernel(const float* psi1, float* out, const fl
 // the pass reads no kappa.  Block (128 x, y, z).
 template <int R, int NDIM>
 __global__ void image_kernel(const float* p, const float* psi, float* gk, FaceInfo f, LapCoef lc) {
+  griddep_launch_dependents();
+  griddep_wait();  // psi of the face launch before
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= f.nx) return;
@@ -783,6 +798,8 @@ __device__ __forceinline__ float mirror_sign(int bc) {
 __global__ void vd_adjoint_kernel(const float* psi, const float* gz, const float* gy, const float* gx,
                                   const float* kappa, const float2* damp, float* out, FaceInfo f, VdWeights W, int R,
                                   int ndim) {
+  griddep_launch_dependents();
+  griddep_wait();  // the adjoint stencil launched before
   const int64_t n = int64_t(f.nz) * f.ny * f.nx;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int x = int(i % f.nx);
@@ -815,6 +832,8 @@ template <int R, int NDIM>
 __global__ void image_vd_kernel(const float* p, const float* psi, const float* gz,
                                 const float* gy, const float* gx, float* gk, float* az, float* ay, float* ax,
                                 FaceInfo f, LapCoef lc, VdWeights W) {
+  griddep_launch_dependents();
+  griddep_wait();  // psi of the face launch before
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= f.nx) return;
@@ -941,6 +960,8 @@ __global__ void unpack_snapshot_kernel(const T* in, const unsigned* scale_bits, 
 // s / 32767 is small next to the values that matter, where a 16-bit float
 // keeps only 8 or 11 bits of every value.  One CTA of 256 threads per row.
 __global__ void pack_rows_i16_kernel(const float* p, const float* base, FaceInfo f, float* scales, int16_t* out) {
+  griddep_launch_dependents();
+  griddep_wait();  // the level of the stencil launched before
   // one warp per (z, y) row; rows of a multiple of 4 nodes in float4 / 4 x int16 pieces
   // (row starts are 128-byte aligned in the padded layout), others one node per lane
   const int lane = threadIdx.x & 31;
@@ -994,6 +1015,8 @@ __global__ void pack_rows_i16_kernel(const float* p, const float* base, FaceInfo
 // (z, y) row, in 4-node pieces when the row length allows.
 __global__ void unpack_rows_i16_kernel(const int16_t* in, const float* scales, FaceInfo f, const float* base,
                                        float* p) {
+  griddep_launch_dependents();
+  griddep_wait();  // the kernels launched before
   const int lane = threadIdx.x & 31;
   const int64_t rows = int64_t(f.nz) * f.ny;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
