@@ -1856,8 +1856,10 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
             unpack_snapshot_kernel<__half><<<row_grid(f), 256, 0, st>>>(
                 reinterpret_cast<const __half*>(src_p), scales + slot, f, base, g->at0(B(i)));
         }
-        for (int i = 0; i < 2; ++i)
-          launch_face_conditions(g->at0(B(i)), f, g->R, none, nullptr, 0, st);  // ghosts of the restored levels
+        // ghosts of the restored p[k0]; p[k0-1] is read at its nodes only (as
+        // the first recomputed step's p[n-1]), and its Dirichlet face nodes
+        // come back as exact zeros (0 - 0 from zero codes), so it needs none
+        launch_face_conditions(g->at0(B(1)), f, g->R, none, nullptr, 0, st);
         SW_CUDA(cudaGetLastError());
       } else {
         SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
@@ -1906,9 +1908,9 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   SW_CUDA(cudaMemcpyAsync(misfit, macc, sizeof(double), cudaMemcpyDeviceToHost, st));
   SW_TRY(check_device_flag(g));
   // + residual and velocity gradient, density gradient, ln rho gradients,
-  // and per 16-bit checkpoint segment absmax + pack and unpack + faces of two levels
+  // and per 16-bit checkpoint segment absmax + pack and unpack + the face pass of the restored level
   g->kernel_launches = nk + 1 + n_shots + (grad_rho ? 1 : 0) + (own_g ? 1 : 0) +
-                       (packed ? (i16 ? 6 : 8) * int64_t(nseg) * n_shots : 0);
+                       (packed ? (i16 ? 5 : 7) * int64_t(nseg) * n_shots : 0);
   g->stencil_launches = 0;
   g->stencil_ms = 0.0;
   return SW_OK;

@@ -6,14 +6,14 @@ afford cudaMalloc's device-wide synchronisation): it keeps its wavefields and
 tables in one static device array instead.  These tests call it through the
 C ABI twice in a row (the array keeps the previous call's contents, so the
 second call checks that everything that must start at zero is cleared) and
-compare with the handle-based sw_forward within the parity tolerance.  The
-file is named to be collected last.
+compare with the handle-based sw_forward and with the FP64 oracle, within the
+parity tolerance.  The file is named to be collected last.
 """
 import numpy as np
 import pytest
 
 from paper_2201_05278_b300 import api
-from tests.harness import FP32_SEIS_TOL, assert_parity, rel_l2, run_gpu
+from tests.harness import FP32_SEIS_TOL, assert_parity, rel_l2, run_gpu, run_oracle
 from tests.test_gpu_parity import small_case
 
 pytestmark = pytest.mark.gpu
@@ -36,11 +36,14 @@ def _noalloc(w, n_steps):
 def test_noalloc_matches_sw_forward_twice(cuda_device, ndim, order, density):
     w = small_case(ndim, order, density, seed=11 + order, n_steps=50)
     s_ref, p_ref = run_gpu(w)
+    s_or, p_or = run_oracle(w)
     for _ in range(2):
         s, p = _noalloc(w, w.n_steps)
         assert np.all(np.isfinite(s)) and np.all(np.isfinite(p))
         assert_parity(s, s_ref, "seismogram")
         assert_parity(p, p_ref, "field")
+        assert_parity(s, s_or, "seismogram vs oracle")
+        assert_parity(p, p_or, "field vs oracle")
 
 
 def _raw_call(shape, vel_ptr, n_steps=1):
