@@ -318,12 +318,25 @@ sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t
  * group: each tile of the model is read once per step for all its shots.
  * Every shot gives the same result as sw_forward on its grid alone.
  *
+ * A batch of 3D constant-density grids (any sizes, one space order, every
+ * grid with equal spacings along its axes or none) runs per time step one
+ * launch of the pipelined stencil over a work list of (64 x 16 tile, plane)
+ * items of all grids, and one launch of every grid's face conditions,
+ * receiver samples and next step's sources (which enter through the level
+ * the step reads as p[n-1], as in sw_forward); small grids, which alone
+ * leave most of the GPU idle or pay a warm-up per tile column, share the
+ * launch.  Each grid gives the same result as sw_forward on it alone, bit
+ * for bit.
+ *
  * sw_create_batch borrows the grids (they must outlive the batch and keep
  * their model and acquisition; a grid changed afterwards makes
- * sw_batch_forward fail with SW_ESTATE).  Errors: SW_EINVAL for 3D or
- * variable-density grids, mixed orders, streams or devices, a grid listed
- * twice, grids with forcing or snapshots; SW_ESTATE for a grid without model
- * or acquisition.
+ * sw_batch_forward fail with SW_ESTATE).  Errors: SW_EINVAL for
+ * variable-density grids, grids of different dimensions, mixed orders,
+ * streams or devices, a grid listed twice, grids with forcing or snapshots,
+ * and (3D) grids the pipelined kernel does not take (sw_set_stencil_variant
+ * plain, too large), mixed equal and unequal spacings, or source windows
+ * where eta dt reaches 1/2; SW_ESTATE for a grid without model or
+ * acquisition.
  *
  * sw_batch_forward runs n_steps steps of every grid from rest (or from its
  * sw_set_initial_state levels).  seismograms[i] is grid i's [n_steps][n_rec]
@@ -332,16 +345,17 @@ sw_status sw_set_saving(sw_grid* g, int saving_stride, float* snapshots, int64_t
  * after the last step (host or device).  The time loop is captured as a CUDA
  * graph on the second call with the same n_steps.  Blocks until done.
  *
- * sw_batch_info: number of model groups and of work items (tile of one
- * shot) per step.
+ * sw_batch_info: number of model groups (3D: grids) and of work items
+ * (tile of one shot; 3D: tile and plane) per step.
  *
- * Tile shape: tiles are 128 columns wide and 16, 32 or 64 rows high.
+ * Tile shape (2D): tiles are 128 columns wide and 16, 32 or 64 rows high.
  * sw_create_batch tunes the height on the batch itself: it times a few
  * stencil launches with each height (on zeroed fields) and keeps the
  * fastest.  sw_batch_get_tile returns the height in use and, if tuned_us is
  * not NULL, the three timings (microseconds per launch, heights 16, 32, 64);
- * sw_batch_set_tile forces a height (SW_EINVAL for another value).  The
- * results do not depend on the height.
+ * sw_batch_set_tile forces a height (SW_EINVAL for another value, and for
+ * a 3D batch, whose tiles are those of the pipelined kernel).  The results
+ * do not depend on the height.
  * sw_batch_set_profiling / sw_batch_get_profile: as for a grid (every
  * every-th stencil launch timed with CUDA events).
  */

@@ -223,7 +223,8 @@ def _ptr_array(items):
 
 
 def sw_create_batch(grids) -> Batch:
-    """Batch of 2D constant-density grids advanced together (shots of one model share its reads)."""
+    """Batch of constant-density grids advanced together: 2D grids (shots of one model share its reads) or 3D
+    grids (one pipelined stencil launch and one face launch per step for all)."""
     grids = list(grids)
     handles = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
     h = ctypes.c_void_p()

@@ -2451,6 +2451,14 @@ struct sw_batch {
   double stencil_ms = 0.0;
   int64_t stencil_launches = 0, kernel_launches = 0;
   int64_t nodes_per_step = 0;
+  // batches of 3D grids: one pipelined stencil launch and one face launch per
+  // step for all grids (descriptors per level parity in device memory)
+  bool is3d = false, iso = false;
+  int units = 0, face_blocks = 0;
+  TmaGridDesc* d_tdesc[2] = {nullptr, nullptr};
+  std::vector<FaceBatchDesc> fdesc;
+  FaceBatchDesc* d_fdesc = nullptr;
+  std::vector<unsigned char*> d_live;  // per grid: per step, some source sample is non-zero
 };
 
 namespace {
@@ -2557,6 +2565,353 @@ sw_status tune_batch(sw_batch* b) {
   return check_device_flag(b->grids[0]);
 }
 
+
+// ---- batches of 3D grids ------------------------------------------------
+
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO>
+void launch_tma_batch_iso(const sw_batch* b, int parity, cudaStream_t st) {
+  using C = TmaConfig<R, TY, PPT, NB, false>;
+  auto kern = stencil_tma_kernel<R, TY, PPT, NB, MINB, ISO, false, false, true>;
+  static int blocks_per_sm = 0;
+  if (!blocks_per_sm) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, C::NT, C::SMEM);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const sw_grid* g0 = b->grids[0];
+  TmaWork wk;
+  wk.tiles_x = 1;
+  wk.nz = 1;
+  wk.total = b->units;
+  wk.starve = g0->starve ? 1 : 0;
+  wk.grids = b->d_tdesc[parity];
+  wk.n_grids = int(b->grids.size());
+  long long grid = (long long)g0->sm_count * blocks_per_sm;
+  if (grid > wk.total) grid = wk.total;
+  // the kernel's own maps and arguments are not read in a batch (each grid's
+  // come from its descriptor); grid 0's stand in
+  const StencilArgs a0 = stencil_args(g0);
+  launch_dependent(kern, dim3(unsigned(grid)), dim3(C::NT), C::SMEM, st, g0->map_halo[0], g0->map_inner[0],
+                   g0->map_warm[0], g0->map_inner[1], g0->map_kappa, g0->map_kappa, g0->map_kappa, g0->map_kappa, a0,
+                   wk, g0->dflag, g0->wait_limit_ns);
+}
+
+template <int R, int TY, int PPT, int NB, int MINB>
+void launch_tma_batch_t(const sw_batch* b, int parity, cudaStream_t st) {
+  if (b->iso)
+    launch_tma_batch_iso<R, TY, PPT, NB, MINB, true>(b, parity, st);
+  else
+    launch_tma_batch_iso<R, TY, PPT, NB, MINB, false>(b, parity, st);
+}
+
+// One step's stencil for every grid of a 3D batch (the tile shapes of the
+// single-grid constant-density kernel).
+void launch_stencil_tma_batch(const sw_batch* b, int parity, cudaStream_t st) {
+  switch (b->R) {
+    case 1: launch_tma_batch_t<1, 16, 4, 3, 3>(b, parity, st); break;
+    case 2: launch_tma_batch_t<2, 16, 4, 3, 3>(b, parity, st); break;
+    case 3: launch_tma_batch_t<3, 16, 4, 3, 3>(b, parity, st); break;
+    case 4: launch_tma_batch_t<4, 16, 4, 3, 3>(b, parity, st); break;
+    case 5: launch_tma_batch_t<5, 16, 2, 4, 2>(b, parity, st); break;
+    case 6: launch_tma_batch_t<6, 16, 2, 4, 2>(b, parity, st); break;
+    case 7: launch_tma_batch_t<7, 16, 2, 4, 1>(b, parity, st); break;
+    case 8: launch_tma_batch_t<8, 16, 2, 4, 1>(b, parity, st); break;
+    case 9: launch_tma_batch_t<9, 16, 2, 4, 1>(b, parity, st); break;
+    case 10: launch_tma_batch_t<10, 16, 2, 4, 1>(b, parity, st); break;
+    default: break;
+  }
+}
+
+void launch_face_batch(const sw_batch* b, int step, int n_steps, cudaStream_t st) {
+  const int n = int(b->grids.size());
+  const dim3 grid(unsigned(b->face_blocks)), block(256);
+  switch (b->R) {
+    case 1: launch_dependent(face_batch_kernel<1>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 2: launch_dependent(face_batch_kernel<2>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 3: launch_dependent(face_batch_kernel<3>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 4: launch_dependent(face_batch_kernel<4>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 5: launch_dependent(face_batch_kernel<5>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 6: launch_dependent(face_batch_kernel<6>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 7: launch_dependent(face_batch_kernel<7>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 8: launch_dependent(face_batch_kernel<8>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 9: launch_dependent(face_batch_kernel<9>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 10: launch_dependent(face_batch_kernel<10>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    default: break;
+  }
+}
+
+
+void free_batch_3d(sw_batch* b) {
+  for (int c = 0; c < 2; ++c) cudaFree(b->d_tdesc[c]);
+  cudaFree(b->d_fdesc);
+  for (unsigned char* p : b->d_live) cudaFree(p);
+  b->d_live.clear();
+}
+
+// A batch of 3D grids of constant density: one work list of (64 x 16 tile,
+// plane) items over every grid for the pipelined stencil, one face launch
+// of every grid's blocks.  The grids keep their own levels, tensor maps,
+// model and acquisition; each grid's sources enter through p[n-1]
+// (PreInject), so their windows must not lie where eta dt reaches 1/2.
+sw_status create_batch_3d(sw_batch** out, sw_grid* const* grids, int n) {
+  const sw_grid* g0 = grids[0];
+  auto iso_of = [](const sw_grid* g) { return g->h[0] == g->h[1] && g->h[1] == g->h[2]; };
+  int64_t units = 0, face_blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    const sw_grid* g = grids[i];
+    if (!g) return fail(SW_EINVAL, "grid %d is NULL", i);
+    if (!g->has_model || !g->has_acq) return fail(SW_ESTATE, "grid %d has no model or acquisition yet", i);
+    if (g->ndim != 3) return fail(SW_EINVAL, "a batch holds grids of one dimension (grid %d)", i);
+    if (g->has_density) return fail(SW_EINVAL, "batches hold constant-density grids only (grid %d)", i);
+    if (g->R != g0->R) return fail(SW_EINVAL, "all grids of a batch need one space order (grid %d)", i);
+    if (iso_of(g) != iso_of(g0))
+      return fail(SW_EINVAL, "3D batches need equal spacings along the axes in every grid or in none (grid %d)", i);
+    if (g->stream != g0->stream || g->device != g0->device)
+      return fail(SW_EINVAL, "all grids of a batch need one device and stream (grid %d)", i);
+    if (g->n_force > 0 || g->snapshots) return fail(SW_EINVAL, "grid %d has forcing or snapshots set", i);
+    if (!use_tma(g)) return fail(SW_EINVAL, "grid %d cannot use the pipelined 3D kernel", i);
+    for (int j = 0; j < i; ++j)
+      if (grids[j] == g) return fail(SW_EINVAL, "grid %d appears twice", i);
+    if (g->n_src > 0) {
+      double sa, se;
+      damping_coefficients(g->alpha, g->degree, g->dt, g->src_d2_max, &sa, &se);
+      if (!(se < 0.5)) return fail(SW_EINVAL, "grid %d has source windows too deep in the absorbing layers", i);
+    }
+    const int64_t tiles = ((g->n[2] + 63) / 64) * ((g->n[1] + 15) / 16);
+    units += tiles * g->n[0];
+    const FaceGrid fg = face_grid(g->faces(), g->R, g->n_rec, g->n_src * g->lz * g->ly * g->lx);
+    face_blocks += fg.total();
+  }
+  if (units >= (int64_t(1) << 31) || face_blocks >= (int64_t(1) << 31))
+    return fail(SW_EINVAL, "the batch is too large for one work list");
+  sw_batch* b = new sw_batch();
+  b->is3d = true;
+  b->iso = iso_of(g0);
+  b->grids.assign(grids, grids + n);
+  b->R = g0->R;
+  b->stream = g0->stream;
+  b->units = int(units);
+  b->face_blocks = int(face_blocks);
+  b->n_groups = n;
+  std::vector<TmaGridDesc> td[2];
+  b->fdesc.resize(size_t(n));
+  int unit0 = 0, block0 = 0;
+  for (int i = 0; i < n; ++i) {
+    sw_grid* g = grids[i];
+    b->gens.push_back(g->config_gen);
+    b->nodes_per_step += g->nodes();
+    const int tx = int((g->n[2] + 63) / 64), ty = int((g->n[1] + 15) / 16);
+    for (int par = 0; par < 2; ++par) {
+      TmaGridDesc D;
+      memset(&D, 0, sizeof(D));
+      D.c = g->map_halo[par];
+      D.f = g->map_inner[par];
+      D.w = g->map_warm[par];
+      D.o = g->map_inner[par ^ 1];
+      D.k = g->map_kappa;
+      D.a = stencil_args(g);
+      D.a.pn = g->at0(g->u[par]);
+      D.a.pnm1 = g->at0(g->u[par ^ 1]);
+      D.a.pout = g->at0(g->u[par ^ 1]);
+      D.unit0 = unit0;
+      D.tiles_x = tx;
+      D.nz = int(g->n[0]);
+      td[par].push_back(D);
+    }
+    unit0 += tx * ty * int(g->n[0]);
+    const int taps = g->lz * g->ly * g->lx;
+    if (g->n_src > 0 && !g->tap_off) {  // the source tap table (filled by every batch forward)
+      const size_t nt = size_t(g->n_src) * taps;
+      sw_status st = dev_alloc(g, (void**)&g->tap_off, nt * sizeof(int64_t));
+      if (st == SW_OK) st = dev_alloc(g, (void**)&g->tap_coef, nt * sizeof(float));
+      if (st == SW_OK) st = dev_alloc(g, (void**)&g->tap_pre, nt * sizeof(float));
+      if (st != SW_OK) {
+        free_batch_3d(b);
+        delete b;
+        return st;
+      }
+    }
+    unsigned char* live = nullptr;
+    if (g->n_src > 0) {
+      if (cudaMalloc((void**)&live, g->sig_live.size()) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch_3d(b);
+        delete b;
+        return fail(SW_ENOMEM, "cudaMalloc of the batch's step table failed");
+      }
+      b->d_live.push_back(live);
+      cudaMemcpyAsync(live, g->sig_live.data(), g->sig_live.size(), cudaMemcpyHostToDevice, b->stream);
+    }
+    FaceBatchDesc& F = b->fdesc[size_t(i)];
+    memset(&F, 0, sizeof(F));
+    F.lv[0] = g->at0(g->u[0]);
+    F.lv[1] = g->at0(g->u[1]);
+    F.f = g->faces();
+    F.rec = point_set(g, false);
+    F.seis = nullptr;
+    F.fg = face_grid(F.f, g->R, g->n_rec, g->n_src * taps);
+    F.tap_off = g->tap_off;
+    F.tap_pre = g->tap_pre;
+    F.sig = g->wavelet;
+    F.live = live;
+    F.taps = taps;
+    F.n_src = g->n_src;
+    F.sig_stride = g->sig_stride;
+    F.block0 = block0;
+    block0 += F.fg.total();
+  }
+  bool ok = true;
+  for (int par = 0; par < 2 && ok; ++par)
+    ok = cudaMalloc((void**)&b->d_tdesc[par], size_t(n) * sizeof(TmaGridDesc)) == cudaSuccess &&
+         cudaMemcpyAsync(b->d_tdesc[par], td[par].data(), size_t(n) * sizeof(TmaGridDesc), cudaMemcpyHostToDevice,
+                         b->stream) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&b->d_fdesc, size_t(n) * sizeof(FaceBatchDesc)) == cudaSuccess &&
+       cudaMemcpyAsync(b->d_fdesc, b->fdesc.data(), size_t(n) * sizeof(FaceBatchDesc), cudaMemcpyHostToDevice,
+                       b->stream) == cudaSuccess &&
+       cudaStreamSynchronize(b->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_batch_3d(b);
+    delete b;
+    return fail(SW_ENOMEM, "device memory for the batch's descriptors");
+  }
+  *out = b;
+  return SW_OK;
+}
+
+sw_status batch_forward_3d(sw_batch* b, int n_steps, float* const* seismograms, float* const* final_fields) {
+  const int n = int(b->grids.size());
+  for (int i = 0; i < n; ++i) {
+    const sw_grid* g = b->grids[size_t(i)];
+    if (g->config_gen != b->gens[size_t(i)] || g->n_force > 0 || g->snapshots || !use_tma(g))
+      return fail(SW_ESTATE, "grid %d changed after sw_create_batch", i);
+    if (g->n_src > 0 && n_steps > g->nt)
+      return fail(SW_EINVAL, "n_steps (%d) exceeds the wavelet length of grid %d (%d)", n_steps, i, g->nt);
+    if (g->n_rec > 0 && n_steps > 0) {
+      if (!seismograms || !seismograms[i]) return fail(SW_EINVAL, "seismogram of grid %d is NULL", i);
+      if (!is_device_pointer(seismograms[i])) return fail(SW_EINVAL, "seismogram of grid %d is not device memory", i);
+    }
+  }
+  cudaStream_t st = b->stream;
+  bool changed = false;
+  for (int i = 0; i < n; ++i) {
+    float* sp = (b->grids[size_t(i)]->n_rec > 0 && n_steps > 0) ? seismograms[i] : nullptr;
+    if (b->fdesc[size_t(i)].seis != sp) {
+      b->fdesc[size_t(i)].seis = sp;
+      changed = true;
+    }
+  }
+  if (changed) {
+    SW_CUDA(cudaMemcpyAsync(b->d_fdesc, b->fdesc.data(), b->fdesc.size() * sizeof(FaceBatchDesc),
+                            cudaMemcpyHostToDevice, st));
+    SW_CUDA(cudaStreamSynchronize(st));  // the host table may change again on the next call
+  }
+  int64_t launches = 0;
+  for (sw_grid* g : b->grids) {  // levels from rest (or the initial state), source taps, step 0's sources
+    const size_t fbytes = size_t(g->lay.total) * sizeof(float);
+    SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
+    const FaceInfo f = g->faces();
+    if (g->init_p0) {
+      insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->init_p0, g->at0(g->u[0]), f, 3, g->R);
+      ++launches;
+    }
+    if (g->init_pm1) {
+      insert_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->init_pm1, g->at0(g->u[1]), f, 3, g->R);
+      ++launches;
+    }
+    const int src_threads = g->n_src * g->lz * g->ly * g->lx;
+    if (src_threads > 0) {
+      source_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(g->at0(g->kappa), g->damp, point_set(g, true), f,
+                                                                    g->tap_off, g->tap_coef, g->tap_pre);
+      ++launches;
+      if (n_steps > 0 && g->live(0)) {  // step 0's sources, into p[-1]
+        inject_taps_kernel<<<(src_threads + 127) / 128, 128, 0, st>>>(
+            g->at0(g->u[1]), g->tap_off, g->tap_pre, g->lz * g->ly * g->lx, g->n_src, g->wavelet, g->sig_stride, 0);
+        ++launches;
+      }
+    }
+  }
+  SW_CUDA(cudaGetLastError());
+  const int timed = b->profiling ? (n_steps + b->profiling - 1) / b->profiling : 0;
+  if (timed && b->events.size() < size_t(2 * timed)) {
+    const size_t old = b->events.size();
+    b->events.resize(size_t(2 * timed));
+    for (size_t i = old; i < b->events.size(); ++i) SW_CUDA(cudaEventCreate(&b->events[i]));
+  }
+  // per step: the stencil of every grid, then every grid's face conditions,
+  // receiver samples and next step's sources
+  auto enqueue = [&](cudaStream_t s, bool capturing) -> sw_status {
+    const unsigned evflags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    for (int step = 0; step < n_steps; ++step) {
+      const bool time_it = b->profiling && step % b->profiling == 0;
+      const int ev = time_it ? 2 * (step / b->profiling) : 0;
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev)], s, evflags));
+      launch_stencil_tma_batch(b, step & 1, s);
+      if (time_it) SW_CUDA(cudaEventRecordWithFlags(b->events[size_t(ev + 1)], s, evflags));
+      launch_face_batch(b, step, n_steps, s);
+    }
+    SW_CUDA(cudaGetLastError());
+    return SW_OK;
+  };
+  if (n_steps > 0 && b->graph && b->graph_steps == n_steps) {
+    SW_CUDA(cudaGraphLaunch(b->graph, st));
+  } else if (n_steps > 0 && b->last_steps == n_steps) {
+    // second call with this length: capture the time loop once, replay it after
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      b->graph_steps = -1;
+    }
+    if (!b->cap_stream) SW_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    SW_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const sw_status s1 = enqueue(b->cap_stream, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (s1 != SW_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s1 != SW_OK ? s1 : fail(SW_ECUDA, "capturing the batch time loop failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      b->graph = nullptr;
+      return fail(SW_ECUDA, "instantiating the batch time loop failed: %s", cudaGetErrorString(ei));
+    }
+    b->graph_steps = n_steps;
+    SW_CUDA(cudaGraphLaunch(b->graph, st));
+  } else if (n_steps > 0) {
+    SW_TRY(enqueue(st, false));
+  }
+  if (n_steps > 0) b->last_steps = n_steps;
+  launches += 2 * int64_t(n_steps);
+  for (int i = 0; final_fields && i < n; ++i) {
+    if (!final_fields[i]) continue;
+    sw_grid* g = b->grids[size_t(i)];
+    float* dst = final_fields[i];
+    const bool fh = !is_device_pointer(dst);
+    if (fh) {
+      if (!g->staging) SW_TRY(dev_alloc(g, (void**)&g->staging, size_t(g->nodes()) * sizeof(float)));
+      dst = g->staging;
+    }
+    extract_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(g->u[n_steps & 1]), dst, g->faces());
+    SW_CUDA(cudaGetLastError());
+    ++launches;
+    if (fh)
+      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  SW_TRY(check_device_flag(b->grids[0]));  // synchronises
+  b->kernel_launches = launches;
+  b->stencil_launches = timed;
+  b->stencil_ms = 0.0;
+  for (int i = 0; i < timed; ++i) {
+    float ms = 0.f;
+    SW_CUDA(cudaEventElapsedTime(&ms, b->events[size_t(2 * i)], b->events[size_t(2 * i + 1)]));
+    b->stencil_ms += ms;
+  }
+  return SW_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -2566,6 +2921,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
   if (!out || !grids || n_grids < 1) return fail(SW_EINVAL, "NULL argument or empty batch");
   *out = nullptr;
   const sw_grid* g0 = grids[0];
+  if (g0 && g0->ndim == 3) return create_batch_3d(out, grids, n_grids);
   for (int i = 0; i < n_grids; ++i) {
     const sw_grid* g = grids[i];
     if (!g) return fail(SW_EINVAL, "grid %d is NULL", i);
@@ -2706,7 +3062,7 @@ sw_status sw_create_batch(sw_batch** out, sw_grid* const* grids, int n_grids) {
 sw_status sw_batch_info(const sw_batch* b, int* n_groups, int* n_items) {
   if (!b) return fail(SW_EINVAL, "NULL batch");
   if (n_groups) *n_groups = b->n_groups;
-  if (n_items) *n_items = b->total_items[b->cfg];
+  if (n_items) *n_items = b->is3d ? b->units : b->total_items[b->cfg];
   return SW_OK;
 }
 
@@ -2720,6 +3076,7 @@ sw_status sw_batch_get_tile(const sw_batch* b, int* tile_rows, float* tuned_us) 
 
 sw_status sw_batch_set_tile(sw_batch* b, int tile_rows) {
   if (!b) return fail(SW_EINVAL, "NULL batch");
+  if (b->is3d) return fail(SW_EINVAL, "a 3D batch has the pipelined kernel's tiles");
   for (int c = 0; c < 3; ++c)
     if (kBatchZBs[c] == tile_rows) {
       if (c != b->cfg) {
@@ -2762,6 +3119,7 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
   g_last_error.clear();
   if (!b) return fail(SW_EINVAL, "NULL batch");
   if (n_steps < 0) return fail(SW_EINVAL, "n_steps < 0");
+  if (b->is3d) return batch_forward_3d(b, n_steps, seismograms, final_fields);
   const int n = int(b->grids.size());
   for (int i = 0; i < n; ++i) {
     const sw_grid* g = b->grids[size_t(i)];
@@ -2914,6 +3272,7 @@ void sw_destroy_batch(sw_batch* b) {
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   for (int c = 0; c < 3; ++c) cudaFree(b->d_groups[c]);
   cudaFree(b->d_shots);
+  free_batch_3d(b);
   delete b;
 }
 

@@ -459,12 +459,10 @@ struct PreInject {
   int taps, count, sig_stride, step;
 };
 
+// Block b of the face launch of one grid (the parts in the order of FaceGrid).
 template <int R>
-__global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg,
-                                       PreInject pi) {
-  griddep_launch_dependents();
-  griddep_wait();  // p[n+1] of the stencil and the injection launched before
-  int b = blockIdx.x;
+__device__ __forceinline__ void face_block(float* p, const FaceInfo& f, const PointSet& rec, float* out, int step,
+                                           const FaceGrid& fg, const PreInject& pi, int b) {
   if (b < fg.pre) {  // a different level from the one the other parts touch
     const int t = b * blockDim.x + threadIdx.x;
     if (t < pi.count * pi.taps) {
@@ -504,6 +502,46 @@ __global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float
   face_x<R>(p, f, side, plane - side * f.nz, y, int(threadIdx.x) % LPR + 1);
 }
 
+template <int R>
+__global__ void face_conditions_kernel(float* p, FaceInfo f, PointSet rec, float* out, int step, FaceGrid fg,
+                                       PreInject pi) {
+  griddep_launch_dependents();
+  griddep_wait();  // p[n+1] of the stencil and the injection launched before
+  face_block<R>(p, f, rec, out, step, fg, pi, blockIdx.x);
+}
+
+// The face launches of a batch of 3D grids in one launch: grid i owns the
+// blocks [block0, block0 + fg.total()) and runs its own face launch there
+// (face conditions of p[n+1], receiver samples, the next step's sources
+// into p[n]).
+struct FaceBatchDesc {
+  float* lv[2];  // the two levels (node (0, 0, 0)); p[n+1] of step n is lv[(n + 1) & 1]
+  FaceInfo f;
+  PointSet rec;
+  float* seis;  // [n_steps][n_rec] receiver samples
+  FaceGrid fg;
+  const int64_t* tap_off;  // source tap table and pre-injection coefficients (PreInject)
+  const float* tap_pre;
+  const float* sig;
+  const unsigned char* live;  // per step: some source sample is non-zero
+  int taps, n_src, sig_stride;
+  int block0;
+};
+
+template <int R>
+__global__ void face_batch_kernel(const FaceBatchDesc* __restrict__ d, int n, int step, int n_steps) {
+  griddep_launch_dependents();
+  griddep_wait();  // the batch's stencil launch
+  const int b = blockIdx.x;
+  int gi = 0;
+  for (int i = 1; i < n && d[i].block0 <= b; ++i) gi = i;
+  const FaceBatchDesc& D = d[gi];
+  PreInject pi{};
+  if (step + 1 < n_steps && D.n_src > 0 && D.live[step + 1])
+    pi = PreInject{D.lv[step & 1], D.tap_off, D.tap_pre, D.sig, D.taps, D.n_src, D.sig_stride, step + 1};
+  face_block<R>(D.lv[(step + 1) & 1], D.f, D.rec, D.seis, step, D.fg, pi, b - D.block0);
+}
+
 // Launch with programmatic stream serialization: the kernel may start before
 // the previous kernel of the stream ends (it calls griddep_wait() first).
 template <typename... P, typename... A>
@@ -525,11 +563,13 @@ inline void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
 // kernel and in the gradient's passes) and, if rec.count > 0, the
 // receiver samples of this step, and, if pi.count > 0, the pre-injection of
 // the next step's sources, in one launch of 256-thread blocks.
-inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
-                                   cudaStream_t st, const PreInject& pi = PreInject{}) {
+// Blocks of each part of a face launch: pre_threads threads of
+// pre-injection, rec_count receivers, the face lines of the axes with a
+// condition.
+inline FaceGrid face_grid(const FaceInfo& f, int R, int rec_count, int pre_threads) {
   FaceGrid fg;
-  fg.pre = (pi.count * pi.taps + 255) / 256;
-  fg.rec = (rec.count + 7) / 8;
+  fg.pre = (pre_threads + 255) / 256;
+  fg.rec = (rec_count + 7) / 8;
   // an axis whose two faces have no condition has nothing to write (its
   // ghosts stay zero): no blocks for it (the y axis of a 2D grid)
   const bool zf = f.bc[0] != kBcNone || f.bc[1] != kBcNone, yf = f.bc[2] != kBcNone || f.bc[3] != kBcNone,
@@ -540,6 +580,12 @@ inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const Poi
   fg.z = zf ? 2 * f.ny * fg.bxz : 0;
   fg.y = yf ? 2 * f.nz * fg.bxz : 0;
   fg.x = xf ? 2 * f.nz * fg.bxx : 0;
+  return fg;
+}
+
+inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
+                                   cudaStream_t st, const PreInject& pi = PreInject{}) {
+  const FaceGrid fg = face_grid(f, R, rec.count, pi.count * pi.taps);
   const unsigned grid = unsigned(fg.total());
   switch (R) {
     case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;

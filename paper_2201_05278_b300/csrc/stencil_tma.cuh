@@ -48,12 +48,53 @@
 
 namespace sw {
 
+// One grid of a batch of 3D grids advanced by one launch (MULTI): its
+// tensor maps for the step's level parity, its stencil arguments and the
+// first work item of its tiles in the batch's list.  Kept in global memory
+// (the tensor maps are written there from the host before any launch).
+struct __align__(128) TmaGridDesc {
+  CUtensorMap c, f, w, o, k;  // centre box with halo, front plane, warm-up box, p[n-1], kappa
+  StencilArgs a;
+  int unit0;    // first work item
+  int tiles_x;  // tiles along x
+  int nz;       // planes per tile column
+};
+
 struct TmaWork {
   int tiles_x;  // tiles along x
   int nz;       // planes per tile column
   int total;    // tiles * nz work items (fits 32 bits: checked on the host)
   int starve;   // failure-path test: issue no copies, so every wait runs into its bound
+  const TmaGridDesc* grids = nullptr;  // MULTI: the batch's grids, unit0 ascending
+  int n_grids = 0;
 };
+
+// Where work item u lies: its grid (MULTI), tile and plane.
+struct TmaLoc {
+  int gi, t, zb, nzg, tiles_x;
+};
+
+template <bool MULTI>
+__device__ __forceinline__ TmaLoc tma_locate(const TmaGridDesc* grids, int n_grids, int nz, int tiles_x, int u) {
+  TmaLoc l;
+  if constexpr (MULTI) {
+    int gi = 0;
+    for (int i = 1; i < n_grids && grids[i].unit0 <= u; ++i) gi = i;
+    const int ul = u - grids[gi].unit0;
+    l.gi = gi;
+    l.nzg = grids[gi].nz;
+    l.tiles_x = grids[gi].tiles_x;
+    l.t = ul / l.nzg;
+    l.zb = ul - l.t * l.nzg;
+  } else {
+    l.gi = 0;
+    l.nzg = nz;
+    l.tiles_x = tiles_x;
+    l.t = u / nz;
+    l.zb = u % nz;
+  }
+  return l;
+}
 
 // Interior planes of p[n] in one warm-up box (its tensor map's box depth).
 constexpr int kTmaWarmPlanes = 4;
@@ -108,14 +149,16 @@ struct RingShared {
 // the same pipeline.  The bundle's p[n-1] box carries psi and its kappa box
 // the accumulator gk, and the store writes gk + psi (L p) to a.pout (= gk):
 // with p the forward state, this accumulates kappa dJ/dkappa.
-template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD, bool IMG = false>
+template <int R, int TY, int PPT, int NB, int MINB, bool ISO, bool VD, bool IMG = false, bool MULTI = false>
 __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     stencil_tma_kernel(const __grid_constant__ CUtensorMap map_c, const __grid_constant__ CUtensorMap map_f,
                        const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_o, const __grid_constant__ CUtensorMap map_k,
                        const __grid_constant__ CUtensorMap map_gz, const __grid_constant__ CUtensorMap map_gy,
-                       const __grid_constant__ CUtensorMap map_gx, const StencilArgs a, const TmaWork wk,
+                       const __grid_constant__ CUtensorMap map_gx, const __grid_constant__ StencilArgs a,
+                       const TmaWork wk,
                        int* err_flag, unsigned long long limit_ns) {
   static_assert(!(IMG && VD), "the imaging pass is constant density");
+  static_assert(!(MULTI && (IMG || VD)), "batches of 3D grids are constant density");
   using C = TmaConfig<R, TY, PPT, NB, VD>;
   constexpr int TX = C::TX, QL = C::QL, H = C::H, PW = C::PW, NCW = C::NCW, W = C::W, WP = C::WP;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -139,7 +182,12 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     return;
   }
   const uint32_t full0 = smem_addr(bars);
-  const int nz = wk.nz;
+  auto locate = [&](int u) { return tma_locate<MULTI>(wk.grids, wk.n_grids, wk.nz, wk.tiles_x, u); };
+  // planes of the segment that starts at u (the rest of its tile column within the range)
+  auto seg_len = [&](int u) {
+    const TmaLoc l = locate(u);
+    return min(u1 - u, l.nzg - l.zb);
+  };
 
   // Bundle `jn` counted from the start of the segment (u, len) into `slot`
   // (one lane); false when it lies past the end of the range.  `mark` > 0
@@ -149,26 +197,35 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       jn -= len + W;
       u += len;
       if (u >= u1) return false;
-      len = segment_len(u, u1, nz);
+      len = seg_len(u);
     }
     if (mark > 0) atomicMax(&ring->issued, mark);
-    const int t = u / nz;
-    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
+    const TmaLoc l = locate(u);
+    const int x0 = (l.t % l.tiles_x) * TX, y0 = (l.t / l.tiles_x) * TY;
+    const CUtensorMap *mc = &map_c, *mf = &map_f, *mw = &map_w, *mo = &map_o, *mk = &map_k;
+    if constexpr (MULTI) {
+      const TmaGridDesc* D = wk.grids + l.gi;
+      mc = &D->c;
+      mf = &D->f;
+      mw = &D->w;
+      mo = &D->o;
+      mk = &D->k;
+    }
     float* sb = slots + slot * C::SLOT_FLOATS;
     const uint32_t bar = full0 + 8u * slot;
-    if (jn < W) {  // WP front planes from padded z (u % nz) + jn * WP, at the slot's start
+    if (jn < W) {  // WP front planes from padded z zb + jn * WP, at the slot's start
       mbar_arrive_expect_tx(bar, uint32_t(WP) * C::I_BYTES);
-      tma_load_3d(smem_addr(sb), &map_w, x0 + kXOff, y0 + R, u % nz + jn * WP, bar);
+      tma_load_3d(smem_addr(sb), mw, x0 + kXOff, y0 + R, l.zb + jn * WP, bar);
     } else {
-      const int zf = u % nz + jn - W + 2 * R;  // padded z of the front plane
+      const int zf = l.zb + jn - W + 2 * R;  // padded z of the front plane
       mbar_arrive_expect_tx(bar, C::C_BYTES + uint32_t(C::NI) * C::I_BYTES);
-      tma_load_3d(smem_addr(sb), &map_c, x0 + kXOff - C::XH, y0, zf - R, bar);
-      tma_load_3d(smem_addr(sb + C::C_FLOATS), &map_f, x0 + kXOff, y0 + R, zf, bar);
+      tma_load_3d(smem_addr(sb), mc, x0 + kXOff - C::XH, y0, zf - R, bar);
+      tma_load_3d(smem_addr(sb + C::C_FLOATS), mf, x0 + kXOff, y0 + R, zf, bar);
       // p[n-1] and kappa are read once: they leave L2 first, so that p[n]
       // planes stay there for the halo rows neighbouring tiles read later
       const uint64_t once = make_policy_evict_first();
-      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), &map_o, x0 + kXOff, y0 + R, zf - R, bar, once);
-      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), &map_k, x0 + kXOff, y0 + R, zf - R, bar, once);
+      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + C::I_FLOATS), mo, x0 + kXOff, y0 + R, zf - R, bar, once);
+      tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 2 * C::I_FLOATS), mk, x0 + kXOff, y0 + R, zf - R, bar, once);
       if constexpr (VD) {
         tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 3 * C::I_FLOATS), &map_gz, x0 + kXOff, y0 + R, zf - R, bar, once);
         tma_load_3d_hint(smem_addr(sb + C::C_FLOATS + 4 * C::I_FLOATS), &map_gy, x0 + kXOff, y0 + R, zf - R, bar, once);
@@ -185,17 +242,19 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       cnt[i] = 0;
     }
     fence_barrier_init();
-    prefetch_tensormap(&map_c);
-    prefetch_tensormap(&map_f);
-    prefetch_tensormap(&map_w);
-    prefetch_tensormap(&map_o);
-    prefetch_tensormap(&map_k);
+    if constexpr (!MULTI) {
+      prefetch_tensormap(&map_c);
+      prefetch_tensormap(&map_f);
+      prefetch_tensormap(&map_w);
+      prefetch_tensormap(&map_o);
+      prefetch_tensormap(&map_k);
+    }
     if constexpr (VD) {
       prefetch_tensormap(&map_gz);
       prefetch_tensormap(&map_gy);
       prefetch_tensormap(&map_gx);
     }
-    const int len0 = segment_len(u0, u1, nz);
+    const int len0 = seg_len(u0);
     int n = 0;
     while (!wk.starve && n < NB && issue(n, u0, len0, n, 0)) ++n;
     ring->issued = n;
@@ -233,25 +292,36 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
   int s = 0;  // slot of bundle k
   uint32_t ph = 0;
   for (int u = u0; u < u1;) {
-    const int len = segment_len(u, u1, nz);
-    const int t = u / nz;
-    const int zb = u % nz;
-    const int x0 = (t % wk.tiles_x) * TX, y0 = (t / wk.tiles_x) * TY;
+    const TmaLoc loc = locate(u);
+    const int len = min(u1 - u, loc.nzg - loc.zb);
+    const int t = loc.t;
+    const int zb = loc.zb;
+    const int x0 = (t % loc.tiles_x) * TX, y0 = (t / loc.tiles_x) * TY;
+    // the segment's grid: the kernel's own, or (MULTI) one of the batch's
+    const StencilArgs& A = MULTI ? wk.grids[loc.gi].a : a;
+    if constexpr (MULTI) {
+#pragma unroll
+      for (int j = 1; j <= R; ++j) {
+        cx2[j] = make_float2(A.cx[j], A.cx[j]);
+        cy2[j] = ISO ? cx2[j] : make_float2(A.cy[j], A.cy[j]);
+        cz2[j] = ISO ? cx2[j] : make_float2(A.cz[j], A.cz[j]);
+      }
+    }
     const int x = x0 + 2 * lane;
     // per-segment invariants (warp-uniform unless noted)
-    const bool va_ok = x < a.nx, vb_ok = x + 1 < a.nx;  // per lane
+    const bool va_ok = x < A.nx, vb_ok = x + 1 < A.nx;  // per lane
     // some lane lies past the last column or some row past the last row
-    const bool ragged = __any_sync(0xffffffffu, !vb_ok) || y0 + r0 + PPT > a.ny;
+    const bool ragged = __any_sync(0xffffffffu, !vb_ok) || y0 + r0 + PPT > A.ny;
     // nodes past the last column or row (ragged tiles; never stored) take
     // distance 0, so every damping-table index stays inside the table
-    const int dxa = va_ok ? layer_distance(x, a.nx, a.nbl[4], a.nbl[5]) : 0;
-    const int dxb = vb_ok ? layer_distance(x + 1, a.nx, a.nbl[4], a.nbl[5]) : 0;
+    const int dxa = va_ok ? layer_distance(x, A.nx, A.nbl[4], A.nbl[5]) : 0;
+    const int dxb = vb_ok ? layer_distance(x + 1, A.nx, A.nbl[4], A.nbl[5]) : 0;
     int d2xy_a[PPT], d2xy_b[PPT];
     bool xy_free = true;  // no node of the warp's rows is in the absorbing layer in x, y
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
       const int y = y0 + r0 + i;
-      const int dyl = y < a.ny ? layer_distance(y, a.ny, a.nbl[2], a.nbl[3]) : 0;
+      const int dyl = y < A.ny ? layer_distance(y, A.ny, A.nbl[2], A.nbl[3]) : 0;
       d2xy_a[i] = dyl * dyl + dxa * dxa;
       d2xy_b[i] = dyl * dyl + dxb * dxb;
       xy_free = xy_free && (d2xy_a[i] | d2xy_b[i]) == 0;
@@ -265,12 +335,12 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       ca0[i] = make_float2(1.f, 1.f);
       e0[i] = make_float2(0.f, 0.f);
       if (!xy_free) {
-        const float2 da = __ldg(&a.damp[d2xy_a[i]]), db = __ldg(&a.damp[d2xy_b[i]]);
+        const float2 da = __ldg(&A.damp[d2xy_a[i]]), db = __ldg(&A.damp[d2xy_b[i]]);
         ca0[i] = make_float2(da.x, db.x);
         e0[i] = make_float2(da.y, db.y);
       }
     }
-    const int rowoff0 = (y0 + r0) * int(a.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
+    const int rowoff0 = (y0 + r0) * int(A.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
     const int nb = len + W;
 #pragma unroll 1
     for (int j = 0; j < nb; ++j) {
@@ -278,7 +348,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       // z layer, else fetched here, before the wait, so that their latency
       // hides behind it
       const int z = zb + j - W;
-      const int dzl = layer_distance(z, a.nz, a.nbl[0], a.nbl[1]);
+      const int dzl = layer_distance(z, A.nz, A.nbl[0], A.nbl[1]);
       const int dz2 = dzl * dzl;
       const bool zlayer = !IMG && j >= W && dz2 != 0;
       const bool damped = !IMG && (zlayer || (j >= W && !xy_free));
@@ -286,8 +356,8 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       if (zlayer) {
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          da[i] = __ldg(&a.damp[dz2 + d2xy_a[i]]);
-          db[i] = __ldg(&a.damp[dz2 + d2xy_b[i]]);
+          da[i] = __ldg(&A.damp[dz2 + d2xy_a[i]]);
+          db[i] = __ldg(&A.damp[dz2 + d2xy_b[i]]);
         }
       }
       // the decision to go on is taken by the whole warp, so its lanes never
@@ -430,15 +500,15 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
             kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
         }
-        float* plane = a.pout + int64_t(z) * a.sz + rowoff0;
+        float* plane = A.pout + int64_t(z) * A.sz + rowoff0;
         if (!ragged) {
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) __stcs(reinterpret_cast<float2*>(plane + i * int(a.sy)), kl[i]);  // streaming
+          for (int i = 0; i < PPT; ++i) __stcs(reinterpret_cast<float2*>(plane + i * int(A.sy)), kl[i]);  // streaming
         } else {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
-            if (y0 + r0 + i >= a.ny) break;
-            float* dst = plane + i * int(a.sy);
+            if (y0 + r0 + i >= A.ny) break;
+            float* dst = plane + i * int(A.sy);
             if (vb_ok) {
               *reinterpret_cast<float2*>(dst) = kl[i];
             } else if (va_ok) {
