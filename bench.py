@@ -199,7 +199,7 @@ class OracleRunner:
         import oracle
         self.oracle = oracle
         self.threads = os.cpu_count() or 1
-        w = workloads.shot_batch()[0] if workload_name in workloads.BATCH_NAMES else workloads.make(workload_name)
+        w = workloads.batch_shots(workload_name)[0] if workload_name in workloads.BATCH_NAMES else workloads.make(workload_name)
         self.w = w
         nbl_lo = [w.nbl[2 * a] for a in range(w.ndim)]
         self.eta = oracle.eta_field(w.shape, w.nbl, w.damp_alpha, w.damp_degree)
@@ -237,6 +237,18 @@ class OracleRunner:
                                                           self.threads)
 
 
+L2_BYTES = 126e6  # B300 L2
+
+
+def _l2_note(step_bytes):
+    """How the per-time-step data compare with the L2 (the timing rule: inputs
+    larger than L2, or say so)."""
+    if step_bytes > L2_BYTES:
+        return "inputs larger than L2 (each time step streams %.0f MB)" % (step_bytes / 1e6)
+    return ("each time step touches %.0f MB, less than the 126 MB L2: the levels stay partly in L2 from one time "
+            "step to the next, as in any run of this workload (no flush)" % (step_bytes / 1e6))
+
+
 def cpu_baseline(workload_name, budget_s=12.0):
     """Times the FP64 oracle on the host cores on a bounded sample of the workload."""
     r = OracleRunner(workload_name)
@@ -247,17 +259,18 @@ def cpu_baseline(workload_name, budget_s=12.0):
 
 
 def run_batch(args, world, rank, local, dev):
-    """The shot batch: every shot of 2d_shot_batch_64 advanced by one batched
-    launch per time step (sw_batch_forward); a bench step = one forward of all
-    shots; Gpts/s counts the nodes of every shot."""
+    """A shot batch: every shot of 2d_shot_batch_64 (or of 3d_shot_batch_16)
+    advanced by one batched launch per time step (sw_batch_forward); a bench
+    step = one forward of all shots; Gpts/s counts the nodes of every shot."""
     import torch
     from paper_2201_05278_b300 import api, workloads
 
-    shots = workloads.shot_batch(n_steps=args.time_steps or None)
+    shots = workloads.batch_shots(args.workload, n_steps=args.time_steps or None)
+    ndim = shots[0].ndim
     stream = torch.cuda.current_stream(dev)
     grids, models = [], {}
     for w in shots:
-        g = api.sw_create_grid(2, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
+        g = api.sw_create_grid(ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt,
                                stream=stream)
         if id(w.velocity) not in models:
             models[id(w.velocity)] = (torch.from_numpy(w.velocity).to(dev), w.nodes)
@@ -318,7 +331,7 @@ def run_batch(args, world, rank, local, dev):
         e2e = {"value": round(job_throughput(shot_nodes * n_steps, args.e2e_steps, world, e2e_s), 3), "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(sum(h.numel() for h in seis_h) * 4)}
 
-    tile_rows, tuned_us = api.sw_batch_get_tile(b)
+    tile_rows, tuned_us = api.sw_batch_get_tile(b) if ndim == 2 else (16, [])
     b.close()
     # the same shots run one after another with the plain single-grid forward
     # (its second call, the captured graph, is the one timed)
@@ -338,7 +351,8 @@ def run_batch(args, world, rank, local, dev):
                      "ms": round(ums, 3), "how": "sw_forward per shot, one after another, same GPU"}
     peak, peak_kind = _peaks()
     avg_launch_s = stencil_ms * 1e-3 / max(stencil_launches, 1)
-    alg_bytes = 12 * shot_nodes + 4 * model_nodes
+    # 2D: shots of one model share its kappa reads; 3D: every grid reads its own
+    alg_bytes = 12 * shot_nodes + 4 * model_nodes if ndim == 2 else 16 * shot_nodes
     achieved = alg_bytes / avg_launch_s / 1e9
     for g in grids:
         g.close()
@@ -351,9 +365,10 @@ def run_batch(args, world, rank, local, dev):
                        "nodes_per_step": shot_nodes, "space_order": shots[0].order,
                        "time_steps_per_forward": n_steps, "receivers_per_shot": len(shots[0].rec_pos),
                        "parallelism": "replicas" if world > 1 else "single",
-                       "tile": "128 x %d (tuner, us per launch for 16/32/64 rows: %s)" % (
-                           tile_rows, ", ".join("%.1f" % t for t in tuned_us)),
-                       "l2": "inputs larger than L2 (each time step streams %.0f MB)" % (alg_bytes / 1e6)},
+                       "tile": ("128 x %d (tuner, us per launch for 16/32/64 rows: %s)" % (
+                           tile_rows, ", ".join("%.1f" % t for t in tuned_us))) if ndim == 2 else
+                       "64 x 16 x plane items of the pipelined kernel",
+                       "l2": _l2_note(alg_bytes)},
             "unbatched": unbatched,
             "roofline": _roofline_traffic(
                 {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -237,6 +237,46 @@ def shot_batch(n_models: int = 8, shots_per_model: int = 8, n_steps: Optional[in
     return out
 
 
+def shot_batch_3d(n_models: int = 8, shots_per_model: int = 2, n_steps: Optional[int] = None,
+                  size_scale: float = 1.0) -> List[Workload]:
+    """The shots of 3d_shot_batch_16: 3D grids too small to fill the GPU
+    alone, advanced together.  8 layered models (seeds 100..107, 3-6 flat
+    layers of 1500-4500 m/s) whose (nz, ny, nx) are drawn from U{48..96} each,
+    h = 10 m, order 8, 12-cell absorbing layer on five faces (top null
+    Neumann), 2 shots per model 2 cells deep, 8 x 8 receivers 2 cells deep,
+    15 Hz Ricker, 1000 steps."""
+    out = []
+    h = (10.0, 10.0, 10.0)
+    nb = 12
+    f = 15.0
+    for m in range(n_models):
+        rng = np.random.default_rng(100 + m)
+        shp = tuple(max(2 * nb + 12, int(round(int(rng.integers(48, 97)) * size_scale))) for _ in range(3))
+        n_layers = int(rng.integers(3, 7))
+        depths = np.sort(rng.choice(np.arange(1, shp[0]), size=n_layers - 1, replace=False))
+        speeds = 1500.0 + 3000.0 * rng.random(n_layers)
+        v1 = speeds[np.searchsorted(depths, np.arange(shp[0]), side="right")].astype(np.float32)
+        vel = np.ascontiguousarray(np.broadcast_to(v1[:, None, None], shp), dtype=np.float32)
+        c_max = float(vel.max())
+        dt = 0.4 * h[0] / c_max
+        py = (shp[1] - 2 * nb - 1) * h[1]
+        px = (shp[2] - 2 * nb - 1) * h[2]
+        ry, rx = np.meshgrid(_grid_positions(0.05 * py, 0.95 * py, 8), _grid_positions(0.05 * px, 0.95 * px, 8),
+                             indexing="ij")
+        rec = np.stack([np.full(ry.size, 2 * h[0]), ry.ravel(), rx.ravel()], 1)
+        for k in range(shots_per_model):
+            src = np.array([[2 * h[0], 0.5 * py, (k + 0.5) / shots_per_model * px]])
+            out.append(Workload("3d_shot_batch_16/model%d/shot%d" % (m, k), 3, shp, h, 8, [0, nb, nb, nb, nb, nb],
+                                ["null_neumann"] + ["null_dirichlet"] * 5, _alpha(c_max, nb, h[0]), 3, dt,
+                                n_steps or 1000, f, 1.0 / f, src, rec, 4, vel))
+    return out
+
+
+def batch_shots(name: str, n_steps: Optional[int] = None) -> List[Workload]:
+    """The shots of a batched workload by name."""
+    return shot_batch(n_steps=n_steps) if name == "2d_shot_batch_64" else shot_batch_3d(n_steps=n_steps)
+
+
 @dataclass
 class GradientCase:
     """A misfit-gradient workload: true and initial models, one source per shot."""
@@ -279,4 +319,4 @@ def fwi_gradient_256(n_steps: Optional[int] = None, shape: Optional[Tuple[int, .
 
 NAMES = ["2d_homogeneous_256", "3d_layered_256", "3d_vd_512x512x384", "2d_layered_4096"]
 GRADIENT_NAMES = ["3d_fwi_gradient_256"]
-BATCH_NAMES = ["2d_shot_batch_64"]
+BATCH_NAMES = ["2d_shot_batch_64", "3d_shot_batch_16"]
