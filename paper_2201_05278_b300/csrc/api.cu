@@ -2624,18 +2624,20 @@ void launch_stencil_tma_batch(const sw_batch* b, int parity, cudaStream_t st) {
 
 void launch_face_batch(const sw_batch* b, int step, int n_steps, cudaStream_t st) {
   const int n = int(b->grids.size());
-  const dim3 grid(unsigned(b->face_blocks)), block(256);
+  // a persistent grid walks every grid's face blocks (many small faces: no block launched per 256 positions)
+  const int total = b->face_blocks;
+  const dim3 grid(unsigned(std::min(total, b->grids[0]->sm_count * 8))), block(256);
   switch (b->R) {
-    case 1: launch_dependent(face_batch_kernel<1>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 2: launch_dependent(face_batch_kernel<2>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 3: launch_dependent(face_batch_kernel<3>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 4: launch_dependent(face_batch_kernel<4>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 5: launch_dependent(face_batch_kernel<5>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 6: launch_dependent(face_batch_kernel<6>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 7: launch_dependent(face_batch_kernel<7>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 8: launch_dependent(face_batch_kernel<8>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 9: launch_dependent(face_batch_kernel<9>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
-    case 10: launch_dependent(face_batch_kernel<10>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, step, n_steps); break;
+    case 1: launch_dependent(face_batch_kernel<1>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 2: launch_dependent(face_batch_kernel<2>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 3: launch_dependent(face_batch_kernel<3>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 4: launch_dependent(face_batch_kernel<4>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 5: launch_dependent(face_batch_kernel<5>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 6: launch_dependent(face_batch_kernel<6>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 7: launch_dependent(face_batch_kernel<7>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 8: launch_dependent(face_batch_kernel<8>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 9: launch_dependent(face_batch_kernel<9>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
+    case 10: launch_dependent(face_batch_kernel<10>, grid, block, 0, st, (const FaceBatchDesc*)b->d_fdesc, n, total, step, n_steps); break;
     default: break;
   }
 }
@@ -2679,7 +2681,7 @@ sw_status create_batch_3d(sw_batch** out, sw_grid* const* grids, int n) {
     }
     const int64_t tiles = ((g->n[2] + 63) / 64) * ((g->n[1] + 15) / 16);
     units += tiles * g->n[0];
-    const FaceGrid fg = face_grid(g->faces(), g->R, g->n_rec, g->n_src * g->lz * g->ly * g->lx);
+    const FaceGrid fg = face_grid(g->faces(), g->R, g->n_rec, g->n_src * g->lz * g->ly * g->lx, true);
     face_blocks += fg.total();
   }
   if (units >= (int64_t(1) << 31) || face_blocks >= (int64_t(1) << 31))
@@ -2749,7 +2751,7 @@ sw_status create_batch_3d(sw_batch** out, sw_grid* const* grids, int n) {
     F.f = g->faces();
     F.rec = point_set(g, false);
     F.seis = nullptr;
-    F.fg = face_grid(F.f, g->R, g->n_rec, g->n_src * taps);
+    F.fg = face_grid(F.f, g->R, g->n_rec, g->n_src * taps, true);
     F.tap_off = g->tap_off;
     F.tap_pre = g->tap_pre;
     F.sig = g->wavelet;

@@ -441,6 +441,7 @@ struct FaceGrid {
   int rec, z, y, x, pre;  // blocks per part
   int bxz;                // blocks per face line along x (z and y faces)
   int bxx;                // blocks per z plane of an x face
+  int flat = 0;           // z, y and x faces numbered across lines (small faces: no idle lanes per line)
   int total() const { return rec + z + y + x + pre; }
 };
 
@@ -481,10 +482,18 @@ __device__ __forceinline__ void face_block(float* p, const FaceInfo& f, const Po
   if (b < fg.z + fg.y) {  // block: 256 consecutive x of one (side, y) or (side, z) line
     const bool zf = b < fg.z;
     if (!zf) b -= fg.z;
-    const int line = b / fg.bxz;
-    const int ib = (b - line * fg.bxz) * 256 + threadIdx.x;
-    if (ib >= f.nx) return;
     const int na = zf ? f.ny : f.nz;
+    int line, ib;
+    if (fg.flat) {  // 256 consecutive (line, x) positions
+      const int t = b * 256 + int(threadIdx.x);
+      if (t >= 2 * na * f.nx) return;
+      line = t / f.nx;
+      ib = t - line * f.nx;
+    } else {
+      line = b / fg.bxz;
+      ib = (b - line * fg.bxz) * 256 + threadIdx.x;
+      if (ib >= f.nx) return;
+    }
     const int side = line >= na ? 1 : 0;
     if (zf)
       face_line<0, R>(p, f, side, line - side * na, ib);
@@ -495,9 +504,17 @@ __device__ __forceinline__ void face_block(float* p, const FaceInfo& f, const Po
   b -= fg.z + fg.y;
   // block: 256 / kFaceLanes consecutive rows of one (side, z) plane of an x face
   constexpr int LPR = face_lanes<R>();
-  const int plane = b / fg.bxx;
-  const int y = (b - plane * fg.bxx) * (256 / LPR) + int(threadIdx.x) / LPR;
-  if (y >= f.ny) return;
+  int plane, y;
+  if (fg.flat) {  // 256 / LPR consecutive (side, z, y) rows
+    const int r = b * (256 / LPR) + int(threadIdx.x) / LPR;
+    if (r >= 2 * f.nz * f.ny) return;
+    plane = r / f.ny;
+    y = r - plane * f.ny;
+  } else {
+    plane = b / fg.bxx;
+    y = (b - plane * fg.bxx) * (256 / LPR) + int(threadIdx.x) / LPR;
+    if (y >= f.ny) return;
+  }
   const int side = plane >= f.nz ? 1 : 0;
   face_x<R>(p, f, side, plane - side * f.nz, y, int(threadIdx.x) % LPR + 1);
 }
@@ -529,17 +546,19 @@ struct FaceBatchDesc {
 };
 
 template <int R>
-__global__ void face_batch_kernel(const FaceBatchDesc* __restrict__ d, int n, int step, int n_steps) {
+__global__ void face_batch_kernel(const FaceBatchDesc* __restrict__ d, int n, int total, int step, int n_steps) {
   griddep_launch_dependents();
   griddep_wait();  // the batch's stencil launch
-  const int b = blockIdx.x;
-  int gi = 0;
-  for (int i = 1; i < n && d[i].block0 <= b; ++i) gi = i;
-  const FaceBatchDesc& D = d[gi];
-  PreInject pi{};
-  if (step + 1 < n_steps && D.n_src > 0 && D.live[step + 1])
-    pi = PreInject{D.lv[step & 1], D.tap_off, D.tap_pre, D.sig, D.taps, D.n_src, D.sig_stride, step + 1};
-  face_block<R>(D.lv[(step + 1) & 1], D.f, D.rec, D.seis, step, D.fg, pi, b - D.block0);
+  // the blocks of all grids' face launches, walked by a persistent grid
+  for (int b = blockIdx.x; b < total; b += gridDim.x) {
+    int gi = 0;
+    for (int i = 1; i < n && d[i].block0 <= b; ++i) gi = i;
+    const FaceBatchDesc& D = d[gi];
+    PreInject pi{};
+    if (step + 1 < n_steps && D.n_src > 0 && D.live[step + 1])
+      pi = PreInject{D.lv[step & 1], D.tap_off, D.tap_pre, D.sig, D.taps, D.n_src, D.sig_stride, step + 1};
+    face_block<R>(D.lv[(step + 1) & 1], D.f, D.rec, D.seis, step, D.fg, pi, b - D.block0);
+  }
 }
 
 // Launch with programmatic stream serialization: the kernel may start before
@@ -566,7 +585,7 @@ inline void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
 // Blocks of each part of a face launch: pre_threads threads of
 // pre-injection, rec_count receivers, the face lines of the axes with a
 // condition.
-inline FaceGrid face_grid(const FaceInfo& f, int R, int rec_count, int pre_threads) {
+inline FaceGrid face_grid(const FaceInfo& f, int R, int rec_count, int pre_threads, bool flat = false) {
   FaceGrid fg;
   fg.pre = (pre_threads + 255) / 256;
   fg.rec = (rec_count + 7) / 8;
@@ -580,6 +599,12 @@ inline FaceGrid face_grid(const FaceInfo& f, int R, int rec_count, int pre_threa
   fg.z = zf ? 2 * f.ny * fg.bxz : 0;
   fg.y = yf ? 2 * f.nz * fg.bxz : 0;
   fg.x = xf ? 2 * f.nz * fg.bxx : 0;
+  if (flat) {
+    fg.flat = 1;
+    fg.z = zf ? int((2 * int64_t(f.ny) * f.nx + 255) / 256) : 0;
+    fg.y = yf ? int((2 * int64_t(f.nz) * f.nx + 255) / 256) : 0;
+    fg.x = xf ? int((2 * int64_t(f.nz) * f.ny + 256 / lpr - 1) / (256 / lpr)) : 0;
+  }
   return fg;
 }
 
