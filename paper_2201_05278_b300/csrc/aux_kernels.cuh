@@ -610,7 +610,10 @@ inline FaceGrid face_grid(const FaceInfo& f, int R, int rec_count, int pre_threa
 
 inline void launch_face_conditions(float* p, const FaceInfo& f, int R, const PointSet& rec, float* out, int step,
                                    cudaStream_t st, const PreInject& pi = PreInject{}) {
-  const FaceGrid fg = face_grid(f, R, rec.count, pi.count * pi.taps);
+  // faces narrower than a block (a 2D grid's x faces are one row per plane)
+  // are numbered across lines, so that no block runs with idle lanes
+  const bool narrow = f.nx < 256 || f.ny < 256 / (R <= 8 ? 8 : 16);
+  const FaceGrid fg = face_grid(f, R, rec.count, pi.count * pi.taps, narrow);
   const unsigned grid = unsigned(fg.total());
   switch (R) {
     case 1: launch_dependent(face_conditions_kernel<1>, dim3(grid), dim3(256), 0, st, p, f, rec, out, step, fg, pi); break;
