@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
     }
     const int rowoff0 = (y0 + r0) * int(A.sy) + x;  // in-plane offsets fit 32 bits (checked on the host)
     const int nb = len + W;
+    bool zl_held = false;  // ca0/e0 hold a z-layer plane's coefficients
 #pragma unroll 1
     for (int j = 0; j < nb; ++j) {
       // damping coefficients of this plane's nodes: per segment outside the
@@ -352,13 +353,30 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
       const int dz2 = dzl * dzl;
       const bool zlayer = !IMG && j >= W && dz2 != 0;
       const bool damped = !IMG && (zlayer || (j >= W && !xy_free));
-      float2 da[PPT], db[PPT];
+      // one set of coefficient registers: a plane of the z layer overwrites
+      // ca0/e0 with its nodes' (1/(1+e), e), the first plane after the layer
+      // puts the x/y values back (a separate set held for the z layer's
+      // planes cost 3% of the launch)
       if (zlayer) {
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          da[i] = __ldg(&A.damp[dz2 + d2xy_a[i]]);
-          db[i] = __ldg(&A.damp[dz2 + d2xy_b[i]]);
+          const float2 da = __ldg(&A.damp[dz2 + d2xy_a[i]]), db = __ldg(&A.damp[dz2 + d2xy_b[i]]);
+          ca0[i] = make_float2(da.x, db.x);
+          e0[i] = make_float2(da.y, db.y);
         }
+        zl_held = true;
+      } else if (zl_held && j >= W) {
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          ca0[i] = make_float2(1.f, 1.f);
+          e0[i] = make_float2(0.f, 0.f);
+          if (!xy_free) {
+            const float2 da = __ldg(&A.damp[d2xy_a[i]]), db = __ldg(&A.damp[d2xy_b[i]]);
+            ca0[i] = make_float2(da.x, db.x);
+            e0[i] = make_float2(da.y, db.y);
+          }
+        }
+        zl_held = false;
       }
       // the decision to go on is taken by the whole warp, so its lanes never
       // split.  The abort flag is not read here (a shared-memory load on the
@@ -485,19 +503,12 @@ __global__ void __launch_bounds__(TmaConfig<R, TY, PPT, NB, VD>::NT, MINB)
             const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
             kl[i] = f2_add(pc, f2_fma(kp, kl[i], f2_sub(pc, po)));
           }
-        } else if (!zlayer) {
+        } else {
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
             const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
             // p[n+1] = a (p + (kappa L + ((p - p[n-1]) + e p[n-1])))
             kl[i] = f2_mul(ca0[i], f2_add(pc, f2_fma(kp, kl[i], f2_fma(e0[i], po, f2_sub(pc, po)))));
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < PPT; ++i) {
-            const float2 pc = qz[i][R], po = O[i * (TX / 2)], kp = K[i * (TX / 2)];
-            const float2 ca = make_float2(da[i].x, db[i].x), e = make_float2(da[i].y, db[i].y);
-            kl[i] = f2_mul(ca, f2_add(pc, f2_fma(kp, kl[i], f2_fma(e, po, f2_sub(pc, po)))));
           }
         }
         float* plane = A.pout + int64_t(z) * A.sz + rowoff0;
