@@ -140,9 +140,14 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  *   misfit           host, one double
  *   grad_vel         [nz][ny][nx] FP32 (2D: [nz][nx]), device or host
  *   grad_rho         same layout, or NULL; needs a density model
- *   checkpoint_every forward states kept every K time steps (0: K about
- *                    sqrt(2 n_steps)); each segment is recomputed during the
- *                    adjoint sweep.
+ *   checkpoint_every forward states kept every K time steps; each segment
+ *                    is recomputed during the adjoint sweep.  K >= n_steps
+ *                    keeps every level: the forward run writes p[0] ..
+ *                    p[n_steps - 1] into n_steps + 1 padded FP32 fields,
+ *                    the sweep recomputes nothing and checkpoint_format
+ *                    does not apply (nothing is rounded).  0: every level
+ *                    kept when the call's fields fit in 80% of the free
+ *                    device memory, else K about sqrt(2 n_steps).
  *   checkpoint_format SW_CKPT_FP32: each checkpoint is a copy of the two
  *                    padded FP32 levels.  16-bit formats keep the nodes of
  *                    p[k0] and of the difference p[k0] - p[k0-1] (small
@@ -157,9 +162,10 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
  *                    step is 1/32767 of the row's largest magnitude instead
  *                    of 8 or 11 bits of every value).  Device memory for the call,
  *                    freed before it returns: (2 n_steps / K + K + 4) padded
- *                    FP32 wavefields (K + 4 with 16-bit checkpoints, plus
- *                    2 n_steps / K node arrays of 2 bytes per node; 3 or 6
- *                    more with density) and three [n_steps][n_rec] arrays.
+ *                    FP32 wavefields (K + 4 with 16-bit checkpoints or when
+ *                    every level is kept, plus 2 n_steps / K node arrays of
+ *                    2 bytes per node with 16-bit checkpoints; 3 or 6 more
+ *                    with density) and three [n_steps][n_rec] arrays.
  * Errors: SW_ESTATE before sw_set_model / sw_set_acquisition; SW_EINVAL for
  * grad_rho without a density model, without receivers, for n_steps < 1 or
  * beyond the wavelet, or with 2R+1 nodes or fewer along an axis; SW_ENOMEM

@@ -1501,23 +1501,34 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   const bool revolve = budget > 0;
   if (revolve && checkpoint_format != SW_CKPT_FP32)
     return fail(SW_EINVAL, "the binomial schedule keeps FP32 states");
-  int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, int(std::lround(std::sqrt(2.0 * N))));
-  K = revolve ? 1 : std::min(K, N);
-  const int nseg = revolve ? budget : (N + K - 1) / K;
   const FaceInfo f = g->faces();
   const size_t fbytes = size_t(g->lay.total) * sizeof(float);
-  const bool tma = use_tma(g);
-  cudaStream_t st = g->stream;
-
-  // device memory of this call: checkpoint pairs (padded FP32 fields, or
-  // 16-bit node arrays with their scales), segment states, psi, dJ/dkappa
-  const bool packed = checkpoint_format != SW_CKPT_FP32;
   const bool vd = g->has_density;
-  const int nck = packed ? 0 : 2 * nseg;
   // with density: dJ/dG_a accumulators, and G_a = D_a ln rho unless the
   // pipelined kernel's copies exist
   const bool own_g = vd && !g->glr[0];
   const int nvd = vd ? 3 + (own_g ? 3 : 0) : 0;
+  int K = checkpoint_every;
+  if (K == 0) {  // every forward level kept when they fit in 80% of the free device memory, else K ~ sqrt(2N)
+    size_t free_b = 0, total_b = 0;
+    SW_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const double need = double(N + 1 + 3 + nvd) * double(fbytes);
+    K = need <= 0.8 * double(free_b) ? N : std::max(1, int(std::lround(std::sqrt(2.0 * N))));
+  }
+  K = revolve ? 1 : std::min(K, N);
+  const int nseg = revolve ? budget : (N + K - 1) / K;
+  // one segment of every step: the forward pass itself writes p[0 .. N-1]
+  // into the segment buffers, so the adjoint sweep recomputes nothing and
+  // nothing is rounded to a checkpoint format
+  const bool keep_all = !revolve && nseg == 1;
+  const bool tma = use_tma(g);
+  cudaStream_t st = g->stream;
+
+  // device memory of this call: checkpoint pairs (padded FP32 fields, or
+  // 16-bit node arrays with their scales), segment states (one block), psi,
+  // dJ/dkappa
+  const bool packed = checkpoint_format != SW_CKPT_FP32 && !keep_all;
+  const int nck = packed || keep_all ? 0 : 2 * nseg;
   const int nfields = nck + (K + 1) + 2 + 1 + nvd;
   const size_t pbytes = size_t(g->nodes()) * 2;  // one packed checkpoint
   void* packs = nullptr;
@@ -1529,12 +1540,15 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   float *syn = nullptr, *obs = nullptr, *res = nullptr;
   double* macc = nullptr;
   const size_t sbytes = size_t(N) * g->n_rec * sizeof(float);
+  const size_t seg_stride = (fbytes + 255) / 256 * 256;  // segment states: one allocation of K + 1 fields
+  float* seg_block = nullptr;
   auto release = [&]() {
     cudaStreamSynchronize(st);
-    for (float*& p : F) {
-      dev_free(g, p, fbytes);
-      p = nullptr;
+    for (size_t i = 0; i < F.size(); ++i) {
+      if (i < size_t(nck) || i > size_t(nck + K)) dev_free(g, F[i], fbytes);
+      F[i] = nullptr;
     }
+    dev_free(g, seg_block, seg_stride * size_t(K + 1));
     dev_free(g, syn, sbytes);
     dev_free(g, obs, sbytes);
     dev_free(g, res, sbytes);
@@ -1547,9 +1561,15 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     std::function<void()> fn;
     ~Guard() { fn(); }
   } guard{release};
-  for (float*& p : F) {
-    SW_TRY(dev_alloc(g, (void**)&p, fbytes));
-    SW_CUDA(cudaMemsetAsync(p, 0, fbytes, st));
+  SW_TRY(dev_alloc(g, (void**)&seg_block, seg_stride * size_t(K + 1)));
+  SW_CUDA(cudaMemsetAsync(seg_block, 0, seg_stride * size_t(K + 1), st));
+  for (size_t i = 0; i < F.size(); ++i) {
+    if (i >= size_t(nck) && i <= size_t(nck + K)) {
+      F[i] = reinterpret_cast<float*>(reinterpret_cast<char*>(seg_block) + seg_stride * (i - size_t(nck)));
+      continue;
+    }
+    SW_TRY(dev_alloc(g, (void**)&F[i], fbytes));
+    SW_CUDA(cudaMemsetAsync(F[i], 0, fbytes, st));
   }
   SW_TRY(dev_alloc(g, (void**)&syn, sbytes));
   SW_TRY(dev_alloc(g, (void**)&obs, sbytes));
@@ -1677,10 +1697,26 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
     if (packed) SW_CUDA(cudaMemsetAsync(scales, 0, sizeof(unsigned) * 2 * nseg, st));
   }
   pending_src = -1;
+  if (keep_all) {
+    // forward into the segment buffers: p[n] in B(n + 1), p[N] (for the
+    // receivers only) in B(0), which held p[-1]
+    SW_CUDA(cudaMemsetAsync(B(0), 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(B(1), 0, fbytes, st));
+    for (int n = 0; n < N; ++n) {
+      float* po = n + 2 <= K ? B(n + 2) : B(0);
+      const StepMaps m{&halo[idx(B(n + 1))], &inner[idx(B(n + 1))], &inner[idx(B(n))], &warm[idx(B(n + 1))]};
+      SW_TRY(step(B(n + 1), B(n), po, tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, rec, syn));
+    }
+    // the grid's levels hold p[N - 1] and p[N], as after sw_forward
+    SW_CUDA(cudaMemcpyAsync(g->u[(N - 1) & 1], B(N), fbytes, cudaMemcpyDeviceToDevice, st));
+    SW_CUDA(cudaMemcpyAsync(g->u[N & 1], B(0), fbytes, cudaMemcpyDeviceToDevice, st));
+  }
   // forward, keeping (p[k0-1], p[k0]) at every segment start
-  SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
-  SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
-  for (int n = 0; n < N; ++n) {
+  if (!keep_all) {
+    SW_CUDA(cudaMemsetAsync(g->u[0], 0, fbytes, st));
+    SW_CUDA(cudaMemsetAsync(g->u[1], 0, fbytes, st));
+  }
+  for (int n = 0; n < (keep_all ? 0 : N); ++n) {
     float* pn = g->u[n & 1];
     float* pm = g->u[(n + 1) & 1];
     if (!revolve && n % K == 0) {
@@ -1839,7 +1875,8 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   } else {  // uniform: per segment, recompute p[k0 .. k1-1], then the adjoint steps k1 .. k0+1
     for (int sgm = nseg - 1; sgm >= 0; --sgm) {
       const int k0 = sgm * K, k1 = std::min(N, k0 + K);
-      if (packed) {
+      if (keep_all) {  // B(1 .. N) hold p[0 .. N-1] from the forward pass
+      } else if (packed) {
         for (int i = 1; i >= 0; --i) {  // p[k0] first, then p[k0-1] = p[k0] - (p[k0] - p[k0-1])
           const int slot = 2 * sgm + i;
           const char* src_p = static_cast<const char*>(packs) + pbytes * slot;
@@ -1865,7 +1902,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
         SW_CUDA(cudaMemcpyAsync(B(0), ck(sgm, 0), fbytes, cudaMemcpyDeviceToDevice, st));
         SW_CUDA(cudaMemcpyAsync(B(1), ck(sgm, 1), fbytes, cudaMemcpyDeviceToDevice, st));
       }
-      for (int n = k0; n <= k1 - 2; ++n) {
+      for (int n = k0; n <= (keep_all ? k0 - 1 : k1 - 2); ++n) {
         const int j = n - k0 + 1;
         const StepMaps m{&halo[idx(B(j))], &inner[idx(B(j))], &inner[idx(B(j - 1))], &warm[idx(B(j))]};
         SW_TRY(step(B(j), B(j - 1), B(j + 1), tma ? &m : nullptr, n, g->wavelet, g->sig_stride, src, none, nullptr));

@@ -64,6 +64,27 @@ def test_gradient_does_not_depend_on_checkpoint_interval(cuda_device):
         assert rel_l2(gk, g0) <= 1e-6
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_every_level_kept_is_the_recomputed_gradient(cuda_device, ndim):
+    """K >= n_steps: the forward run writes every level into the segment
+    buffers and the sweep recomputes nothing.  The levels are the ones a
+    recomputation from exact FP32 checkpoints gives (the same kernels on the
+    same inputs), so the misfit is the same bits and the gradient differs
+    only by the order of the Neumann correction's atomic sums (run to run);
+    a 16-bit format does not apply there (nothing is stored rounded)."""
+    n = 37
+    w, wav, obs, _ = _setup(ndim, 8, n, seed=11 + ndim)
+    J_all, g_all = _gpu_gradient(w, wav, obs, n, n)
+    J_auto, g_auto = _gpu_gradient(w, wav, obs, n, 0)  # small grid: every level fits
+    J_k, g_k = _gpu_gradient(w, wav, obs, n, 6)
+    J_i16, g_i16 = _gpu_gradient(w, wav, obs, n, n + 5, api.SW_CKPT_I16)
+    assert np.abs(g_all).max() > 0
+    assert J_all == J_k == J_auto == J_i16
+    assert rel_l2(g_k, g_all) <= 1e-6
+    assert rel_l2(g_auto, g_all) <= 1e-6
+    assert rel_l2(g_i16, g_all) <= 1e-6
+
+
 def test_density_gradient_needs_a_density_model(cuda_device):
     w, wav, obs, _ = _setup(2, 8, 10, seed=2)
     g = api.sw_create_grid(w.ndim, w.shape, w.spacing, w.order, w.nbl, w.bc, w.damp_alpha, w.damp_degree, w.dt)
@@ -104,6 +125,14 @@ def test_variable_density_gradients_match_oracle(cuda_device, ndim, order, varia
         gr = np.zeros(w.shape, np.float32)  # host output
         J = api.sw_gradient(g, n, torch.from_numpy(obs).to(dev), gv, 9, grad_rho=gr)
         gv = gv.cpu().numpy()
+        # every level kept (no recomputation): the same misfit, the gradient
+        # up to the order of atomic sums
+        gv_all = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+        gr_all = np.zeros(w.shape, np.float32)
+        J_all = api.sw_gradient(g, n, torch.from_numpy(obs).to(dev), gv_all, n, grad_rho=gr_all)
+        assert J_all == J
+        assert rel_l2(gv_all.cpu().numpy(), gv) <= 1e-6
+        assert rel_l2(gr_all, gr) <= 1e-6
     finally:
         g.close()
     pb = A.make_problem(w.ndim, w.shape, w.spacing, w.order, w.velocity.astype(np.float64), w.dt,
