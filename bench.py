@@ -467,6 +467,9 @@ def gradient_error_reduced(dev):
             gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
             api.sw_gradient(g, n, obs, gv, c.checkpoint_every, fmt)
             grads[fmt] = gv.cpu().numpy().astype(np.float64)
+        gv = torch.zeros(w.shape, dtype=torch.float32, device=dev)
+        api.sw_gradient(g, n, obs, gv, n)  # every level kept
+        grads["all_levels"] = gv.cpu().numpy().astype(np.float64)
         obs = obs.cpu().numpy().astype(np.float64)
     finally:
         g.close()
@@ -475,7 +478,8 @@ def gradient_error_reduced(dev):
                         damp_alpha=w.damp_alpha, damp_degree=w.damp_degree, window_radius=w.window_radius)
     _, g_ref, _ = A.adjoint_gradient(pb, np.asarray(wav, np.float64), obs, n)
     nr = float(np.linalg.norm(g_ref))
-    return {CKPT_NAMES[f] + "_rel_l2": round(float(np.linalg.norm(grads[f] - g_ref)) / nr, 6) for f in CKPT_NAMES}
+    names = dict(CKPT_NAMES, all_levels="every_level_kept")
+    return {names[f] + "_rel_l2": round(float(np.linalg.norm(grads[f] - g_ref)) / nr, 6) for f in grads}
 
 
 def fwi_summary(world, rank, dev, steps=1, warmup=1):
