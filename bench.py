@@ -114,9 +114,11 @@ def _traffic_record(workload):
         return None
 
 
-def _roofline_traffic(roof, workload):
-    """Fills roofline["traffic"] (bytes per launch) and its read/write split."""
-    t = _traffic_record(workload)
+def _roofline_traffic(roof, workload, shape=""):
+    """Fills roofline["traffic"] (bytes per launch) and its read/write split;
+    None when the run's grid is not the workload's own (--shape): the
+    records are captures of the full-size grid."""
+    t = None if shape else _traffic_record(workload)
     roof["traffic"] = None if t is None else t["total"]
     if t is not None:
         roof["traffic_read"] = t["read"]
@@ -910,7 +912,7 @@ def main():
                             "launch, %d launches timed)" % (PROFILE_EVERY, stencil_launches)) if two_step else
                            ("stencil (CUDA events around every %dth launch, %d launches timed)" % (
                                PROFILE_EVERY, stencil_launches)),
-                 "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}, args.workload),
+                 "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}, args.workload, args.shape),
             "e2e": e2e,
             "gpu_launches": int(kernels),
             "clocks": clk,
