@@ -283,6 +283,17 @@ def test_gradient_over_shots_is_the_sum_of_the_shots(cuda_device, density, fmt):
         out = fwi.misfit_gradient(g, shots, obs_d, n, 9, fmt, density=density)
         assert out[0] == pytest.approx(J, rel=1e-9)  # atomic sums: equal up to their order
         assert rel_l2(out[1].cpu().numpy(), gv.cpu().numpy()) <= 1e-6
+        # every level kept (one segment of all n steps; the levels of each
+        # shot overwrite the previous shot's): the sums of exact levels, so
+        # those of FP32 checkpoints
+        gk = torch.zeros_like(gv)
+        grk = torch.zeros_like(gv) if density else None
+        Jk = api.sw_gradient_shots(g, shots, n, obs_d, gk, n, fmt, grad_rho=grk)
+        assert Jk == pytest.approx(J, rel=1e-9)
+        if fmt == api.SW_CKPT_FP32:
+            assert rel_l2(gk.cpu().numpy(), gv.cpu().numpy()) <= 1e-6
+            if density:
+                assert rel_l2(grk.cpu().numpy(), gr.cpu().numpy()) <= 1e-6
         # shot by shot
         J1, gv1 = 0.0, torch.zeros_like(gv)
         gr1 = torch.zeros_like(gv) if density else None
