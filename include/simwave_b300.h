@@ -15,8 +15,10 @@
  *   - Grid-shaped arrays are dense row-major FP32 [nz][ny][nx] (3D) or
  *     [nz][nx] (2D) and include the absorbing layer.
  *   - Array arguments marked "host or device" may point to host memory
- *     (pageable or pinned) or to device memory of the grid's device; the
- *     library detects which and copies as needed.  The caller keeps
+ *     (pageable or pinned) or to device memory; the library detects which.
+ *     Device memory of the current device (which must be the grid's) and
+ *     managed memory are used in place; host memory and device memory of
+ *     another GPU go through a buffer of the grid's own.  The caller keeps
  *     ownership of every buffer it passes; input buffers are only read
  *     during the call.
  *   - All device work runs on the stream given to sw_create_grid.

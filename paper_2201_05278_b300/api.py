@@ -35,6 +35,21 @@ def _check(status: int):
         raise SimwaveError(status, msg.decode() if msg else "")
 
 
+def _numel(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") and callable(a.numel) else int(np.asarray(a).size)
+
+
+def _need(name: str, a, n: int, at_least: bool = False) -> None:
+    """Raises ValueError unless the buffer `a` (if given) holds n values (at
+    least n with at_least): the C calls read and write whole buffers of the
+    sizes the grid implies and cannot see the caller's."""
+    if a is None:
+        return
+    k = _numel(a)
+    if (k < n) if at_least else (k != n):
+        raise ValueError("%s holds %d values, needs %s%d" % (name, k, ">= " if at_least else "", n))
+
+
 def _ptr(a) -> Optional[int]:
     """Raw address of a contiguous FP32 tensor / array (None passes NULL)."""
     if a is None:
@@ -58,8 +73,13 @@ class Grid:
         self.ndim = ndim
         self.shape = tuple(int(s) for s in shape)
         self.stream = stream
+        self.n_src = 0
         self.n_rec = 0
         self._keep = []
+
+    @property
+    def nodes(self) -> int:
+        return int(np.prod(self.shape))
 
     def __del__(self):
         try:
@@ -101,6 +121,8 @@ def sw_create_grid(ndim: int, shape: Sequence[int], spacing: Sequence[float], sp
 
 
 def sw_set_model(g: Grid, velocity, density=None) -> None:
+    _need("velocity", velocity, g.nodes)
+    _need("density", density, g.nodes)
     _check(_lib.load().sw_set_model(g.handle, _ptr(velocity), _ptr(density)))
 
 
@@ -118,12 +140,15 @@ def sw_set_acquisition(g: Grid, src_pos, rec_pos, wavelet, window_radius: int = 
     _check(_lib.load().sw_set_acquisition(
         g.handle, int(src.shape[0]), src.ctypes.data_as(dp), int(rec.shape[0]), rec.ctypes.data_as(dp),
         nt, _ptr(wav), int(bool(wavelet_per_source)), int(window_radius)))
+    g.n_src = int(src.shape[0])
     g.n_rec = int(rec.shape[0])
     g._keep = [wav]
 
 
 def sw_forward(g: Grid, n_steps: int, seismogram=None, final_field=None) -> None:
     """Runs n_steps steps; writes into the given output tensors/arrays (either may be None)."""
+    _need("seismogram", seismogram, max(int(n_steps), 0) * g.n_rec, at_least=True)
+    _need("final_field", final_field, g.nodes)
     _check(_lib.load().sw_forward(g.handle, int(n_steps), _ptr(seismogram), _ptr(final_field)))
 
 
@@ -135,6 +160,9 @@ def sw_gradient(g: Grid, n_steps: int, observed, grad_vel, checkpoint_every: int
     """Misfit J = 1/2 |d - observed|^2 of a forward run, dJ/dvelocity into
     grad_vel and (density models) dJ/ddensity into grad_rho (adjoint-state
     method); returns J."""
+    _need("observed", observed, max(int(n_steps), 0) * g.n_rec, at_least=True)
+    _need("grad_vel", grad_vel, g.nodes)
+    _need("grad_rho", grad_rho, g.nodes)
     j = ctypes.c_double()
     _check(_lib.load().sw_gradient(g.handle, int(n_steps), _ptr(observed), ctypes.byref(j), _ptr(grad_vel),
                                    _ptr(grad_rho), int(checkpoint_every), int(checkpoint_format)))
@@ -152,8 +180,13 @@ def sw_gradient_shots(g: Grid, shot_src_pos, n_steps: int, observed, grad_vel, c
     n_shots = int(pos.shape[0])
     if n_shots < 1 or pos.size % (n_shots * g.ndim) != 0:
         raise ValueError("shot_src_pos must be [n_shots][n_src][ndim]")
+    if pos.size != n_shots * g.n_src * g.ndim:
+        raise ValueError("shot_src_pos holds %d values, needs n_shots x n_src x ndim = %d"
+                         % (pos.size, n_shots * g.n_src * g.ndim))
     if int(np.prod(observed.shape)) != n_shots * int(n_steps) * g.n_rec:
         raise ValueError("observed must hold [n_shots][n_steps][n_rec] = %d values" % (n_shots * n_steps * g.n_rec))
+    _need("grad_vel", grad_vel, g.nodes)
+    _need("grad_rho", grad_rho, g.nodes)
     j = ctypes.c_double()
     _check(_lib.load().sw_gradient_shots(g.handle, n_shots, pos.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          int(n_steps), _ptr(observed), ctypes.byref(j), _ptr(grad_vel),

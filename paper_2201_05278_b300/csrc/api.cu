@@ -50,13 +50,23 @@ sw_status fail(sw_status s, const char* fmt, ...) {
     if (s_ != SW_OK) return s_;   \
   } while (0)
 
+// Can kernels on the current device use p directly?  Device memory of the
+// current device, or managed memory.  Host memory and device memory of
+// another GPU are not: callers stage those through a buffer of their own
+// with cudaMemcpyDefault copies (which reach either).
 bool is_device_pointer(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // Is p plain device memory (not managed, not host) of the current device?
@@ -255,7 +265,7 @@ sw_status device_input(sw_grid* g, const float* src, float** staging, const floa
   }
   const size_t bytes = size_t(g->nodes()) * sizeof(float);
   if (!*staging) SW_TRY(dev_alloc(g, (void**)staging, bytes));
-  SW_CUDA(cudaMemcpyAsync(*staging, src, bytes, cudaMemcpyHostToDevice, g->stream));
+  SW_CUDA(cudaMemcpyAsync(*staging, src, bytes, cudaMemcpyDefault, g->stream));  // host or another GPU
   *out = *staging;
   return SW_OK;
 }
@@ -1438,11 +1448,11 @@ sw_status sw_forward(sw_grid* g, int n_steps, float* seismogram, float* final_fi
     SW_CUDA(cudaGetLastError());
     ++launches;
     if (fh)
-      SW_CUDA(cudaMemcpyAsync(final_field, dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost,
+      SW_CUDA(cudaMemcpyAsync(final_field, dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDefault,
                               g->stream));
   }
   if (seis_host && seis_elems > 0)
-    SW_CUDA(cudaMemcpyAsync(seismogram, seis_dev, size_t(seis_elems) * sizeof(float), cudaMemcpyDeviceToHost,
+    SW_CUDA(cudaMemcpyAsync(seismogram, seis_dev, size_t(seis_elems) * sizeof(float), cudaMemcpyDefault,
                             g->stream));
   SW_TRY(check_device_flag(g));
   g->kernel_launches = launches;
@@ -1928,7 +1938,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
   gradient_velocity_kernel<<<grid_blocks(g->nodes(), 256), 256, 0, st>>>(g->at0(GK), a.kappa, out, f, float(g->dt));
   SW_CUDA(cudaGetLastError());
   if (host_out)
-    SW_CUDA(cudaMemcpyAsync(grad_vel, out, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+    SW_CUDA(cudaMemcpyAsync(grad_vel, out, size_t(g->nodes()) * sizeof(float), cudaMemcpyDefault, st));
   if (grad_rho) {  // dJ/drho
     float* ro = grad_rho;
     const bool host_r = !is_device_pointer(grad_rho);
@@ -1940,7 +1950,7 @@ static sw_status gradient_impl(sw_grid* g, int n_shots, const double* shot_src_p
                                                                            f, vw, g->R, g->ndim);
     SW_CUDA(cudaGetLastError());
     if (host_r)
-      SW_CUDA(cudaMemcpyAsync(grad_rho, ro, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(cudaMemcpyAsync(grad_rho, ro, size_t(g->nodes()) * sizeof(float), cudaMemcpyDefault, st));
   }
   SW_CUDA(cudaMemcpyAsync(misfit, macc, sizeof(double), cudaMemcpyDeviceToHost, st));
   SW_TRY(check_device_flag(g));
@@ -2938,7 +2948,7 @@ sw_status batch_forward_3d(sw_batch* b, int n_steps, float* const* seismograms, 
     SW_CUDA(cudaGetLastError());
     ++launches;
     if (fh)
-      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDefault, st));
   }
   SW_TRY(check_device_flag(b->grids[0]));  // synchronises
   b->kernel_launches = launches;
@@ -3289,7 +3299,7 @@ sw_status sw_batch_forward(sw_batch* b, int n_steps, float* const* seismograms, 
     SW_CUDA(cudaGetLastError());
     ++launches;
     if (fh)
-      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDeviceToHost, st));
+      SW_CUDA(cudaMemcpyAsync(final_fields[i], dst, size_t(g->nodes()) * sizeof(float), cudaMemcpyDefault, st));
   }
   SW_TRY(check_device_flag(b->grids[0]));  // synchronises
   b->kernel_launches = launches;

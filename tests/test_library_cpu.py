@@ -66,3 +66,36 @@ def test_workloads_are_deterministic():
     assert v.density is not None and v.order == 16
     c1 = workloads.make("2d_homogeneous_256")
     assert c1.updates == 256 * 256 * 1000 and len(c1.rec_pos) == 64
+
+
+def test_binding_checks_buffer_sizes_before_the_call():
+    """The C calls read and write whole buffers of the sizes the grid implies
+    and cannot see the caller's: the binding refuses a buffer of the wrong size
+    (and shot positions that do not match the acquisition's sources) before
+    anything reaches the library.  A handle-less Grid stands in for a real one:
+    every case must raise before the library is touched."""
+    g = api.Grid(None, 3, (4, 5, 6), None)
+    g.n_src, g.n_rec = 2, 7
+    nodes = 4 * 5 * 6
+    f32 = lambda n: np.zeros(n, np.float32)
+    with pytest.raises(ValueError, match="velocity"):
+        api.sw_set_model(g, f32(nodes - 1))
+    with pytest.raises(ValueError, match="density"):
+        api.sw_set_model(g, f32(nodes), f32(nodes + 1))
+    with pytest.raises(ValueError, match="seismogram"):
+        api.sw_forward(g, 10, f32(10 * 7 - 1))
+    with pytest.raises(ValueError, match="final_field"):
+        api.sw_forward(g, 10, f32(10 * 7), f32(nodes - 6))
+    with pytest.raises(ValueError, match="observed"):
+        api.sw_gradient(g, 10, f32(10 * 7 - 1), f32(nodes))
+    with pytest.raises(ValueError, match="grad_vel"):
+        api.sw_gradient(g, 10, f32(10 * 7), f32(nodes + 1))
+    with pytest.raises(ValueError, match="grad_rho"):
+        api.sw_gradient(g, 10, f32(10 * 7), f32(nodes), grad_rho=f32(1))
+    # one position per shot while the acquisition has two sources
+    with pytest.raises(ValueError, match="shot_src_pos"):
+        api.sw_gradient_shots(g, np.zeros((3, 3)), 10, f32(3 * 10 * 7), f32(nodes))
+    with pytest.raises(ValueError, match="observed"):
+        api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7 - 1), f32(nodes))
+    with pytest.raises(ValueError, match="grad_vel"):
+        api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7), f32(nodes - 1))
