@@ -226,6 +226,7 @@ def sw_set_initial_state(g: Grid, p0=None, pm1=None) -> None:
 def sw_set_saving(g: Grid, saving_stride: int, snapshots=None, max_frames: int = 0) -> None:
     """Every later sw_forward writes p after saving_stride, 2 saving_stride, ...
     steps into the frames of `snapshots` (device, [max_frames, *grid]); 0 turns it off."""
+    _need("snapshots", snapshots, max(int(max_frames), 0) * g.nodes, at_least=True)
     _check(_lib.load().sw_set_saving(g.handle, int(saving_stride), _ptr(snapshots), int(max_frames)))
 
 
@@ -268,8 +269,17 @@ def sw_create_batch(grids) -> Batch:
 def sw_batch_forward(b: Batch, n_steps: int, seismograms=None, final_fields=None) -> None:
     """seismograms: per grid a device tensor [n_steps, n_rec] (or None); final_fields: per grid or None."""
     n = len(b.grids)
-    seis = _ptr_array(list(seismograms) if seismograms is not None else [None] * n)
-    fin = _ptr_array(list(final_fields)) if final_fields is not None else None
+    seismograms = list(seismograms) if seismograms is not None else [None] * n
+    if len(seismograms) != n or (final_fields is not None and len(list(final_fields)) != n):
+        raise ValueError("expected one seismogram (or None) and one final field per grid (%d)" % n)
+    for i, (g, s_) in enumerate(zip(b.grids, seismograms)):
+        _need("seismogram of grid %d" % i, s_, max(int(n_steps), 0) * g.n_rec, at_least=True)
+    if final_fields is not None:
+        final_fields = list(final_fields)
+        for i, (g, f_) in enumerate(zip(b.grids, final_fields)):
+            _need("final field of grid %d" % i, f_, g.nodes)
+    seis = _ptr_array(seismograms)
+    fin = _ptr_array(final_fields) if final_fields is not None else None
     _check(_lib.load().sw_batch_forward(b.handle, int(n_steps), seis, fin))
 
 

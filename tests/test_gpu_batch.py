@@ -160,8 +160,9 @@ def test_batch_errors(cuda_device):
             seis = [torch.zeros((10, len(s.recs)), device="cuda:0") for s in shots[:2]]
             with pytest.raises(api.SimwaveError):  # host seismograms are refused
                 api.sw_batch_forward(b, 10, [np.zeros((10, len(shots[0].recs)), np.float32), seis[1]])
+            long_seis = [torch.zeros((shots[0].n_steps + 1, len(s.recs)), device="cuda:0") for s in shots[:2]]
             with pytest.raises(api.SimwaveError):  # longer than the wavelets
-                api.sw_batch_forward(b, shots[0].n_steps + 1, seis)
+                api.sw_batch_forward(b, shots[0].n_steps + 1, long_seis)
             api.sw_batch_forward(b, 10, seis)
             api.sw_set_acquisition(g1, np.zeros((0, 2)), np.zeros((0, 2)), np.zeros(1, np.float32))
             with pytest.raises(api.SimwaveError):  # a grid changed after the batch was made

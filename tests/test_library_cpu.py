@@ -99,3 +99,21 @@ def test_binding_checks_buffer_sizes_before_the_call():
         api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7 - 1), f32(nodes))
     with pytest.raises(ValueError, match="grad_vel"):
         api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7), f32(nodes - 1))
+
+
+def test_binding_checks_batch_and_snapshot_buffers():
+    """The same size checks for the snapshot frames and for a batch's per-grid
+    outputs (one of each per grid, each of its own grid's size)."""
+    g1 = api.Grid(None, 3, (4, 5, 6), None)
+    g2 = api.Grid(None, 3, (3, 5, 6), None)
+    g1.n_rec, g2.n_rec = 7, 2
+    f32 = lambda n: np.zeros(n, np.float32)
+    with pytest.raises(ValueError, match="snapshots"):
+        api.sw_set_saving(g1, 5, f32(3 * 120 - 1), max_frames=3)
+    b = api.Batch(None, [g1, g2])
+    with pytest.raises(ValueError, match="per grid"):
+        api.sw_batch_forward(b, 10, [f32(70)])
+    with pytest.raises(ValueError, match="seismogram of grid 1"):
+        api.sw_batch_forward(b, 10, [f32(70), f32(19)])
+    with pytest.raises(ValueError, match="final field of grid 1"):
+        api.sw_batch_forward(b, 10, [None, None], [f32(120), f32(120)])
