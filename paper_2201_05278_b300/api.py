@@ -136,6 +136,8 @@ def sw_set_acquisition(g: Grid, src_pos, rec_pos, wavelet, window_radius: int = 
     else:
         wav = np.ascontiguousarray(np.asarray(wavelet, dtype=np.float32))
         nt = int(wav.shape[-1])
+    # the library reads n_src * nt samples with one wavelet per source, nt otherwise
+    _need("wavelet", wav, (int(src.shape[0]) if wavelet_per_source else 1) * nt, at_least=True)
     dp = ctypes.POINTER(ctypes.c_double)
     _check(_lib.load().sw_set_acquisition(
         g.handle, int(src.shape[0]), src.ctypes.data_as(dp), int(rec.shape[0]), rec.ctypes.data_as(dp),

@@ -99,6 +99,9 @@ def test_binding_checks_buffer_sizes_before_the_call():
         api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7 - 1), f32(nodes))
     with pytest.raises(ValueError, match="grad_vel"):
         api.sw_gradient_shots(g, np.zeros((3, 2, 3)), 10, f32(3 * 10 * 7), f32(nodes - 1))
+    # one wavelet per source asked for, one wavelet given
+    with pytest.raises(ValueError, match="wavelet"):
+        api.sw_set_acquisition(g, np.zeros((2, 3)), np.zeros((7, 3)), f32(50), wavelet_per_source=True)
 
 
 def test_binding_checks_batch_and_snapshot_buffers():
